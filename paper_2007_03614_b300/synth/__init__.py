@@ -1,0 +1,270 @@
+"""Seeded synthetic road networks and trip tables (input generation only).
+
+Stands in for the paper's data pipeline -- the OSM street network (Section II-A),
+the TAZ-level demand with nodes sampled uniformly inside each zone (Section II-B)
+and the shortest-path routing computed only for the OD pairs needed (Section II-C).
+None of the simulation's arithmetic lives here; both the CPU oracle and the CUDA
+library consume the arrays this module returns.
+
+``Network`` and ``Trips`` are plain containers of numpy arrays whose names match
+the arguments of ``manta_create`` / ``manta_load_trips``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "synth.c")
+_LIB = os.path.join(_HERE, "libmanta_synth.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile synth.c into an in-tree shared library (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                               "-o", _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+class _Net(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_edges", C.c_int32),
+                ("edge_src", C.POINTER(C.c_int32)), ("edge_dst", C.POINTER(C.c_int32)),
+                ("edge_lanes", C.POINTER(C.c_uint8)), ("edge_class", C.POINTER(C.c_uint8)),
+                ("edge_length_m", C.POINTER(C.c_float)), ("edge_speed_mps", C.POINTER(C.c_float)),
+                ("node_type", C.POINTER(C.c_uint8)),
+                ("node_cycle", C.POINTER(C.c_int32)), ("node_offset", C.POINTER(C.c_int32)),
+                ("edge_green_start", C.POINTER(C.c_int16)), ("edge_green_len", C.POINTER(C.c_int16)),
+                ("n_conn", C.c_int64), ("conn_lane_mask", C.POINTER(C.c_uint32)),
+                ("node_i", C.POINTER(C.c_int32)), ("node_j", C.POINTER(C.c_int32)),
+                ("edge_dir", C.POINTER(C.c_uint8))]
+
+
+class _LatticeParams(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32),
+                ("arterial_every", C.c_int32), ("freeway_every", C.c_int32),
+                ("local_keep", C.c_double),
+                ("len_median_m", C.c_double), ("len_sigma", C.c_double),
+                ("len_min_m", C.c_double), ("len_max_m", C.c_double),
+                ("speed_mps", C.c_float * 3), ("lanes", C.c_uint8 * 3),
+                ("signal_cycle_steps", C.c_int32), ("signal_green_steps", C.c_int32),
+                ("signals_at", C.c_int32), ("all_stop", C.c_int32), ("seed", C.c_uint64)]
+
+
+class _Trips(C.Structure):
+    _fields_ = [("n_trips", C.c_int64),
+                ("origin", C.POINTER(C.c_int32)), ("dest", C.POINTER(C.c_int32)),
+                ("depart_time_s", C.POINTER(C.c_float)),
+                ("route_off", C.POINTER(C.c_int64)), ("route_edges", C.POINTER(C.c_int32)),
+                ("n_route_edges", C.c_int64), ("n_unroutable", C.c_int64)]
+
+
+class _TripParams(C.Structure):
+    _fields_ = [("n_trips", C.c_int64), ("od_model", C.c_int32),
+                ("zones_x", C.c_int32), ("zones_y", C.c_int32), ("pool_per_zone", C.c_int32),
+                ("spacing_km", C.c_double), ("beta_km", C.c_double), ("zone_mass_sigma", C.c_double),
+                ("depart_model", C.c_int32),
+                ("t_lo_s", C.c_double), ("t_hi_s", C.c_double), ("mean_s", C.c_double),
+                ("sd_s", C.c_double), ("mean2_s", C.c_double), ("sd2_s", C.c_double), ("w2", C.c_double),
+                ("seed", C.c_uint64), ("n_threads", C.c_int32)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(_LIB)
+        lib.synth_lattice.restype = C.POINTER(_Net)
+        lib.synth_lattice.argtypes = [C.POINTER(_LatticeParams)]
+        lib.synth_net_free.argtypes = [C.POINTER(_Net)]
+        lib.synth_make_trips.restype = C.POINTER(_Trips)
+        lib.synth_make_trips.argtypes = [C.POINTER(_Net), C.POINTER(_TripParams)]
+        lib.synth_trips_free.argtypes = [C.POINTER(_Trips)]
+        _lib = lib
+    return _lib
+
+
+def _copy(ptr, n, dtype):
+    if n == 0:
+        return np.zeros(0, dtype=dtype)
+    return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
+
+
+@dataclass
+class Network:
+    """A directed road network in the layout ``manta_create`` takes."""
+    edge_src: np.ndarray
+    edge_dst: np.ndarray
+    edge_lanes: np.ndarray
+    edge_length_m: np.ndarray
+    edge_speed_limit_mps: np.ndarray
+    edge_class: np.ndarray
+    node_type: np.ndarray
+    node_cycle_steps: np.ndarray
+    node_offset_steps: np.ndarray
+    edge_green_start: np.ndarray
+    edge_green_len: np.ndarray
+    conn_lane_mask: np.ndarray | None
+    node_i: np.ndarray | None = None
+    node_j: np.ndarray | None = None
+    edge_dir: np.ndarray | None = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.node_type.shape[0])
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.edge_src.shape[0])
+
+
+@dataclass
+class Trips:
+    """Trips in the layout ``manta_load_trips`` takes (route CSR + departure times)."""
+    route_off: np.ndarray      # int64 [n+1]
+    route_edges: np.ndarray    # int32
+    depart_time_s: np.ndarray  # float32 [n], seconds since midnight
+    origin: np.ndarray | None = None
+    dest: np.ndarray | None = None
+
+    @property
+    def n_trips(self) -> int:
+        return int(self.depart_time_s.shape[0])
+
+
+# Road classes used by the lattice generator: local, arterial, freeway.
+CLASS_LOCAL, CLASS_ARTERIAL, CLASS_FREEWAY = 0, 1, 2
+
+
+def lattice(nx, ny, *, arterial_every=0, freeway_every=0, local_keep=1.0,
+            len_median_m=100.0, len_sigma=0.0, len_min_m=20.0, len_max_m=2000.0,
+            speed_mps=(11.111, 19.444, 29.167), lanes=(1, 2, 4),
+            signal_cycle_steps=120, signal_green_steps=60, signals_at=0, all_stop=False,
+            seed=1) -> Network:
+    lib = _load()
+    p = _LatticeParams()
+    p.nx, p.ny = nx, ny
+    p.arterial_every, p.freeway_every = arterial_every, freeway_every
+    p.local_keep = local_keep
+    p.len_median_m, p.len_sigma, p.len_min_m, p.len_max_m = len_median_m, len_sigma, len_min_m, len_max_m
+    for i in range(3):
+        p.speed_mps[i] = speed_mps[i]
+        p.lanes[i] = lanes[i]
+    p.signal_cycle_steps, p.signal_green_steps = signal_cycle_steps, signal_green_steps
+    p.signals_at, p.all_stop, p.seed = signals_at, int(all_stop), seed
+    h = lib.synth_lattice(C.byref(p))
+    n = h.contents
+    try:
+        N, E = n.n_nodes, n.n_edges
+        net = Network(
+            edge_src=_copy(n.edge_src, E, np.int32), edge_dst=_copy(n.edge_dst, E, np.int32),
+            edge_lanes=_copy(n.edge_lanes, E, np.uint8),
+            edge_length_m=_copy(n.edge_length_m, E, np.float32),
+            edge_speed_limit_mps=_copy(n.edge_speed_mps, E, np.float32),
+            edge_class=_copy(n.edge_class, E, np.uint8),
+            node_type=_copy(n.node_type, N, np.uint8),
+            node_cycle_steps=_copy(n.node_cycle, N, np.int32),
+            node_offset_steps=_copy(n.node_offset, N, np.int32),
+            edge_green_start=_copy(n.edge_green_start, E, np.int16),
+            edge_green_len=_copy(n.edge_green_len, E, np.int16),
+            conn_lane_mask=_copy(n.conn_lane_mask, n.n_conn, np.uint32),
+            node_i=_copy(n.node_i, N, np.int32), node_j=_copy(n.node_j, N, np.int32),
+            edge_dir=_copy(n.edge_dir, E, np.uint8))
+    finally:
+        lib.synth_net_free(h)
+    net.meta = dict(kind="lattice", nx=nx, ny=ny, seed=seed)
+    return net
+
+
+def make_trips(net: Network, n_trips, *, od_model="uniform", zones=(20, 25), pool_per_zone=16,
+               spacing_km=0.15, beta_km=10.0, zone_mass_sigma=1.0,
+               depart="uniform", t_lo_s=0.0, t_hi_s=600.0, mean_s=0.0, sd_s=1.0,
+               mean2_s=0.0, sd2_s=1.0, w2=0.0, seed=1, n_threads=None) -> Trips:
+    lib = _load()
+    cn = _Net()
+    keep = []
+
+    def ptr(a, ct):
+        a = np.ascontiguousarray(a)
+        keep.append(a)
+        return a.ctypes.data_as(C.POINTER(ct))
+
+    cn.n_nodes, cn.n_edges = net.n_nodes, net.n_edges
+    cn.edge_src, cn.edge_dst = ptr(net.edge_src, C.c_int32), ptr(net.edge_dst, C.c_int32)
+    cn.edge_length_m = ptr(net.edge_length_m.astype(np.float32), C.c_float)
+    cn.edge_speed_mps = ptr(net.edge_speed_limit_mps.astype(np.float32), C.c_float)
+    ni = net.node_i if net.node_i is not None else np.zeros(net.n_nodes, np.int32)
+    nj = net.node_j if net.node_j is not None else np.zeros(net.n_nodes, np.int32)
+    cn.node_i, cn.node_j = ptr(ni.astype(np.int32), C.c_int32), ptr(nj.astype(np.int32), C.c_int32)
+    tp = _TripParams()
+    tp.n_trips = n_trips
+    tp.od_model = {"uniform": 0, "gravity": 1}[od_model]
+    tp.zones_x, tp.zones_y = zones
+    tp.pool_per_zone = pool_per_zone
+    tp.spacing_km, tp.beta_km, tp.zone_mass_sigma = spacing_km, beta_km, zone_mass_sigma
+    tp.depart_model = {"uniform": 0, "normal": 1, "bimodal": 2}[depart]
+    tp.t_lo_s, tp.t_hi_s, tp.mean_s, tp.sd_s = t_lo_s, t_hi_s, mean_s, sd_s
+    tp.mean2_s, tp.sd2_s, tp.w2 = mean2_s, sd2_s, w2
+    tp.seed = seed
+    tp.n_threads = n_threads or os.cpu_count() or 1
+    h = lib.synth_make_trips(C.byref(cn), C.byref(tp))
+    t = h.contents
+    try:
+        if t.n_unroutable:
+            raise RuntimeError(f"{t.n_unroutable} trips had no route")
+        trips = Trips(route_off=_copy(t.route_off, n_trips + 1, np.int64),
+                      route_edges=_copy(t.route_edges, t.n_route_edges, np.int32),
+                      depart_time_s=_copy(t.depart_time_s, n_trips, np.float32),
+                      origin=_copy(t.origin, n_trips, np.int32), dest=_copy(t.dest, n_trips, np.int32))
+    finally:
+        lib.synth_trips_free(h)
+    return trips
+
+
+# ---------------------------------------------------------------- workloads --
+def tiny_network(seed=1) -> Network:
+    """10x10 grid, 100 m edges, 2 lanes per direction, 50 km/h, fixed-time
+    signals (two 30 s phases, 120-step cycle) at the 64 interior nodes,
+    boundary nodes uncontrolled."""
+    return lattice(10, 10, arterial_every=1, len_median_m=100.0, len_sigma=0.0,
+                   len_min_m=100.0, len_max_m=100.0, speed_mps=(13.889, 13.889, 13.889),
+                   lanes=(2, 2, 2), signals_at=2, seed=seed)
+
+
+def tiny_trips(net: Network, n_trips=1000, seed=1) -> Trips:
+    """Uniform-random OD node pairs, departures uniform over the first 10 min."""
+    return make_trips(net, n_trips, od_model="uniform", depart="uniform", t_lo_s=0.0,
+                      t_hi_s=600.0, seed=seed)
+
+
+METRO_SIDE = 482
+
+
+def metro_network(seed=2, side=METRO_SIDE) -> Network:
+    """Metro-shaped synthetic network: perturbed-free lattice with local (1 lane,
+    40 km/h), arterial every 8th line (2 lanes, 70 km/h) and freeway every 32nd
+    line (4 lanes, 105 km/h); lognormal lengths (median 120 m, sigma 0.8);
+    local segments thinned to about 550k directed edges; fixed-time signals at
+    arterial crossings."""
+    return lattice(side, side, arterial_every=8, freeway_every=32, local_keep=0.545,
+                   len_median_m=120.0, len_sigma=0.8, len_min_m=20.0, len_max_m=2000.0,
+                   speed_mps=(11.111, 19.444, 29.167), lanes=(1, 2, 4),
+                   signals_at=1, seed=seed)
+
+
+def metro_trips(net: Network, n_trips=3_200_000, seed=2, t_lo_s=5 * 3600.0, t_hi_s=12 * 3600.0,
+                n_threads=None) -> Trips:
+    """Gravity OD over 20x25 zones (lognormal masses, exp(-d/10 km)), origins from
+    a pool of 16 nodes per zone, destinations uniform in the zone; departures
+    normal(08:00, 75 min) truncated to [05:00, 12:00)."""
+    return make_trips(net, n_trips, od_model="gravity", zones=(20, 25), pool_per_zone=16,
+                      spacing_km=0.15, beta_km=10.0, depart="normal", t_lo_s=t_lo_s, t_hi_s=t_hi_s,
+                      mean_s=8 * 3600.0, sd_s=75 * 60.0, seed=seed, n_threads=n_threads)

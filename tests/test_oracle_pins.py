@@ -1,0 +1,421 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of the expected values below comes from the CUDA path or from the
+oracle itself: they are closed forms (IDM ODE, IDM steady state), published
+generator outputs, invariants, or hand traces.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import nets
+from oracle import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+G64 = 0x9E3779B97F4A7C15
+
+
+# ---------------------------------------------------------------- RNG pins --
+def test_splitmix64_reference_outputs():
+    """SplitMix64 (Steele, Lea, Flood 2014): outputs from state 0."""
+    vals = [int(l.strip(), 16) for l in open(os.path.join(HERE, "golden", "splitmix64_reference.txt"))
+            if l.strip() and not l.startswith("#")]
+    got = [O.splitmix64((i * G64) & (2**64 - 1)) for i in range(3)]
+    assert got == vals
+
+
+def test_uniform_and_irwin_hall_moments():
+    """U in [0,1) with mean 1/2, var 1/12; the Irwin-Hall normal has mean 0, var 1,
+    support [-6, 6] (epsilon of Eqs. 3-4: mean 0, sd 1 m)."""
+    u = np.array([O.rng_u(7, i, 3, 0) for i in range(20000)])
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 0.01 and abs(u.var() - 1 / 12) < 0.003
+    n = np.array([O.rng_n(7, i, 3, 1) for i in range(20000)])
+    assert n.min() >= -6.0 and n.max() <= 6.0
+    assert abs(n.mean()) < 0.03 and abs(n.var() - 1.0) < 0.04
+    # different streams and steps are different draws
+    assert O.rng_n(7, 5, 3, 1) != O.rng_n(7, 5, 3, 2)
+    assert O.rng_u(7, 5, 3, 0) != O.rng_u(7, 5, 4, 0)
+
+
+def test_defaults_match_paper_constants():
+    rows = {}
+    for line in open(os.path.join(HERE, "golden", "paper_constants.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        rows[parts[0]] = parts[1:]
+    d = O.DEFAULTS
+    assert d["dt"] == float(rows["dt"][0])
+    assert d["cell_m"] == float(rows["cell_m"][0])
+    assert d["lc_x0_m"] == float(rows["lc_x0_m"][0])
+    assert d["alpha_lo"] == float(rows["alpha_lo"][0]) and d["alpha_hi"] == float(rows["alpha_hi"][0])
+    assert d["stop_dwell_steps"] * d["dt"] == float(rows["stop_s"][0])
+    lo, hi = map(float, rows["gap_low_range"][:2])
+    assert lo <= d["g_low"] <= hi
+    lo, hi = map(float, rows["gap_high_range"][:2])
+    assert lo <= d["g_high"] <= hi
+    for key, name in (("a", "a_range"), ("b", "b_range"), ("T", "T_range"), ("s0", "s0_range")):
+        lo, hi = map(float, rows[name][:2])
+        assert all(lo <= x <= hi for x in d[key])
+    assert abs(d["g_speed_split"] - 25 * 0.44704) < 1e-3   # 25 mph
+
+
+# ------------------------------------------------------- T1: free-flow ODE --
+def _lone_vehicle(dt, n_updates, v0=20.0, a=1.0):
+    net = nets.line(20, length=2000.0, speed=v0)
+    tr = nets.trips([list(range(20))], [0.0])
+    s = O.OracleSim(net, dt=dt, a=[a] * 8)
+    nets.load(s, tr)
+    s.step(1)                      # departure at step 0 (enters at x = 0, v = 0)
+    out = []
+    for _ in range(n_updates):
+        s.step(1)
+        sn = s.snapshot()
+        out.append((float(sn["v"][0]), int(sn["route_pos"][0]), float(sn["x"][0])))
+    return out
+
+
+def _t_of_v(v, v0, a):
+    """Closed form of the free-road IDM ODE dv/dt = a (1 - (v/v0)^4), v(0) = 0."""
+    u = v / v0
+    return v0 / (2 * a) * (math.atanh(u) + math.atan(u))
+
+
+def _v_of_t(t, v0, a):
+    lo, hi = 0.0, v0 * (1 - 1e-15)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if _t_of_v(mid, v0, a) < t:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_free_flow_matches_float64_replay():
+    """Same discrete map (explicit velocity step, ballistic position) in float64."""
+    v0, a, dt = 20.0, 1.0, 0.5
+    traj = _lone_vehicle(dt, 200, v0, a)
+    v, x = 0.0, 0.0
+    for vg, rp, xg in traj:
+        acc = a * (1 - (v / v0) ** 4)
+        x = x + v * dt + 0.5 * acc * dt * dt
+        v = v + acc * dt
+        assert abs(vg - v) <= 2e-5 * max(1.0, v)
+        assert abs(rp * 2000.0 + xg - x) <= 2e-3
+    assert traj[-1][0] > 19.0
+
+
+def test_free_flow_first_order_convergence_to_ode():
+    """|v_k - v(t_k)| is first order in dt: halving dt halves the error."""
+    v0, a, t = 20.0, 1.0, 20.0
+    exact = _v_of_t(t, v0, a)
+    e1 = abs(_lone_vehicle(0.5, int(t / 0.5), v0, a)[-1][0] - exact)
+    e2 = abs(_lone_vehicle(0.25, int(t / 0.25), v0, a)[-1][0] - exact)
+    assert e1 < 0.05 * v0
+    assert 1.7 < e1 / e2 < 2.3
+
+
+# ------------------------------------------------------ T2: ring equilibrium --
+def _ring_sim(n_veh, ring_edges=4, edge_len=100.0, v_init=0.0, laps=400, **cfg):
+    total = int(ring_edges * edge_len)
+    d = total // n_veh
+    net = nets.ring(ring_edges, length=edge_len, speed=20.0)
+    routes = []
+    for i in range(n_veh):
+        e0 = (i * d) // int(edge_len)
+        routes.append([(e0 + j) % ring_edges for j in range(ring_edges * laps)])
+    tr = nets.trips(routes, [1e7] * n_veh)
+    s = O.OracleSim(net, **cfg)
+    nets.load(s, tr)
+    for i in range(n_veh):
+        s.place(i, 0, 0, float((i * d) % int(edge_len)) + 0.5, v_init)
+    return s, d
+
+
+def _ieq(v, s, v0=20.0, a=1.0, b=2.0, T=1.5, s0=2.0):
+    code = min(254, int(v * 8 + 0.5))
+    dv = v - code * 0.125
+    return 1 - (v / v0) ** 4 - ((s0 + v * T + v * dv / (2 * math.sqrt(a * b))) / s) ** 2
+
+
+def _equilibrium_speeds(s):
+    """All roots of the steady-state relation. The one-byte leader speed makes
+    it piecewise continuous (one piece per speed code), so each piece is
+    bisected on its own."""
+    roots = []
+    for code in range(0, 161):
+        lo, hi = max(0.0, (code - 0.5) / 8), min(20.0, (code + 0.5) / 8)
+        lo, hi = lo + 1e-12, hi - 1e-12
+        if lo >= hi or (_ieq(lo, s) > 0) == (_ieq(hi, s) > 0):
+            continue
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if (_ieq(mid, s) > 0) == (_ieq(lo, s) > 0):
+                lo = mid
+            else:
+                hi = mid
+        roots.append(0.5 * (lo + hi))
+    return roots
+
+
+@pytest.mark.parametrize("n_veh", [4, 8])
+def test_ring_converges_to_idm_steady_state(n_veh):
+    """Homogeneous ring: every vehicle settles at the speed solving the IDM
+    equilibrium 1 - (v/v0)^4 - (s*(v, dv)/s)^2 = 0 with s = d - L and the
+    leader speed seen through the one-byte code (Treiber & Kesting 2013)."""
+    s, d = _ring_sim(n_veh, a=[1.0] * 8)
+    s.step(3000)
+    vs = []
+    for _ in range(100):
+        s.step(1)
+        vs.append(s.snapshot()["v"].copy())
+    vs = np.array(vs)
+    roots = _equilibrium_speeds(d - 5)
+    assert roots
+    assert min(abs(vs.mean() - r) for r in roots) < 2e-3, (vs.mean(), roots)
+    assert vs.std() < 5e-3
+    s.check()
+
+
+def test_ring_jam_below_minimum_gap():
+    """Spacing d with d - L <= s0: the IDM interaction term is >= the free
+    term at v = 0, so a queue at rest never moves."""
+    s, d = _ring_sim(60, edge_len=105.0, v_init=0.0)        # 420 cells / 60: d = 7 -> s = 2 = s0
+    assert d == 7
+    s.step(200)
+    sn = s.snapshot()
+    assert np.all(sn["v"] == 0.0)
+    assert s.stats()["arrived"] == 0
+
+
+# --------------------------------------------- T3/T4: conservation, no overlap --
+def _lane_orders(sn):
+    orders = {}
+    for i in np.argsort(-(sn["edge"].astype(np.int64) * 10**7 + sn["lane"].astype(np.int64) * 10**6
+                          - sn["x"].astype(np.float64))):
+        orders.setdefault((int(sn["edge"][i]), int(sn["lane"][i])), []).append(int(sn["id"][i]))
+    return orders
+
+
+def test_tiny_conservation_overlap_fifo():
+    from paper_2007_03614_b300 import synth
+    net = synth.tiny_network()
+    tr = synth.tiny_trips(net)
+    s = O.OracleSim(net)
+    nets.load(s, tr)
+    prev = None
+    for k in range(2000):
+        s.step(1)
+        s.check()                       # map == vehicles, fronts >= L apart, conservation
+        st = s.stats()
+        assert st["departed"] == st["arrived"] + st["on_network"]
+        assert st["loaded"] == st["departed"] + st["waiting"]
+        sn = s.snapshot()
+        cur = _lane_orders(sn)
+        if prev is not None:
+            # vehicles that stayed in the same lane keep their order (no overtaking in a lane)
+            for key, ids in cur.items():
+                old = prev.get(key, [])
+                common = [i for i in ids if i in set(old)]
+                old_common = [i for i in old if i in set(common)]
+                assert common == old_common, (k, key)
+        prev = cur
+    st = s.stats()
+    assert st["arrived"] == 1000 and st["on_network"] == 0
+    ec = s.edge_counters(0)
+    assert int(ec["entries"].sum()) == int(ec["exits"].sum())
+
+
+# ------------------------------------------------------------- T5: merge --
+def test_merge_lowest_id_wins_hand_trace():
+    """Two vehicles reach the merge node in the same step: the lower id enters
+    the out-edge, the other is held at its position with v = 0; next step the
+    held one finds the winner in front and stays."""
+    net = nets.merge(length=100.0, speed=13.889)
+    routes = [[0, 2]] * 8
+    routes[3] = [0, 2]
+    routes[7] = [1, 2]
+    tr = nets.trips(routes, [1e7] * 8)
+    s = O.OracleSim(net)
+    nets.load(s, tr)
+    s.place(3, 0, 0, 99.75, 2.0)
+    s.place(7, 0, 0, 99.75, 2.0)
+    s.step(1)
+    sn = s.snapshot()
+    byid = {int(i): j for j, i in enumerate(sn["id"])}
+    # hand trace of Eq. 1 on a free road and the ballistic update:
+    acc = 1.0 * (1 - (2.0 / 13.889) ** 4)
+    x_new = 99.75 + 2.0 * 0.5 + 0.5 * acc * 0.25
+    w, l = byid[3], byid[7]
+    assert sn["edge"][w] == 2 and abs(sn["x"][w] - (x_new - 100.0)) < 1e-5
+    assert abs(sn["v"][w] - (2.0 + acc * 0.5)) < 1e-5
+    assert sn["edge"][l] == 1 and sn["x"][l] == np.float32(99.75) and sn["v"][l] == 0.0
+    ec = s.edge_counters(0)
+    assert ec["entries"][2] == 1 and ec["exits"][0] == 1 and ec["exits"][1] == 0
+    # step 2: 7 sees 3 at cell 0 of edge 2: gap 0 - 99 - 5 < 0 -> stays put
+    s.step(1)
+    sn = s.snapshot()
+    byid = {int(i): j for j, i in enumerate(sn["id"])}
+    assert sn["edge"][byid[7]] == 1 and sn["v"][byid[7]] == 0.0
+    # a few steps later 3 has moved on and 7 follows onto edge 2
+    s.step(20)
+    sn = s.snapshot()
+    byid = {int(i): j for j, i in enumerate(sn["id"])}
+    assert sn["edge"][byid[7]] == 2
+    assert sn["x"][byid[3]] - sn["x"][byid[7]] >= 5
+    s.check()
+
+
+def test_departure_competes_with_crossing():
+    """A departure onto edge 2 and a crossing into lane 0 of edge 2 in the same
+    step: the lower id wins, the other waits (departure) or is held (crossing)."""
+    for dep_id, cross_id in ((1, 5), (5, 1)):
+        net = nets.merge()
+        routes = [[0, 2]] * 6
+        routes[dep_id] = [2]
+        routes[cross_id] = [0, 2]
+        tr = nets.trips(routes, [1e7 if i not in (dep_id,) else 0.0 for i in range(6)])
+        s = O.OracleSim(net)
+        nets.load(s, tr)
+        s.place(cross_id, 0, 0, 99.75, 2.0)
+        s.step(1)
+        sn = s.snapshot()
+        byid = {int(i): j for j, i in enumerate(sn["id"])}
+        if dep_id < cross_id:
+            assert dep_id in byid and sn["edge"][byid[dep_id]] == 2 and sn["x"][byid[dep_id]] == 0.0
+            assert sn["edge"][byid[cross_id]] == 0 and sn["v"][byid[cross_id]] == 0.0
+        else:
+            assert dep_id not in byid
+            assert sn["edge"][byid[cross_id]] == 2
+        s.check()
+
+
+# --------------------------------------------------- T6: signal and stop sign --
+def test_red_signal_stop_and_go():
+    """Fixed-time signal: the approach is red for steps [0, 60) of each 120-step
+    cycle. A vehicle stops short of the stop line and leaves once it turns green."""
+    edges = [(0, 1, 1, 150.0, 13.889, 0), (1, 2, 1, 1000.0, 13.889, 0)]
+    net = nets.network(3, edges, node_type=[0, 2, 0], cycle=[0, 120, 0], green={0: (60, 60)})
+    tr = nets.trips([[0, 1]], [0.0])
+    s = O.OracleSim(net)
+    nets.load(s, tr)
+    xs = []
+    for k in range(60):
+        s.step(1)
+        sn = s.snapshot()
+        xs.append((int(sn["edge"][0]), float(sn["x"][0]), float(sn["v"][0])))
+    e, x, v = xs[-1]
+    assert e == 0 and v < 0.05
+    assert 150 - 1 - 2 - 1.5 <= x <= 150 - 1        # within about s0 of the stop line, never past it
+    s.step(40)
+    sn = s.snapshot()
+    assert sn["edge"][0] == 1                        # crossed after the light turned green at k = 60
+
+
+def test_stop_sign_dwell_permit_round_robin():
+    """Flashing red: each vehicle stops for 4 steps (2 s) and holds the node's
+    only permit while crossing; in-lanes are served in round-robin order."""
+    edges = [(0, 2, 1, 60.0, 13.889, 0), (1, 2, 1, 60.0, 13.889, 0), (2, 3, 1, 400.0, 13.889, 0)]
+    net = nets.network(4, edges, node_type=[0, 0, 1, 0])
+    routes = [[0, 2], [1, 2], [0, 2], [1, 2]]
+    tr = nets.trips(routes, [1e7] * 4)
+    s = O.OracleSim(net)
+    nets.load(s, tr)
+    s.place(0, 0, 0, 40.0, 0.0)
+    s.place(1, 0, 0, 40.0, 0.0)
+    s.place(2, 0, 0, 20.0, 0.0)
+    s.place(3, 0, 0, 20.0, 0.0)
+    order, permits = [], []
+    seen = set()
+    for k in range(600):
+        s.step(1)
+        permits.append(s.permit(2))
+        sn = s.snapshot()
+        for i, e in zip(sn["id"], sn["edge"]):
+            if e == 2 and int(i) not in seen:
+                seen.add(int(i))
+                order.append(int(i))
+        s.check()
+    assert order == [0, 1, 2, 3]                     # round robin over in-lanes (edge 0, edge 1, ...)
+    # never two vehicles hold/cross at once: a permit changes only to NONE in between holders
+    holders = [p for p in permits if p != 0xFFFFFFFF]
+    assert sorted(set(holders)) == [0, 1, 2, 3]
+
+
+# -------------------------------------------------------- T7: lane change --
+def _gap_eval(v, va, vb, lead_gap, lag_gap, alpha, eps_a, eps_b, g):
+    glead = max(g, g + alpha * v + alpha * (v - va)) + eps_a      # Eq. 3
+    glag = max(g, g + alpha * v + alpha * (v - vb)) + eps_b       # Eq. 4
+    return lead_gap >= glead and lag_gap >= glag, glead, glag
+
+
+@pytest.mark.parametrize("lead_at,lag_at", [(80, 30), (62, 30), (80, 45), (80, 20), (80, 40), (80, 38)])
+def test_discretionary_change_gap_acceptance_hand_trace(lead_at, lag_at):
+    """Vehicle 0 at cell 50 (v = 10) behind a slow leader in lane 0 (cell 60);
+    lane 1 has a lead at `lead_at` and a lag at `lag_at`. On an even step the
+    target is lane 1; the change happens iff Eqs. 3-4 accept both gaps."""
+    net = nets.line(1, length=300.0, lanes=2, speed=20.0)
+    tr = nets.trips([[0]] * 4, [1e7] * 4)
+    seed = 11
+    s = O.OracleSim(net, seed=seed)
+    nets.load(s, tr)
+    s.place(0, 0, 0, 50.2, 10.0)
+    s.place(1, 0, 0, 60.2, 2.0)
+    s.place(2, 0, 1, lead_at + 0.2, 6.0)
+    s.place(3, 0, 1, lag_at + 0.2, 12.0)
+    k = 0
+    alpha = 0.05 + 0.35 * O.rng_u(seed, 0, 0, 3)
+    eps_a, eps_b = O.rng_n(seed, 0, k, 1), O.rng_n(seed, 0, k, 2)
+    L = 5
+    overlap = abs(lead_at - 50) < L or abs(lag_at - 50) < L
+    ok, gl, gg = _gap_eval(10.0, 6.0, 12.0, lead_at - L - 50, 50 - L - lag_at, alpha, eps_a, eps_b, 3.0)
+    # the own gap is 60 - 5 - 50 = 5; the target lead gap must be larger
+    own_ok = (lead_at - L - 50) > 5
+    expected = ok and own_ok and not overlap
+    assert abs((lead_at - L - 50) - gl) > 0.05 and abs((50 - L - lag_at) - gg) > 0.05  # not a rounding tie
+    s.step(1)
+    sn = s.snapshot()
+    byid = {int(i): j for j, i in enumerate(sn["id"])}
+    assert int(sn["lane"][byid[0]]) == (1 if expected else 0)
+    assert s.stats()["lane_changes"] == (1 if expected else 0)
+
+
+def test_mandatory_change_probability_eq2():
+    """Eq. 2 with x0 = 1 m: at 1 m from the end the change is certain (if the
+    gaps accept); far from the end (m ~ 0) it never happens."""
+    # edge 0 (2 lanes) -> edge 1 turns right: only lane 0 may continue
+    edges = [(0, 1, 2, 200.0, 13.889, 0), (1, 2, 1, 200.0, 13.889, 0)]
+    net = nets.network(3, edges, conn=[1])
+    for x, expect in ((150.3, 0), (198.3, 1)):
+        tr = nets.trips([[0, 1]], [1e7])
+        s = O.OracleSim(net)
+        nets.load(s, tr)
+        s.place(0, 0, 1, x, 0.0)
+        s.step(1)          # k = 0: dir = +1, away from lane 0: nothing
+        s.step(1)          # k = 1: dir = -1, toward lane 0
+        sn = s.snapshot()
+        assert int(sn["lane"][0]) == (0 if expect else 1)
+
+
+def test_wrong_lane_holds_at_stop_line():
+    """A vehicle in a lane that may not take its next turn stops at the end of
+    the edge instead of crossing (virtual leader at the stop line)."""
+    edges = [(0, 1, 2, 100.0, 13.889, 0), (1, 2, 1, 200.0, 13.889, 0)]
+    net = nets.network(3, edges, conn=[1])
+    tr = nets.trips([[0, 1], [0, 1]], [1e7, 1e7])
+    s = O.OracleSim(net)
+    nets.load(s, tr)
+    s.place(0, 0, 1, 50.0, 10.0)
+    s.place(1, 0, 0, 90.0, 0.0)     # blocks lane 0 around the end for a while
+    for _ in range(30):
+        s.step(1)
+        sn = s.snapshot()
+        byid = {int(i): j for j, i in enumerate(sn["id"])}
+        j = byid[0]
+        if sn["lane"][j] == 1:
+            assert sn["edge"][j] == 0 and sn["x"][j] <= 99.0
+        s.check()
