@@ -1,0 +1,332 @@
+"""Benchmark: vehicle-updates/s of the metro-shaped morning (05:00-12:00,
+dt = 0.5 s, 3.2M trips, ~550k edges) on one B300, through the C ABI.
+
+A bench "step" is one chunk of `--chunk` simulated time steps (default 1800 =
+15 simulated minutes) of the whole hot path: departures, lane changes, leader
+scans, IDM, merges, arrivals, lane-map writes, statistics.  `--warmup W`
+chunks run untimed, then `--steps K` chunks are timed with CUDA events on the
+simulation's stream; the default W + K = 28 chunks is the whole morning.
+
+Between timed chunks the L2 is flushed (a 256 MB write, outside the events);
+the working set (two 140 MB lane maps, 1.8 GB of routes) is larger than L2.
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload.  With torchrun (N > 1) every rank runs an independent
+replica of the same workload (the update does not shard without an exchange
+step); value = updates of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vehicle-updates/s & wall-time of 3.2M-trip morning at dt=0.5 s; % HBM peak"
+UNIT = "vehicle-updates/s"
+T0_STEP = 36000                     # 05:00 at dt = 0.5 s
+MORNING_STEPS = 50400               # 05:00-12:00
+
+# Algorithmic bytes of the step kernel ("Roofline"): per vehicle
+# update, per lane-map cell examined by the leader scan, per route boundary
+# crossed by a scan, per gap-acceptance evaluation.
+BYTES_PER_UPDATE = 114
+BYTES_PER_CELL = 1
+BYTES_PER_ROUTE_READ = 20
+BYTES_PER_LC_EVAL = 48
+
+
+def algorithmic_bytes(d: dict) -> int:
+    return (d["vehicle_updates"] * BYTES_PER_UPDATE + d["cells_scanned"] * BYTES_PER_CELL
+            + d["route_reads"] * BYTES_PER_ROUTE_READ + d["lc_evals"] * BYTES_PER_LC_EVAL)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, world
+
+
+def workload(seed=2):
+    from paper_2007_03614_b300 import synth
+    net = synth.metro_network(seed=seed)
+    tr = synth.metro_trips(net, seed=seed)
+    return net, tr
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [int(r[1]) for r in rows]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for nm, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": int(statistics.median(sm)), "sm_max_mhz": int(rows[0][2]), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2007_03614_b300 import manta
+    from paper_2007_03614_b300.build import build
+
+    rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world > 1:
+        build() if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    manta.load_library()
+    net, tr = workload()
+    stream = torch.cuda.Stream()
+    chunk = args.chunk
+    # ---- device-resident run (the headline value) ----
+    sim = manta.Sim(net, stream=stream, t0_step=T0_STEP)
+    sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sim.step(chunk)
+    s0 = sim.stats()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    times = []
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                sim.step(chunk)
+                ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1) / 1000.0)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    s1 = sim.stats()
+    elapsed = sum(times)
+    d = {k: s1[k] - s0[k] for k in ("vehicle_updates", "cells_scanned", "route_reads", "lc_evals", "clamps",
+                                    "lane_changes", "departed", "arrived")}
+    if world > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        u = torch.tensor([d["vehicle_updates"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_updates = float(u.item())
+    else:
+        total_updates = float(d["vehicle_updates"])
+    morning = None
+    if T0_STEP + (args.warmup + args.steps) * chunk >= T0_STEP + MORNING_STEPS:
+        morning = None  # filled by the e2e run below, which always simulates the whole morning
+    sim.close()
+    del flush
+    # ---- end-to-end through the C ABI from host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        h2d = sum(a.nbytes for a in (net.edge_src, net.edge_dst, net.edge_lanes, net.edge_length_m,
+                                      net.edge_speed_limit_mps, net.edge_class, net.node_type, net.node_cycle_steps,
+                                      net.node_offset_steps, net.edge_green_start, net.edge_green_len,
+                                      net.conn_lane_mask, tr.route_off, tr.route_edges, tr.depart_time_s))
+        n_chunks = args.warmup + args.steps
+        t0 = time.perf_counter()
+        sim2 = manta.Sim(net, stream=stream, t0_step=T0_STEP)
+        sim2.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+        t_load = time.perf_counter() - t0
+        upd = 0
+        for _ in range(n_chunks):
+            sim2.step(chunk)
+            st = sim2.stats()                 # device -> host read of the step's result
+        upd = st["vehicle_updates"]
+        t_e2e = time.perf_counter() - t0
+        morning_steps = n_chunks * chunk
+        e2e = {"value": upd / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d // n_chunks),
+               "d2h_bytes_per_step": 96, "seconds": round(t_e2e, 3), "create_load_s": round(t_load, 3),
+               "sim_steps": morning_steps}
+        if morning_steps >= MORNING_STEPS:
+            morning = round(t_e2e - t_load, 3)
+        sim2.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    bytes_alg = algorithmic_bytes(d)
+    per_launch_s = elapsed / max(1, args.steps)
+    achieved = bytes_alg / max(1, args.steps) / per_launch_s / 1e9
+    out = {
+        "metric": METRIC, "value": total_updates / elapsed, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded metro-shaped lattice network and gravity-model trips)",
+        "config": {"workload": "metro-shaped morning: ~550k directed edges / ~218k nodes, 3.2M trips, "
+                               "05:00-12:00 departures N(08:00, 75 min), dt = 0.5 s",
+                   "sim_steps_per_bench_step": chunk, "t0_step": T0_STEP,
+                   "timed_sim_window": [T0_STEP + args.warmup * chunk, T0_STEP + (args.warmup + args.steps) * chunk],
+                   "l2": "flushed between timed steps (256 MB write) and working set > L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "gpu_launches": args.steps * ((chunk + 2047) // 2048),
+        "morning_wall_s": morning,
+        "counters": d,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(bytes_alg / max(1, args.steps))},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(net, tr, args.cpu_steps)
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _sample(tr, lo_s, hi_s):
+    sel = np.nonzero((tr.depart_time_s >= lo_s) & (tr.depart_time_s < hi_s))[0]
+    ro = tr.route_off
+    lens = ro[sel + 1] - ro[sel]
+    off = np.zeros(len(sel) + 1, np.int64)
+    off[1:] = np.cumsum(lens)
+    idx = np.concatenate([np.arange(ro[i], ro[i + 1]) for i in sel]) if len(sel) else np.zeros(0, np.int64)
+    return off, tr.route_edges[idx], tr.depart_time_s[sel]
+
+
+def cpu_baseline(net, tr, n_steps):
+    """The CPU oracle, single-threaded, on a bounded sample of the workload:
+    the metro network from an empty start at 07:30 with the trips departing
+    07:30-07:40, `n_steps` steps."""
+    from oracle import oracle as O
+    lo = 7.5 * 3600
+    off, edges, dep = _sample(tr, lo, lo + 600)
+    s = O.OracleSim(net, t0_step=int(lo / 0.5), n_stats_windows=4)
+    s.load_trips(off, edges, dep)
+    t0 = time.perf_counter()
+    s.step(n_steps)
+    dt = time.perf_counter() - t0
+    upd = s.stats()["vehicle_updates"]
+    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"metro network, trips departing 07:30-07:40 ({len(dep)}), {n_steps} steps from an empty "
+                      f"network at 07:30, {upd} vehicle updates in {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world = _dist()
+    if rank != 0:
+        return
+    net, tr = workload()
+    from oracle import oracle as O
+    lo = 7.5 * 3600
+    off, edges, dep = _sample(tr, lo, lo + 600)
+    s = O.OracleSim(net, t0_step=int(lo / 0.5), n_stats_windows=4)
+    s.load_trips(off, edges, dep)
+    per = args.ref_chunk
+    for _ in range(args.warmup):
+        s.step(per)
+    u0 = s.stats()["vehicle_updates"]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(per)
+    dt = time.perf_counter() - t0
+    upd = s.stats()["vehicle_updates"] - u0
+    v = upd / dt
+    sample = (f"metro network, trips departing 07:30-07:40 ({len(dep)}), empty start at 07:30; each step = "
+              f"{per} oracle time steps")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * dt / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "metro-shaped network, CPU oracle sample", "sim_steps_per_bench_step": per},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=25)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--chunk", type=int, default=1800)
+    ap.add_argument("--impl", default="manta", choices=["manta", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=200)
+    ap.add_argument("--ref-chunk", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        raise SystemExit("need --steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * manta.h -- C ABI of the B300 (sm_103a) microsimulation library.
+ *
+ * The library runs the per-timestep update of the MANTA traffic
+ * microsimulator (Yedavalli, Kumar, Waddell, arXiv 2007.03614, Section II-D):
+ * every on-network vehicle looks up its leader in a byte-per-metre lane map
+ * ("traffic atlas"), scanning ahead along its precomputed route; applies the
+ * Intelligent Driver Model (Eq. 1) with the lane-change rule (Eq. 2) and the
+ * gap-acceptance rule (Eqs. 3-4) and the intersection controls of Section
+ * II-D (case 1 flashing red, case 2 green) plus fixed-time signals; advances
+ * at dt; and writes itself into a double-buffered next-step map.  Departing
+ * trips are injected and arrivals retired in the same step.
+ *
+ * Conventions for every call:
+ *  - Status: each call returns a manta_status and sets a thread-local message
+ *    readable with manta_last_error().
+ *  - Ownership: every input array is caller-owned HOST memory, copied during
+ *    the call; the library keeps no caller pointer.  Every output array is
+ *    caller-owned host memory of the stated length.
+ *  - Device memory: the library allocates and owns all device memory of a
+ *    simulation (cudaMalloc); manta_destroy frees it.
+ *  - Streams: work is enqueued on the cudaStream_t given to manta_create
+ *    (NULL = the legacy default stream).  manta_step returns without waiting;
+ *    calls that return data (manta_stats, manta_edge_counters, manta_snapshot,
+ *    manta_lane_map) synchronise that stream.
+ *  - Device errors: a bounded wait that ran out (grid barrier) or an index
+ *    check that failed sets a sticky error word on the device; the next
+ *    synchronising call returns MANTA_E_TIMEOUT or MANTA_E_DEVICE and every
+ *    later manta_step does nothing.
+ *  - Threads: a simulation handle must not be used from two threads at once.
+ */
+#ifndef MANTA_H
+#define MANTA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MANTA_API __attribute__((visibility("default")))
+#else
+#define MANTA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct manta_sim manta_sim;
+
+typedef enum {
+  MANTA_OK = 0,
+  MANTA_E_INVALID = -1,   /* bad argument or configuration                       */
+  MANTA_E_ROUTE = -2,     /* empty, out-of-range or non-contiguous route          */
+  MANTA_E_STATE = -3,     /* call not allowed in the current state                */
+  MANTA_E_OOM = -4,       /* device allocation failed                              */
+  MANTA_E_CUDA = -5,      /* a CUDA runtime call failed                            */
+  MANTA_E_TIMEOUT = -6,   /* a device-side bounded wait ran out                    */
+  MANTA_E_DEVICE = -7     /* a device-side index check failed                      */
+} manta_status;
+
+/* Node control types (Section II-D "case 1" / "case 2", plus fixed-time signals). */
+enum { MANTA_NODE_GREEN = 0, MANTA_NODE_STOP = 1, MANTA_NODE_SIGNAL = 2 };
+
+/* Model configuration.  Lengths in metres (= cells, cell_m must be 1),
+ * times in seconds or steps of dt as named.  Defaults: manta_default_config. */
+typedef struct {
+  float dt;                 /* time step, Section II-D: 0.5 s                                   */
+  float cell_m;             /* lane-map cell length t_m, Section II-D: 1 m (only 1 supported)  */
+  int32_t veh_len_cells;    /* vehicle length L in cells: 5                                     */
+  int32_t horizon_cells;    /* leader-scan horizon H in cells (>= 16): 256                      */
+  int32_t n_classes;        /* road classes (1..8); edge_class < n_classes                      */
+  float v0f[8];             /* desired speed v0 = speed limit x v0f[class] (Eq. 1): 1           */
+  float T[8];               /* time headway T (Eq. 1), s: 1.5                                   */
+  float a[8];               /* maximum acceleration a (Eq. 1), m/s^2: 1.0                       */
+  float b[8];               /* comfortable deceleration b (Eq. 1), m/s^2: 2.0                   */
+  float s0[8];              /* jam distance s0 (Eq. 1), m: 2.0                                  */
+  float lc_x0_m;            /* critical distance x0 of Eq. 2: 1 m                               */
+  float lc_len_scale_m;     /* length scale of Eq. 2's exponent: 1 m (the literal equation)     */
+  float alpha_lo, alpha_hi; /* anticipation-time range of Eqs. 3-4: 0.05, 0.40 s                */
+  float g_low, g_high;      /* desired lead/lag gap below / above g_speed_split: 3.0, 7.5 m     */
+  float g_speed_split;      /* 25 mph = 11.176 m/s                                              */
+  int32_t stop_dwell_steps; /* flashing-red stop before proceeding, Section IV-C: 4 (= 2 s)     */
+  float stop_v_eps;         /* speed below which a vehicle counts as stopped: 0.1 m/s           */
+  int32_t stats_window_steps; /* per-edge speed statistics window: 600 steps (5 min)            */
+  int32_t n_stats_windows;  /* windows kept per edge: 96                                        */
+  int32_t idm_textbook;     /* 0: Eq. 1 as printed; 1: s* = s0 + max(0, vT + v dv / 2 sqrt(ab)) */
+  int64_t t0_step;          /* absolute step index of the first manta_step (t = t0_step * dt)   */
+  uint64_t seed;            /* seed of the counter-based random numbers (Eqs. 2-4)              */
+} manta_config;
+
+typedef struct {
+  int64_t step;             /* absolute index of the next step to run                  */
+  int64_t loaded, departed, arrived, on_network, waiting;
+  uint64_t vehicle_updates; /* vehicle-steps updated (one per on-network vehicle and step) */
+  uint64_t cells_scanned;   /* lane-map cells examined by leader scans                 */
+  uint64_t clamps;          /* updates clamped to the leader's rear / a stop line      */
+  uint64_t lane_changes;    /* lane changes applied                                    */
+  uint64_t lc_evals;        /* gap-acceptance evaluations (Eqs. 3-4)                   */
+  uint64_t route_reads;     /* route entries read by leader scans crossing a node       */
+} manta_stats_t;
+
+/* Fills *cfg with the defaults listed above. */
+MANTA_API void manta_default_config(manta_config *cfg);
+
+/* Builds a simulation on the current CUDA device from a directed road network
+ * (Section II-A: edges with lanes, length and speed limit; Section II-D: node
+ * control).  Arrays (host memory, copied):
+ *   edge_src, edge_dst [n_edges]   node ids in [0, n_nodes)
+ *   edge_lanes [n_edges]           1..8
+ *   edge_length_m [n_edges]        > 0; the edge gets max(L + ceil(max s0) + 1,
+ *                                  round(length / cell_m)) cells (Section II-D)
+ *   edge_speed_limit_mps [n_edges] > 0
+ *   edge_class [n_edges]           < cfg->n_classes
+ *   node_type [n_nodes]            MANTA_NODE_*
+ *   node_cycle_steps, node_offset_steps [n_nodes]  signal cycle (1..32767) and
+ *                                  offset in steps; read for signal nodes only
+ *   edge_green_start, edge_green_len [n_edges]  green window of an in-edge
+ *                                  within its head node's cycle: green iff
+ *                                  ((k - offset) mod cycle) in [start, start+len)
+ *   conn_lane_mask                 NULL = every lane may take every turn; else,
+ *                                  for each in-edge e in id order and each
+ *                                  out-edge e2 of e's head node in ascending
+ *                                  id, a bitmask of e's lanes allowed to
+ *                                  continue onto e2 (non-empty)
+ *   cuda_stream                    cudaStream_t for all work, or NULL
+ * Errors: MANTA_E_INVALID (bad array/config), MANTA_E_OOM, MANTA_E_CUDA.
+ * On success *out owns the simulation; release it with manta_destroy. */
+MANTA_API manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_src, const int32_t *edge_dst,
+                          const uint8_t *edge_lanes, const float *edge_length_m,
+                          const float *edge_speed_limit_mps, const uint8_t *edge_class,
+                          const uint8_t *node_type, const int32_t *node_cycle_steps,
+                          const int32_t *node_offset_steps, const int16_t *edge_green_start,
+                          const int16_t *edge_green_len, const uint32_t *conn_lane_mask,
+                          const manta_config *cfg, void *cuda_stream, manta_sim **out);
+
+/* Loads the trips (Section II-C routes, Section II-D departure times), once,
+ * before the first manta_step.  Trip i (its vehicle id) follows edges
+ * route_edges[route_off[i] .. route_off[i+1]) and may depart at absolute step
+ * ceil(depart_time_s[i] / dt) or later (seconds on the same clock as
+ * t0_step * dt).  route_off has n_trips + 1 entries, route_off[0] = 0.
+ * Departures enter lane 0 of the first edge at x = 0, v = 0.
+ * Errors: MANTA_E_ROUTE (empty route, edge out of range, consecutive edges not
+ * sharing a node), MANTA_E_INVALID, MANTA_E_STATE (already loaded), MANTA_E_OOM. */
+MANTA_API manta_status manta_load_trips(manta_sim *sim, int64_t n_trips, const int64_t *route_off,
+                              const int32_t *route_edges, const float *depart_time_s);
+
+/* Enqueues n_steps >= 0 time steps (Section II-D update) on the stream and
+ * returns.  A device error from earlier work is reported here only if it is
+ * already known on the host; otherwise at the next synchronising call.
+ * Errors: MANTA_E_STATE (no trips loaded or a sticky device error),
+ * MANTA_E_CUDA. */
+MANTA_API manta_status manta_step(manta_sim *sim, int64_t n_steps);
+
+/* Synchronises the stream and returns the scalar counters. */
+MANTA_API manta_status manta_stats(manta_sim *sim, manta_stats_t *out);
+
+/* Synchronises and copies per-edge counters: entries and exits since the
+ * start [n_edges], and, for statistics window `window` (window w covers steps
+ * t0_step + [w, w+1) * stats_window_steps), the per-edge sum of end-of-step
+ * speeds in units of 2^-20 m/s (truncated per vehicle-step) and the number of
+ * vehicle-steps (link speeds of Sections IV-A/B).  Any pointer may be NULL. */
+MANTA_API manta_status manta_edge_counters(manta_sim *sim, uint32_t *entries, uint32_t *exits, uint64_t *speed_sum_fx,
+                                 uint32_t *speed_cnt, int32_t window);
+
+/* Synchronises and copies the on-network vehicles in ascending id into arrays
+ * of capacity `cap`: front position in cells from the start of the edge,
+ * speed, edge, lane, id, stop dwell counter, position in the route.  *n_out
+ * receives the count; MANTA_E_INVALID if cap is too small.  Pointers may be NULL. */
+MANTA_API manta_status manta_snapshot(manta_sim *sim, int64_t cap, int64_t *n_out, float *x, float *v, int32_t *edge,
+                            uint8_t *lane, uint32_t *id, uint8_t *dwell, int32_t *route_pos);
+
+/* Synchronises and copies the current lane map in canonical layout: edges in
+ * id order, lanes in order, one byte per cell (0xFF empty, else the speed code
+ * round(8 v) saturated at 254).  *n_out = total bytes; MANTA_E_INVALID if cap
+ * is too small. */
+MANTA_API manta_status manta_lane_map(manta_sim *sim, uint8_t *out, int64_t cap, int64_t *n_out);
+
+/* Bytes of the canonical lane map (sum over edges of cells x lanes). */
+MANTA_API int64_t manta_lane_map_bytes(const manta_sim *sim);
+
+/* Releases every device and host resource of the simulation (NULL is a no-op). */
+MANTA_API void manta_destroy(manta_sim *sim);
+
+/* Message of the last failing call on this thread ("" if none). */
+MANTA_API const char *manta_last_error(void);
+
+/* Self-test of the device grid barrier's bounded wait: launches a small
+ * cooperative kernel in which one block never arrives, with a wait limit of
+ * about `limit_ms` milliseconds; returns MANTA_E_TIMEOUT when every waiting
+ * block gave up and returned (the expected outcome), MANTA_OK if the wait
+ * did not run out.  The context stays usable. */
+MANTA_API manta_status manta_selftest_barrier_timeout(int32_t limit_ms, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MANTA_H */

@@ -1,0 +1,620 @@
+// manta.cu -- host side of the C ABI declared in include/manta.h.
+//
+// Validation, lane-map layout, departure queues and every device allocation
+// live here; the per-step work is the persistent kernel in step_kernel.cuh.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "manta.h"
+#include "sim.cuh"
+#include "step_kernel.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+manta_status fail(manta_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+constexpr int32_t kStepsPerLaunch = 2048;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per grid barrier wait
+
+__global__ void prime_kernel(Params p, uint32_t hi, int cb) {
+  uint32_t *dep = cb ? p.dep1 : p.dep0;
+  const uint32_t gsz = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gsz) {
+    const uint32_t e = p.due_edge[i];
+    const bool first = atomicAdd(p.pending + e, 1u) == 0u;
+    const uint32_t at = warp_append(&p.ctl->n_dep[cb], first);
+    if (first) dep[at] = e;
+  }
+}
+
+__global__ void barrier_selftest_kernel(Ctl *ctl, uint64_t limit_ns) {
+  __shared__ int s_ok;
+  if (blockIdx.x == 0) return;   // this block never arrives
+  grid_sync(ctl, limit_ns, &s_ok);
+}
+
+}  // namespace
+
+struct manta_sim {
+  manta_config cfg;
+  cudaStream_t stream = nullptr;
+  int32_t N = 0, E = 0;
+  std::vector<uint32_t> cells, lanes, row0, lane_base;
+  std::vector<int32_t> esrc, edst;
+  std::vector<int64_t> out_off, conn_off;
+  std::vector<int32_t> out_e;
+  std::vector<uint32_t> conn;
+  uint64_t atlas_bytes = 0, canon_bytes = 0;
+  uint32_t n_lanes = 0;
+  std::vector<void *> allocs;
+  Params P;
+  bool loaded = false, primed = false, dead = false;
+  int64_t k = 0, n_trips = 0;
+  uint32_t prime_hi = 0;
+  std::vector<uint32_t> route_off_h;
+  int grid = 0;
+};
+
+namespace {
+
+template <class T>
+T *dalloc(manta_sim *S, size_t n, bool *ok) {
+  void *p = nullptr;
+  if (n == 0) n = 1;
+  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *ok = false;
+    return nullptr;
+  }
+  S->allocs.push_back(p);
+  return static_cast<T *>(p);
+}
+
+template <class T>
+bool upload(manta_sim *S, T *dst, const std::vector<T> &src) {
+  if (src.empty()) return true;
+  return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
+}
+
+manta_status check_cfg(const manta_config *c) {
+  if (!c) return fail(MANTA_E_INVALID, "config is NULL");
+  if (c->cell_m != 1.0f) return fail(MANTA_E_INVALID, "cell_m must be 1");
+  if (!(c->dt > 0.0f) || !(c->dt < 60.0f)) return fail(MANTA_E_INVALID, "dt out of range");
+  if (c->veh_len_cells < 1 || c->veh_len_cells > 100) return fail(MANTA_E_INVALID, "veh_len_cells out of range");
+  if (c->horizon_cells < 16 || c->horizon_cells > (1 << 20)) return fail(MANTA_E_INVALID, "horizon_cells out of range");
+  if (c->n_classes < 1 || c->n_classes > 8) return fail(MANTA_E_INVALID, "n_classes out of range");
+  for (int i = 0; i < c->n_classes; ++i)
+    if (!(c->a[i] > 0.0f) || !(c->b[i] > 0.0f) || !(c->T[i] >= 0.0f) || !(c->s0[i] >= 0.0f) ||
+        !(c->s0[i] < 100.0f) || !(c->v0f[i] > 0.0f))
+      return fail(MANTA_E_INVALID, "bad class parameters");
+  if (c->stop_dwell_steps < 1 || c->stop_dwell_steps > 255) return fail(MANTA_E_INVALID, "stop_dwell_steps out of range");
+  if (c->stats_window_steps < 1 || c->n_stats_windows < 1) return fail(MANTA_E_INVALID, "bad statistics windows");
+  if (c->t0_step < 0 || c->t0_step > (int64_t)1 << 40) return fail(MANTA_E_INVALID, "t0_step out of range");
+  if (!(c->lc_len_scale_m > 0.0f)) return fail(MANTA_E_INVALID, "lc_len_scale_m must be > 0");
+  return MANTA_OK;
+}
+
+uint32_t stride16(uint32_t c) { return (c + 15u) & ~15u; }
+
+}  // namespace
+
+extern "C" {
+
+void manta_default_config(manta_config *c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->dt = 0.5f;
+  c->cell_m = 1.0f;
+  c->veh_len_cells = 5;
+  c->horizon_cells = 256;
+  c->n_classes = 3;
+  for (int i = 0; i < 8; ++i) { c->v0f[i] = 1.0f; c->T[i] = 1.5f; c->a[i] = 1.0f; c->b[i] = 2.0f; c->s0[i] = 2.0f; }
+  c->lc_x0_m = 1.0f;
+  c->lc_len_scale_m = 1.0f;
+  c->alpha_lo = 0.05f;
+  c->alpha_hi = 0.40f;
+  c->g_low = 3.0f;
+  c->g_high = 7.5f;
+  c->g_speed_split = 11.176f;
+  c->stop_dwell_steps = 4;
+  c->stop_v_eps = 0.1f;
+  c->stats_window_steps = 600;
+  c->n_stats_windows = 96;
+  c->idm_textbook = 0;
+  c->t0_step = 0;
+  c->seed = 1;
+}
+
+const char *manta_last_error(void) { return g_err.c_str(); }
+
+void manta_destroy(manta_sim *S) {
+  if (!S) return;
+  if (S->stream || true) cudaStreamSynchronize(S->stream);
+  for (void *p : S->allocs) cudaFree(p);
+  delete S;
+}
+
+manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_src, const int32_t *edge_dst,
+                          const uint8_t *edge_lanes, const float *edge_length_m,
+                          const float *edge_speed_limit_mps, const uint8_t *edge_class,
+                          const uint8_t *node_type, const int32_t *node_cycle_steps,
+                          const int32_t *node_offset_steps, const int16_t *edge_green_start,
+                          const int16_t *edge_green_len, const uint32_t *conn_lane_mask,
+                          const manta_config *cfg, void *cuda_stream, manta_sim **out) {
+  g_err.clear();
+  if (!out) return fail(MANTA_E_INVALID, "out is NULL");
+  *out = nullptr;
+  manta_status st = check_cfg(cfg);
+  if (st != MANTA_OK) return st;
+  if (n_nodes <= 0 || n_edges <= 0) return fail(MANTA_E_INVALID, "empty network");
+  if (n_edges > (int32_t)MANTA_EDGE_MASK) return fail(MANTA_E_INVALID, "too many edges (max 2^24 - 1)");
+  if (!edge_src || !edge_dst || !edge_lanes || !edge_length_m || !edge_speed_limit_mps || !edge_class || !node_type)
+    return fail(MANTA_E_INVALID, "required network array is NULL");
+  const int32_t N = n_nodes, E = n_edges, L = cfg->veh_len_cells;
+  float s0max = 0.0f;
+  for (int i = 0; i < cfg->n_classes; ++i) s0max = std::max(s0max, cfg->s0[i]);
+  const uint32_t cmin = (uint32_t)(L + (int)std::ceil(s0max) + 1);
+  for (int32_t n = 0; n < N; ++n) {
+    if (node_type[n] > 2) return fail(MANTA_E_INVALID, "node_type out of range at node " + std::to_string(n));
+    if (node_type[n] == MANTA_NODE_SIGNAL &&
+        (!node_cycle_steps || !node_offset_steps || node_cycle_steps[n] < 1 || node_cycle_steps[n] > 32767))
+      return fail(MANTA_E_INVALID, "signal node without a cycle in 1..32767 at node " + std::to_string(n));
+  }
+  manta_sim *S = new manta_sim();
+  S->cfg = *cfg;
+  S->stream = static_cast<cudaStream_t>(cuda_stream);
+  S->N = N;
+  S->E = E;
+  S->cells.resize(E); S->lanes.resize(E); S->row0.resize(E); S->lane_base.resize(E + 1);
+  S->esrc.assign(edge_src, edge_src + E); S->edst.assign(edge_dst, edge_dst + E);
+  std::vector<EdgeMeta> em(E);
+  std::vector<EdgeSig> es(E);
+  uint64_t bytes = 0, canon = 0;
+  uint32_t lanes_total = 0, maxC = 0;
+  for (int32_t e = 0; e < E; ++e) {
+    const float len = edge_length_m[e], lim = edge_speed_limit_mps[e];
+    if (edge_src[e] < 0 || edge_src[e] >= N || edge_dst[e] < 0 || edge_dst[e] >= N || edge_lanes[e] < 1 ||
+        edge_lanes[e] > 8 || edge_class[e] >= cfg->n_classes || !(lim > 0.0f) || !(len > 0.0f) || !(len <= 1.0e6f)) {
+      delete S;
+      return fail(MANTA_E_INVALID, "bad edge " + std::to_string(e));
+    }
+    // Section II-D: one cell per t_m = 1 m of length
+    int64_t c = std::llround((double)len / (double)cfg->cell_m);
+    if (c < (int64_t)cmin) c = cmin;
+    S->cells[e] = (uint32_t)c;
+    S->lanes[e] = edge_lanes[e];
+    maxC = std::max(maxC, (uint32_t)c);
+    S->row0[e] = (uint32_t)bytes;
+    S->lane_base[e] = lanes_total;
+    bytes += (uint64_t)stride16((uint32_t)c) * edge_lanes[e];
+    canon += (uint64_t)c * edge_lanes[e];
+    lanes_total += edge_lanes[e];
+    if (bytes > 0xFFFFFF00ull) { delete S; return fail(MANTA_E_INVALID, "lane map larger than 4 GB"); }
+    em[e].row0 = S->row0[e];
+    em[e].cnl = (uint32_t)c | ((uint32_t)edge_lanes[e] << 24) | ((uint32_t)edge_class[e] << 28);
+    em[e].lim = lim;
+    em[e].dst = (uint32_t)edge_dst[e];
+    es[e] = EdgeSig{0, 0, 0, 0};
+    const int32_t n = edge_dst[e];
+    if (node_type[n] == MANTA_NODE_SIGNAL) {
+      if (!edge_green_start || !edge_green_len) { delete S; return fail(MANTA_E_INVALID, "signal windows are NULL"); }
+      const int32_t cyc = node_cycle_steps[n];
+      int64_t off = (int64_t)node_offset_steps[n] % cyc;
+      if (off < 0) off += cyc;
+      es[e].cyc = (int16_t)cyc;
+      es[e].off = (int16_t)off;
+      es[e].gs = edge_green_start[e];
+      es[e].gl = edge_green_len[e];
+    }
+  }
+  S->lane_base[E] = lanes_total;
+  S->n_lanes = lanes_total;
+  S->atlas_bytes = bytes;
+  S->canon_bytes = canon;
+  // out-edges per node (ascending id) and lane masks per (in-edge, out-edge)
+  S->out_off.assign(N + 1, 0);
+  for (int32_t e = 0; e < E; ++e) S->out_off[edge_src[e] + 1]++;
+  for (int32_t n = 0; n < N; ++n) S->out_off[n + 1] += S->out_off[n];
+  S->out_e.resize(E);
+  {
+    std::vector<int64_t> f(S->out_off.begin(), S->out_off.end() - 1);
+    for (int32_t e = 0; e < E; ++e) S->out_e[f[edge_src[e]]++] = e;
+  }
+  S->conn_off.assign(E + 1, 0);
+  for (int32_t e = 0; e < E; ++e) {
+    const int32_t n = edge_dst[e];
+    S->conn_off[e + 1] = S->conn_off[e] + (S->out_off[n + 1] - S->out_off[n]);
+  }
+  S->conn.resize(S->conn_off[E]);
+  for (int32_t e = 0; e < E; ++e) {
+    const uint32_t all = (1u << S->lanes[e]) - 1u;
+    for (int64_t j = S->conn_off[e]; j < S->conn_off[e + 1]; ++j) {
+      const uint32_t m = conn_lane_mask ? (conn_lane_mask[j] & all) : all;
+      if (!m) { delete S; return fail(MANTA_E_INVALID, "lane mask with no lane for in-edge " + std::to_string(e)); }
+      S->conn[j] = m;
+    }
+  }
+  // in-lanes of every node in (edge id, lane) order; stop-node list
+  std::vector<uint32_t> nin_off(N + 1, 0), nin(lanes_total);
+  for (int32_t e = 0; e < E; ++e) nin_off[edge_dst[e] + 1] += S->lanes[e];
+  for (int32_t n = 0; n < N; ++n) nin_off[n + 1] += nin_off[n];
+  {
+    std::vector<uint32_t> f(nin_off.begin(), nin_off.end() - 1);
+    for (int32_t e = 0; e < E; ++e)
+      for (uint32_t l = 0; l < S->lanes[e]; ++l) nin[f[edge_dst[e]]++] = S->lane_base[e] + l;
+  }
+  std::vector<uint32_t> stops;
+  for (int32_t n = 0; n < N; ++n)
+    if (node_type[n] == MANTA_NODE_STOP) stops.push_back((uint32_t)n);
+  // Eq. 2 probability of a mandatory change by distance to the end of the edge
+  std::vector<float> mtab(maxC + 1);
+  for (uint32_t d = 0; d <= maxC; ++d) {
+    const double xm = (double)d * cfg->cell_m, x0 = cfg->lc_x0_m, lam = cfg->lc_len_scale_m;
+    mtab[d] = (float)(xm <= x0 ? 1.0 : std::exp(-((xm - x0) / lam) * ((xm - x0) / lam)));
+  }
+  std::vector<uint32_t> esrc_u(E);
+  for (int32_t e = 0; e < E; ++e) esrc_u[e] = (uint32_t)edge_src[e];
+  std::vector<uint32_t> lane_base_e(S->lane_base.begin(), S->lane_base.end() - 1);
+  std::vector<uint8_t> ntype(node_type, node_type + N);
+  // device allocations
+  bool ok = true;
+  Params &P = S->P;
+  memset(&P, 0, sizeof(P));
+  EdgeMeta *d_em = dalloc<EdgeMeta>(S, E, &ok);
+  EdgeSig *d_es = dalloc<EdgeSig>(S, E, &ok);
+  uint8_t *d_nt = dalloc<uint8_t>(S, N, &ok);
+  uint32_t *d_esrc = dalloc<uint32_t>(S, E, &ok);
+  uint32_t *d_lb = dalloc<uint32_t>(S, E, &ok);
+  uint32_t *d_nin_off = dalloc<uint32_t>(S, N + 1, &ok);
+  uint32_t *d_nin = dalloc<uint32_t>(S, lanes_total, &ok);
+  uint32_t *d_stops = dalloc<uint32_t>(S, stops.size(), &ok);
+  float *d_mtab = dalloc<float>(S, mtab.size(), &ok);
+  P.atlas0 = dalloc<uint8_t>(S, bytes, &ok);
+  P.atlas1 = dalloc<uint8_t>(S, bytes, &ok);
+  P.permit = dalloc<uint32_t>(S, N, &ok);
+  P.rr = dalloc<uint32_t>(S, N, &ok);
+  P.req_key = dalloc<unsigned long long>(S, lanes_total, &ok);
+  P.req_tgt = dalloc<uint32_t>(S, lanes_total, &ok);
+  P.slot_td = dalloc<uint32_t>(S, lanes_total, &ok);
+  P.slot_id = dalloc<uint32_t>(S, lanes_total, &ok);
+  P.entry = dalloc<uint32_t>(S, E, &ok);
+  P.exitc = dalloc<uint32_t>(S, E, &ok);
+  P.ssum = dalloc<unsigned long long>(S, (size_t)E * cfg->n_stats_windows, &ok);
+  P.scnt = dalloc<uint32_t>(S, (size_t)E * cfg->n_stats_windows, &ok);
+  P.pending = dalloc<uint32_t>(S, E, &ok);
+  P.q_pos = dalloc<uint32_t>(S, E, &ok);
+  P.dep_key = dalloc<unsigned long long>(S, E, &ok);
+  P.dep0 = dalloc<uint32_t>(S, E, &ok);
+  P.dep1 = dalloc<uint32_t>(S, E, &ok);
+  P.ctl = dalloc<Ctl>(S, 1, &ok);
+  if (!ok) { manta_destroy(S); return fail(MANTA_E_OOM, "device allocation failed in manta_create"); }
+  bool cp = upload(S, d_em, em) && upload(S, d_es, es) && upload(S, d_nt, ntype) && upload(S, d_esrc, esrc_u) &&
+            upload(S, d_lb, lane_base_e) && upload(S, d_nin_off, nin_off) && upload(S, d_nin, nin) &&
+            upload(S, d_stops, stops) && upload(S, d_mtab, mtab);
+  cp = cp && cudaMemsetAsync(P.atlas0, 0xFF, bytes, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.atlas1, 0xFF, bytes, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.permit, 0xFF, sizeof(uint32_t) * N, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.rr, 0, sizeof(uint32_t) * N, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.req_key, 0, sizeof(unsigned long long) * std::max<uint32_t>(lanes_total, 1), S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.slot_td, 0, sizeof(uint32_t) * std::max<uint32_t>(lanes_total, 1), S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.entry, 0, sizeof(uint32_t) * E, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.exitc, 0, sizeof(uint32_t) * E, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.ssum, 0, sizeof(unsigned long long) * (size_t)E * cfg->n_stats_windows, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.scnt, 0, sizeof(uint32_t) * (size_t)E * cfg->n_stats_windows, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.pending, 0, sizeof(uint32_t) * E, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.q_pos, 0, sizeof(uint32_t) * E, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.dep_key, 0, sizeof(unsigned long long) * E, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.ctl, 0, sizeof(Ctl), S->stream) == cudaSuccess;
+  if (!cp || cudaStreamSynchronize(S->stream) != cudaSuccess) {
+    std::string m = cudaGetErrorString(cudaGetLastError());
+    manta_destroy(S);
+    return fail(MANTA_E_CUDA, "upload failed in manta_create: " + m);
+  }
+  P.em = d_em; P.es = d_es; P.ntype = d_nt; P.esrc = d_esrc; P.lane_base = d_lb;
+  P.nin_off = d_nin_off; P.nin = d_nin; P.stop_nodes = d_stops; P.mtab = d_mtab;
+  P.dt = cfg->dt; P.L = cfg->veh_len_cells; P.H = cfg->horizon_cells;
+  for (int i = 0; i < 8; ++i) {
+    P.T[i] = cfg->T[i]; P.a[i] = cfg->a[i]; P.b[i] = cfg->b[i]; P.s0[i] = cfg->s0[i]; P.v0f[i] = cfg->v0f[i];
+    P.s0c[i] = (int32_t)std::ceil(cfg->s0[i]);
+  }
+  P.alpha_lo = cfg->alpha_lo; P.alpha_hi = cfg->alpha_hi; P.g_low = cfg->g_low; P.g_high = cfg->g_high;
+  P.g_split = cfg->g_speed_split; P.stop_eps = cfg->stop_v_eps; P.stop_dwell = cfg->stop_dwell_steps;
+  P.win_steps = cfg->stats_window_steps; P.n_win = cfg->n_stats_windows; P.textbook = cfg->idm_textbook;
+  P.t0 = cfg->t0_step; P.seed = cfg->seed;
+  P.E = (uint32_t)E; P.N = (uint32_t)N; P.n_stop = (uint32_t)stops.size(); P.mtab_n = (uint32_t)mtab.size();
+  P.wait_limit_ns = kWaitLimitNs;
+  S->k = cfg->t0_step;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, manta_step_kernel, kBlock, 0) != cudaSuccess || per_sm < 1) {
+    manta_destroy(S);
+    return fail(MANTA_E_CUDA, "occupancy query failed");
+  }
+  S->grid = sms * per_sm;
+  *out = S;
+  return MANTA_OK;
+}
+
+manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off, const int32_t *route_edges,
+                              const float *depart_time_s) {
+  g_err.clear();
+  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
+  if (S->loaded) return fail(MANTA_E_STATE, "trips already loaded");
+  if (n < 0 || n > 0x7FFFFFFE) return fail(MANTA_E_INVALID, "n_trips out of range");
+  if (n > 0 && (!route_off || !route_edges || !depart_time_s)) return fail(MANTA_E_INVALID, "trip array is NULL");
+  if (n > 0 && route_off[0] != 0) return fail(MANTA_E_ROUTE, "route_off[0] != 0");
+  const int64_t nr = n > 0 ? route_off[n] : 0;
+  if (nr < 0 || nr > 0xFFFFFFF0ll) return fail(MANTA_E_ROUTE, "too many route entries");
+  std::vector<uint32_t> route((size_t)nr), roff((size_t)n + 1);
+  std::vector<int64_t> dstep((size_t)n);
+  const double dt = S->cfg.dt;
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t a = route_off[j], b = route_off[j + 1];
+    if (b <= a || b > nr) return fail(MANTA_E_ROUTE, "empty or unordered route of trip " + std::to_string(j));
+    roff[j] = (uint32_t)a;
+    for (int64_t q = a; q < b; ++q) {
+      const int32_t e = route_edges[q];
+      if (e < 0 || e >= S->E) return fail(MANTA_E_ROUTE, "route edge out of range in trip " + std::to_string(j));
+      uint32_t mask = 0xFFu;
+      if (q + 1 < b) {
+        const int32_t e2 = route_edges[q + 1];
+        if (e2 < 0 || e2 >= S->E || S->edst[e] != S->esrc[e2])
+          return fail(MANTA_E_ROUTE, "route of trip " + std::to_string(j) + " is not contiguous");
+        const int32_t nd = S->edst[e];
+        int64_t idx = -1;
+        for (int64_t z = S->out_off[nd]; z < S->out_off[nd + 1]; ++z)
+          if (S->out_e[z] == e2) { idx = z - S->out_off[nd]; break; }
+        mask = S->conn[S->conn_off[e] + idx];
+      }
+      route[q] = (uint32_t)e | (mask << MANTA_EDGE_BITS);
+    }
+    const float t = depart_time_s[j];
+    if (!(t == t) || std::fabs((double)t / dt) > 2.0e9) return fail(MANTA_E_INVALID, "bad departure time of trip " + std::to_string(j));
+    dstep[j] = (int64_t)std::ceil((double)t / dt);
+  }
+  roff[n] = (uint32_t)nr;
+  // departure queues per first edge, ordered by (step, id)
+  std::vector<uint32_t> order((size_t)n);
+  std::iota(order.begin(), order.end(), 0u);
+  auto first_edge = [&](uint32_t j) { return route[roff[j]] & MANTA_EDGE_MASK; };
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+    const uint32_t ea = first_edge(a), eb = first_edge(b);
+    if (ea != eb) return ea < eb;
+    return dstep[a] < dstep[b];
+  });
+  std::vector<uint32_t> q_off(S->E + 1, 0);
+  for (int64_t j = 0; j < n; ++j) q_off[first_edge((uint32_t)j) + 1]++;
+  for (int32_t e = 0; e < S->E; ++e) q_off[e + 1] += q_off[e];
+  // trips in departure-step order
+  std::vector<uint32_t> dorder((size_t)n);
+  std::iota(dorder.begin(), dorder.end(), 0u);
+  std::stable_sort(dorder.begin(), dorder.end(), [&](uint32_t a, uint32_t b) { return dstep[a] < dstep[b]; });
+  std::vector<int32_t> due_step((size_t)n);
+  std::vector<uint32_t> due_edge((size_t)n);
+  uint32_t prime_hi = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t d = dstep[dorder[i]];
+    due_step[i] = (int32_t)std::max<int64_t>(std::min<int64_t>(d, INT32_MAX), INT32_MIN);
+    due_edge[i] = first_edge(dorder[i]);
+    if (d <= S->k) prime_hi = (uint32_t)(i + 1);
+  }
+  Params &P = S->P;
+  bool ok = true;
+  uint32_t *d_route = dalloc<uint32_t>(S, route.size(), &ok);
+  uint32_t *d_roff = dalloc<uint32_t>(S, roff.size(), &ok);
+  uint32_t *d_qoff = dalloc<uint32_t>(S, q_off.size(), &ok);
+  uint32_t *d_qtrip = dalloc<uint32_t>(S, order.size(), &ok);
+  int32_t *d_due = dalloc<int32_t>(S, due_step.size(), &ok);
+  uint32_t *d_due_e = dalloc<uint32_t>(S, due_edge.size(), &ok);
+  const size_t NT = (size_t)std::max<int64_t>(n, 1);
+  P.x = dalloc<float>(S, NT, &ok); P.v = dalloc<float>(S, NT, &ok);
+  P.id = dalloc<uint32_t>(S, NT, &ok); P.rc = dalloc<uint32_t>(S, NT, &ok);
+  P.rend = dalloc<uint32_t>(S, NT, &ok); P.e = dalloc<uint32_t>(S, NT, &ok);
+  P.ld = dalloc<uint32_t>(S, NT, &ok); P.pcell = dalloc<uint32_t>(S, NT, &ok);
+  P.act0 = dalloc<uint32_t>(S, NT, &ok); P.act1 = dalloc<uint32_t>(S, NT, &ok);
+  P.freel = dalloc<uint32_t>(S, NT, &ok); P.chg = dalloc<uint32_t>(S, NT, &ok);
+  P.req = dalloc<uint32_t>(S, NT, &ok); P.arr = dalloc<uint32_t>(S, NT, &ok);
+  P.req_x = dalloc<float>(S, NT, &ok); P.req_v = dalloc<float>(S, NT, &ok); P.req_dw = dalloc<uint32_t>(S, NT, &ok);
+  if (!ok) return fail(MANTA_E_OOM, "device allocation failed in manta_load_trips");
+  bool cp = upload(S, d_route, route) && upload(S, d_roff, roff) && upload(S, d_qoff, q_off) &&
+            upload(S, d_qtrip, order) && upload(S, d_due, due_step) && upload(S, d_due_e, due_edge);
+  Ctl c0;
+  memset(&c0, 0, sizeof(c0));
+  c0.due_pos = prime_hi;
+  c0.due_next = prime_hi;
+  cp = cp && cudaMemcpyAsync(P.ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
+  if (!cp) return fail(MANTA_E_CUDA, "upload failed in manta_load_trips");
+  P.route = d_route; P.route_off = d_roff; P.q_off = d_qoff; P.q_trip = d_qtrip;
+  P.due_step = d_due; P.due_edge = d_due_e; P.n_trips = (uint32_t)n;
+  S->route_off_h = std::move(roff);
+  S->n_trips = n;
+  S->prime_hi = prime_hi;
+  // trips already due at the first step join their queues
+  if (prime_hi > 0) {
+    const int cb = (int)(S->k & 1);
+    const int blocks = (int)std::min<uint32_t>((prime_hi + kBlock - 1) / kBlock, 4096u);
+    prime_kernel<<<blocks, kBlock, 0, S->stream>>>(P, prime_hi, cb);
+    if (cudaGetLastError() != cudaSuccess) return fail(MANTA_E_CUDA, "prime kernel launch failed");
+  }
+  if (cudaStreamSynchronize(S->stream) != cudaSuccess)
+    return fail(MANTA_E_CUDA, std::string("manta_load_trips: ") + cudaGetErrorString(cudaGetLastError()));
+  S->loaded = true;
+  return MANTA_OK;
+}
+
+manta_status manta_step(manta_sim *S, int64_t n_steps) {
+  g_err.clear();
+  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
+  if (!S->loaded) return fail(MANTA_E_STATE, "no trips loaded");
+  if (S->dead) return fail(MANTA_E_STATE, "simulation stopped after a device error");
+  if (n_steps < 0) return fail(MANTA_E_INVALID, "n_steps < 0");
+  while (n_steps > 0) {
+    const int32_t chunk = (int32_t)std::min<int64_t>(n_steps, kStepsPerLaunch);
+    Params P = S->P;
+    P.k0 = S->k;
+    P.n_steps = chunk;
+    void *args[] = {&P};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)manta_step_kernel, dim3(S->grid), dim3(kBlock), args, 0,
+                                                S->stream);
+    if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+    S->k += chunk;
+    n_steps -= chunk;
+  }
+  return MANTA_OK;
+}
+
+namespace {
+manta_status sync_and_check(manta_sim *S, Ctl *c) {
+  cudaError_t e = cudaStreamSynchronize(S->stream);
+  if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+  if (cudaMemcpy(c, S->P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(MANTA_E_CUDA, "reading the control block failed");
+  if (c->err == 1) { S->dead = true; return fail(MANTA_E_TIMEOUT, "a device grid-barrier wait ran out"); }
+  if (c->err != 0) { S->dead = true; return fail(MANTA_E_DEVICE, "a device index check failed"); }
+  return MANTA_OK;
+}
+}  // namespace
+
+manta_status manta_stats(manta_sim *S, manta_stats_t *out) {
+  g_err.clear();
+  if (!S || !out) return fail(MANTA_E_INVALID, "NULL argument");
+  memset(out, 0, sizeof(*out));
+  out->step = S->k;
+  out->loaded = S->n_trips;
+  out->waiting = S->n_trips;
+  if (!S->loaded) return MANTA_OK;
+  Ctl c;
+  manta_status st = sync_and_check(S, &c);
+  if (st != MANTA_OK) return st;
+  out->departed = (int64_t)c.cnt[CNT_DEP];
+  out->arrived = (int64_t)c.cnt[CNT_ARR];
+  out->on_network = c.n_act[S->k & 1];
+  out->waiting = S->n_trips - out->departed;
+  out->vehicle_updates = c.cnt[CNT_UPD];
+  out->cells_scanned = c.cnt[CNT_SCAN];
+  out->clamps = c.cnt[CNT_CLAMP];
+  out->lane_changes = c.cnt[CNT_LC];
+  out->lc_evals = c.cnt[CNT_LCE];
+  out->route_reads = c.cnt[CNT_RR];
+  return MANTA_OK;
+}
+
+manta_status manta_edge_counters(manta_sim *S, uint32_t *entries, uint32_t *exits, uint64_t *speed_sum_fx,
+                                 uint32_t *speed_cnt, int32_t window) {
+  g_err.clear();
+  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
+  if ((speed_sum_fx || speed_cnt) && (window < 0 || window >= S->cfg.n_stats_windows))
+    return fail(MANTA_E_INVALID, "window out of range");
+  Ctl c;
+  manta_status st = sync_and_check(S, &c);
+  if (st != MANTA_OK && st != MANTA_E_TIMEOUT && st != MANTA_E_DEVICE) return st;
+  const size_t E = (size_t)S->E;
+  bool ok = true;
+  if (entries) ok = ok && cudaMemcpy(entries, S->P.entry, 4 * E, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (exits) ok = ok && cudaMemcpy(exits, S->P.exitc, 4 * E, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (speed_sum_fx) ok = ok && cudaMemcpy(speed_sum_fx, S->P.ssum + (size_t)window * E, 8 * E, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (speed_cnt) ok = ok && cudaMemcpy(speed_cnt, S->P.scnt + (size_t)window * E, 4 * E, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (!ok) return fail(MANTA_E_CUDA, "copy of edge counters failed");
+  return st;
+}
+
+manta_status manta_snapshot(manta_sim *S, int64_t cap, int64_t *n_out, float *x, float *v, int32_t *edge,
+                            uint8_t *lane, uint32_t *id, uint8_t *dwell, int32_t *route_pos) {
+  g_err.clear();
+  if (!S || !n_out) return fail(MANTA_E_INVALID, "NULL argument");
+  *n_out = 0;
+  if (!S->loaded) return MANTA_OK;
+  Ctl c;
+  manta_status st = sync_and_check(S, &c);
+  if (st != MANTA_OK) return st;
+  const uint32_t n = c.n_act[S->k & 1];
+  *n_out = n;
+  if ((int64_t)n > cap) return fail(MANTA_E_INVALID, "snapshot capacity too small");
+  if (n == 0) return MANTA_OK;
+  const Params &P = S->P;
+  std::vector<uint32_t> act(n);
+  if (cudaMemcpy(act.data(), (S->k & 1) ? P.act1 : P.act0, 4ull * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(MANTA_E_CUDA, "copy of the active list failed");
+  const size_t NT = (size_t)std::max<int64_t>(S->n_trips, 1);
+  std::vector<float> hx(NT), hv(NT);
+  std::vector<uint32_t> hid(NT), hrc(NT), he(NT), hld(NT);
+  bool ok = cudaMemcpy(hx.data(), P.x, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess &&
+            cudaMemcpy(hv.data(), P.v, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess &&
+            cudaMemcpy(hid.data(), P.id, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess &&
+            cudaMemcpy(hrc.data(), P.rc, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess &&
+            cudaMemcpy(he.data(), P.e, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess &&
+            cudaMemcpy(hld.data(), P.ld, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (!ok) return fail(MANTA_E_CUDA, "copy of vehicle state failed");
+  std::sort(act.begin(), act.end(), [&](uint32_t a, uint32_t b) { return hid[a] < hid[b]; });
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t s = act[i];
+    if (x) x[i] = hx[s];
+    if (v) v[i] = hv[s];
+    if (edge) edge[i] = (int32_t)he[s];
+    if (lane) lane[i] = (uint8_t)(hld[s] & 0xFFu);
+    if (id) id[i] = hid[s];
+    if (dwell) dwell[i] = (uint8_t)((hld[s] >> 8) & 0xFFu);
+    if (route_pos) route_pos[i] = (int32_t)(hrc[s] - S->route_off_h[hid[s]]);
+  }
+  return MANTA_OK;
+}
+
+int64_t manta_lane_map_bytes(const manta_sim *S) { return S ? (int64_t)S->canon_bytes : 0; }
+
+manta_status manta_lane_map(manta_sim *S, uint8_t *out, int64_t cap, int64_t *n_out) {
+  g_err.clear();
+  if (!S || !n_out || !out) return fail(MANTA_E_INVALID, "NULL argument");
+  *n_out = (int64_t)S->canon_bytes;
+  if (cap < (int64_t)S->canon_bytes) return fail(MANTA_E_INVALID, "lane map capacity too small");
+  Ctl c;
+  if (S->loaded) {
+    manta_status st = sync_and_check(S, &c);
+    if (st != MANTA_OK) return st;
+  } else if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
+    return fail(MANTA_E_CUDA, "stream synchronisation failed");
+  }
+  std::vector<uint8_t> buf(S->atlas_bytes);
+  const uint8_t *src = (S->k & 1) ? S->P.atlas1 : S->P.atlas0;
+  if (cudaMemcpy(buf.data(), src, S->atlas_bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(MANTA_E_CUDA, "copy of the lane map failed");
+  uint64_t o = 0;
+  for (int32_t e = 0; e < S->E; ++e)
+    for (uint32_t l = 0; l < S->lanes[e]; ++l) {
+      memcpy(out + o, buf.data() + S->row0[e] + (uint64_t)l * stride16(S->cells[e]), S->cells[e]);
+      o += S->cells[e];
+    }
+  return MANTA_OK;
+}
+
+manta_status manta_selftest_barrier_timeout(int32_t limit_ms, void *cuda_stream) {
+  g_err.clear();
+  if (limit_ms < 1 || limit_ms > 10000) return fail(MANTA_E_INVALID, "limit_ms out of range");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  Ctl *c = nullptr;
+  if (cudaMalloc(&c, sizeof(Ctl)) != cudaSuccess) return fail(MANTA_E_OOM, "selftest allocation failed");
+  cudaMemsetAsync(c, 0, sizeof(Ctl), s);
+  barrier_selftest_kernel<<<2, 32, 0, s>>>(c, (uint64_t)limit_ms * 1000000ull);
+  cudaError_t e = cudaStreamSynchronize(s);
+  Ctl h;
+  memset(&h, 0, sizeof(h));
+  if (e == cudaSuccess) e = cudaMemcpy(&h, c, sizeof(Ctl), cudaMemcpyDeviceToHost);
+  cudaFree(c);
+  if (e != cudaSuccess) return fail(MANTA_E_CUDA, cudaGetErrorString(e));
+  if (h.err == 1) return fail(MANTA_E_TIMEOUT, "barrier wait ran out as expected");
+  return MANTA_OK;
+}
+
+}  // extern "C"

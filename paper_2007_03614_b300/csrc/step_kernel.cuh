@@ -1,0 +1,649 @@
+// step_kernel.cu -- the persistent per-timestep update (sm_103a).
+//
+// One cooperative launch runs n_steps steps.  Per step k the grid goes
+// through four phases separated by grid barriers with bounded waits:
+//   P1  clear last step's cells in the spare map buffer; lane-change decision
+//       on M_k (Section II-D, Eqs. 2-4); stop-sign permits for this step
+//   P2  lane-change apply in place, M_k -> M_k' (skipped when nobody changes)
+//   P3  leader scan along the route on M_k', IDM (Eq. 1), ballistic update,
+//       clamp; write M_{k+1} for vehicles that stay on their edge; crossing
+//       requests; departure requests; arrivals
+//   P4  merge resolution (lowest id wins per target lane), crossings,
+//       departures, arrivals' cells, departure-queue bookkeeping
+// Arithmetic is binary32 with the operation order of the definition; the
+// library is compiled with -fmad=false -prec-div=true -prec-sqrt=true so
+// every operation is one correctly rounded IEEE op.
+#include <stdint.h>
+#include "sim.cuh"
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ldv(const uint32_t *p) { return *(const volatile uint32_t *)p; }
+__device__ __forceinline__ int ldvi(const int *p) { return *(const volatile int *)p; }
+
+// Grid barrier with a bounded wait.  Thread 0 of each block arrives; the last
+// arriver releases the generation word.  A waiter that passes the wall-clock
+// limit sets the sticky error word and the block leaves the kernel.
+__device__ __noinline__ bool grid_sync(Ctl *ctl, uint64_t limit_ns, int *s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned gen = ld_acquire(&ctl->bar_gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      ctl->bar_count = 0u;
+      __threadfence();
+      st_release(&ctl->bar_gen, gen + 1u);
+    } else {
+      const uint64_t t0 = globaltimer();
+      uint32_t spins = 0;
+      while (ld_acquire(&ctl->bar_gen) == gen) {
+        if ((++spins & 63u) == 0u && globaltimer() - t0 > limit_ns) {
+          atomicCAS(&ctl->err, 0, 1);
+          ok = 0;
+          break;
+        }
+        if (spins > 64u) __nanosleep(40);
+      }
+    }
+    __threadfence();
+    if (ldvi(&ctl->err) != 0) ok = 0;
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// ------------------------------------------------------------ random numbers
+// SplitMix64 (Steele, Lea, Flood 2014) of a key from (seed, id, step, stream).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint32_t draw24(uint64_t seed, uint32_t id, int64_t k, uint32_t stream) {
+  const uint64_t key = seed ^ ((uint64_t)id * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)k * 0xC2B2AE3D27D4EB4Full) ^
+                       (uint64_t)stream;
+  return (uint32_t)(splitmix64(key) >> 40);
+}
+// uniform [0,1): 24 bits times 2^-24
+__device__ __forceinline__ float uni(uint64_t seed, uint32_t id, int64_t k, uint32_t stream) {
+  return __uint2float_rn(draw24(seed, id, k, stream)) * 5.9604644775390625e-8f;
+}
+// normal(0,1) approximated by the centred sum of twelve 24-bit uniforms
+__device__ __forceinline__ float irwin_hall(uint64_t seed, uint32_t id, int64_t k, uint32_t s) {
+  int32_t acc = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < 12; ++j) acc += (int32_t)draw24(seed, id, k, 16u * s + j);
+  return __int2float_rn(acc - 100663296) * 5.9604644775390625e-8f;
+}
+
+// ---------------------------------------------------------------- lane map
+__device__ __forceinline__ uint32_t cells_of(uint32_t cnl) { return cnl & 0xFFFFFFu; }
+__device__ __forceinline__ int lanes_of(uint32_t cnl) { return (int)((cnl >> 24) & 0xFu); }
+__device__ __forceinline__ int class_of(uint32_t cnl) { return (int)(cnl >> 28); }
+__device__ __forceinline__ uint32_t stride_of(uint32_t cells) { return (cells + 15u) & ~15u; }
+__device__ __forceinline__ uint8_t speed_code(float v) {
+  const int c = (int)(v * 8.0f + 0.5f);
+  return (uint8_t)(c > 254 ? 254 : c);
+}
+__device__ __forceinline__ float speed_decode(uint32_t c) { return __uint2float_rn(c) * 0.125f; }
+
+// bit 7 of each byte of the result is set iff that byte of w is not 0xFF
+__device__ __forceinline__ uint32_t occupied_bits(uint32_t w) {
+  const uint32_t t = ~w;
+  return (t | ((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu)) & 0x80808080u;
+}
+
+// First occupied cell in row[lo..hi] (inclusive) or -1.  16-byte loads over
+// the 16-byte aligned row; bytes outside [lo, hi] are masked off.
+__device__ __forceinline__ int first_up(const uint8_t *row, int lo, int hi) {
+  if (lo > hi) return -1;
+  for (int c = lo & ~15; c <= hi; c += 16) {
+    const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(row + c));
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int base = c + 4 * j;
+      uint32_t m = occupied_bits(w[j]);
+      if (base < lo) m = (lo - base >= 4) ? 0u : (m & (0xFFFFFFFFu << (8 * (lo - base))));
+      if (base + 3 > hi) m = (base > hi) ? 0u : (m & (0xFFFFFFFFu >> (8 * (base + 3 - hi))));
+      if (m) return base + ((__ffs(m) - 1) >> 3);
+    }
+  }
+  return -1;
+}
+
+// Last occupied cell in row[lo..hi] (scanning downward from hi) or -1.
+__device__ __forceinline__ int first_down(const uint8_t *row, int hi, int lo) {
+  if (lo > hi) return -1;
+  for (int c = hi & ~15; c + 15 >= lo; c -= 16) {
+    const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(row + c));
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 3; j >= 0; --j) {
+      const int base = c + 4 * j;
+      uint32_t m = occupied_bits(w[j]);
+      if (base < lo) m = (lo - base >= 4) ? 0u : (m & (0xFFFFFFFFu << (8 * (lo - base))));
+      if (base + 3 > hi) m = (base > hi) ? 0u : (m & (0xFFFFFFFFu >> (8 * (base + 3 - hi))));
+      if (m) return base + ((31 - __clz(m)) >> 3);
+    }
+    if (c == 0) break;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ uint8_t cell_byte(const uint8_t *row, int c) { return __ldcg(row + c); }
+
+__device__ __forceinline__ EdgeSig load_sig(const Params &p, uint32_t e) {
+  const int2 w = __ldg(reinterpret_cast<const int2 *>(p.es) + e);
+  EdgeSig s;
+  s.cyc = (int16_t)(w.x & 0xFFFF); s.off = (int16_t)((uint32_t)w.x >> 16);
+  s.gs = (int16_t)(w.y & 0xFFFF); s.gl = (int16_t)((uint32_t)w.y >> 16);
+  return s;
+}
+
+__device__ __forceinline__ bool is_green(const EdgeSig &s, int64_t k) {
+  if (s.cyc == 0) return true;
+  int64_t m = (k - (int64_t)s.off) % (int64_t)s.cyc;
+  if (m < 0) m += s.cyc;
+  return m >= s.gs && m < (int64_t)s.gs + s.gl;
+}
+
+// Warp-aggregated append: returns this lane's index in the list.
+__device__ __forceinline__ uint32_t warp_append(uint32_t *counter, bool pred) {
+  const unsigned am = __activemask();
+  const unsigned bal = __ballot_sync(am, pred);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(am) - 1;
+  uint32_t base = 0;
+  if (lane == leader && bal) base = atomicAdd(counter, (uint32_t)__popc(bal));
+  base = __shfl_sync(am, base, leader);
+  return base + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+}
+
+// ------------------------------------------------------------ lane change
+// Target lane or -1 (Section II-D: mandatory vs discretionary; Eq. 2; Eqs. 3-4).
+__device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, uint32_t vid, float x, float v, const EdgeMeta &em,
+                         int lane, uint32_t rc, uint32_t rend, uint64_t &c_lce) {
+  const int nl = lanes_of(em.cnl);
+  if (nl < 2) return -1;
+  const int dir = (k & 1) ? -1 : 1;
+  const int lt = lane + dir;
+  if (lt < 0 || lt >= nl) return -1;
+  const int C = (int)cells_of(em.cnl), L = p.L, H = p.H;
+  const int cell = (int)floorf(x);
+  const bool has_next = rc + 1u < rend;
+  const uint32_t mask = has_next ? (__ldg(p.route + rc) >> MANTA_EDGE_BITS) : 0xFFu;
+  const bool ok_l = (mask >> lane) & 1u, ok_lt = (mask >> lt) & 1u;
+  bool mandatory = false;
+  if (has_next && !ok_l) {
+    int dp = 99, dm = 99;
+    for (int q = lane + 1; q < nl; ++q)
+      if ((mask >> q) & 1u) { dp = q - lane; break; }
+    for (int q = lane - 1; q >= 0; --q)
+      if ((mask >> q) & 1u) { dm = lane - q; break; }
+    const bool toward = dir > 0 ? (dp < 99 && dp <= dm) : (dm < 99 && dm <= dp);
+    if (!toward) return -1;
+    mandatory = true;
+  } else if (!ok_lt) {
+    return -1;
+  }
+  const uint32_t stride = stride_of((uint32_t)C);
+  const uint8_t *trow = cur + em.row0 + (uint32_t)lt * stride;
+  const int hi = min(cell + H, C - 1);
+  if (mandatory) {
+    const float u1 = uni(p.seed, vid, k, 0);
+    if (!(u1 < __ldg(p.mtab + (C - 1 - cell)))) return -1;
+  } else {
+    const uint8_t *orow = cur + em.row0 + (uint32_t)lane * stride;
+    const int co = first_up(orow, cell + 1, hi);
+    if (co < 0) return -1;
+    if (!(speed_decode(cell_byte(orow, co)) < v)) return -1;
+    const int own_gap = co - L - cell;
+    const int ca = first_up(trow, cell + L, hi);
+    if (ca >= 0 && !(ca - L - cell > own_gap)) return -1;
+  }
+  c_lce++;
+  if (first_up(trow, max(0, cell - L + 1), min(C - 1, cell + L - 1)) >= 0) return -1;   // lateral overlap
+  const int ca = first_up(trow, cell + L, hi);
+  const int cb = first_down(trow, cell - L, max(0, cell - H));
+  const float g = v < p.g_split ? p.g_low : p.g_high;
+  const float alpha = p.alpha_lo + (p.alpha_hi - p.alpha_lo) * uni(p.seed, vid, 0, 3);
+  if (ca >= 0) {
+    const float va = speed_decode(cell_byte(trow, ca));
+    const float eps_a = irwin_hall(p.seed, vid, k, 1);
+    float t = g + alpha * v;          // Eq. 3, alpha_a = alpha_i
+    t = t + alpha * (v - va);
+    const float glead = fmaxf(g, t) + eps_a;
+    if (!(__int2float_rn(ca - L - cell) >= glead)) return -1;
+  }
+  if (cb >= 0) {
+    const float vb = speed_decode(cell_byte(trow, cb));
+    const float eps_b = irwin_hall(p.seed, vid, k, 2);
+    float t = g + alpha * v;          // Eq. 4, alpha_b = alpha_i
+    t = t + alpha * (v - vb);
+    const float glag = fmaxf(g, t) + eps_b;
+    if (!(__int2float_rn(cell - L - cb) >= glag)) return -1;
+  }
+  return lt;
+}
+
+// ------------------------------------------------------------ leader scan
+enum { SC_FREE = 0, SC_LEADER = 1, SC_VIRTUAL = 2 };
+struct Scan {
+  int kind;
+  int cL;            // route-relative front cell of the leader
+  float vL;
+  bool reached_own;  // the scan examined the vehicle's own head node
+  bool stop_only;    // ... and only a stop sign (no permit) held it there
+  uint32_t e2;       // next route edge, when read
+};
+
+// Walk the lane map along the route from the cell ahead, at most H cells,
+// stopping at the first occupied byte or at a node that holds the vehicle.
+__device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, uint32_t vid, int cell, uint32_t e,
+                            const EdgeMeta &em0, int lane, uint32_t rc, uint32_t rend, uint64_t &c_scan,
+                            uint64_t &c_rr) {
+  Scan s;
+  s.kind = SC_FREE; s.cL = 0; s.vL = 0.0f; s.reached_own = false; s.stop_only = false; s.e2 = MANTA_NONE;
+  const int limit = cell + p.H;
+  int base = 0, pos = cell + 1, sl = lane;
+  uint32_t r = rc, se = e;
+  EdgeMeta sm = em0;
+  bool own = true;
+  for (;;) {
+    const int segC = (int)cells_of(sm.cnl);
+    const int hi_pos = min(limit, base + segC - 1);
+    if (pos <= hi_pos) {
+      const uint8_t *row = cur + sm.row0 + (uint32_t)sl * stride_of((uint32_t)segC);
+      const int c = first_up(row, pos - base, hi_pos - base);
+      if (c >= 0) {
+        s.kind = SC_LEADER; s.cL = base + c; s.vL = speed_decode(cell_byte(row, c));
+        c_scan += (uint64_t)(s.cL - cell);
+        return s;
+      }
+    }
+    const int B = base + segC;
+    if (B > limit) { c_scan += (uint64_t)p.H; return s; }
+    if (r + 1u >= rend) { c_scan += (uint64_t)(B - 1 - cell); return s; }
+    c_rr++;
+    const uint32_t n = sm.dst;
+    const uint32_t cur_ent = __ldg(p.route + r);
+    const uint32_t e2 = __ldg(p.route + r + 1u) & MANTA_EDGE_MASK;
+    const uint8_t nt = __ldg(p.ntype + n);
+    bool blocked = false;
+    if (nt == 2 && !is_green(load_sig(p, se), k)) blocked = true;
+    if (own) {
+      const bool stop_np = (nt == 1) && (ldv(p.permit + n) != vid);
+      const bool wrong = !(((cur_ent >> MANTA_EDGE_BITS) >> sl) & 1u);
+      s.reached_own = true;
+      s.stop_only = stop_np && !wrong;
+      s.e2 = e2;
+      if (stop_np || wrong) blocked = true;
+    } else if (nt == 1) {
+      blocked = true;
+    }
+    if (blocked) {
+      s.kind = SC_VIRTUAL; s.cL = B + p.L - 1; s.vL = 0.0f;
+      c_scan += (uint64_t)(B - 1 - cell);
+      return s;
+    }
+    ++r; base = B; pos = B; se = e2;
+    sm = p.em[e2];
+    sl = min(sl, lanes_of(sm.cnl) - 1);
+    own = false;
+  }
+}
+
+// ------------------------------------------------------------ the kernel
+__global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
+  __shared__ int s_ok;
+  __shared__ unsigned long long s_cnt[CNT_N];
+  Ctl *ctl = p.ctl;
+  if (threadIdx.x < CNT_N) s_cnt[threadIdx.x] = 0ull;
+  __syncthreads();
+  uint64_t c_upd = 0, c_scan = 0, c_clamp = 0, c_lc = 0, c_lce = 0, c_rr = 0, c_dep = 0, c_arr = 0;
+  const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t gsz = gridDim.x * blockDim.x;
+  const int L = p.L;
+  bool alive = ldvi(&ctl->err) == 0;
+  for (int it = 0; it < p.n_steps && alive; ++it) {
+    const int64_t k = p.k0 + it;
+    const int cb = (int)(k & 1);
+    uint8_t *cur = cb ? p.atlas1 : p.atlas0;
+    uint8_t *nxt = cb ? p.atlas0 : p.atlas1;
+    uint32_t *act = cb ? p.act1 : p.act0;
+    uint32_t *act_n = cb ? p.act0 : p.act1;
+    uint32_t *dep = cb ? p.dep1 : p.dep0;
+    uint32_t *dep_n = cb ? p.dep0 : p.dep1;
+    const uint32_t nact = ldv(&ctl->n_act[cb]);
+    // ================================================================ P1
+    if (gtid == 0) {
+      ctl->due_pos = ctl->due_next;
+      ctl->n_req = 0u;
+      ctl->n_arr = 0u;
+      ctl->n_act[cb ^ 1] = 0u;
+      ctl->n_dep[cb ^ 1] = 0u;
+      const uint32_t fc = ctl->free_count, w = ctl->n_depwin;
+      if (w <= fc) ctl->free_count = fc - w;
+      else { ctl->n_slots += w - fc; ctl->free_count = 0u; }
+      ctl->n_depwin = 0u;
+    }
+    for (uint32_t i = gtid; i < nact; i += gsz) {
+      const uint32_t s = __ldcg(act + i);
+      const uint32_t pc = __ldcg(p.pcell + s);
+      if (pc != MANTA_NONE) nxt[pc] = (uint8_t)MANTA_EMPTY;
+      const uint32_t e = __ldcg(p.e + s);
+      const EdgeMeta em = p.em[e];
+      int tgt = -1;
+      if (lanes_of(em.cnl) >= 2) {
+        const uint32_t ldw = __ldcg(p.ld + s);
+        tgt = lc_decide(p, cur, k, __ldcg(p.id + s), __ldcg(p.x + s), __ldcg(p.v + s), em, (int)(ldw & 0xFFu),
+                        __ldcg(p.rc + s), __ldcg(p.rend + s), c_lce);
+        if (tgt >= 0) p.ld[s] = (ldw & 0xFFFFu) | ((uint32_t)tgt << 16);
+      }
+      const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
+      if (tgt >= 0) p.chg[at] = s;
+    }
+    for (uint32_t j = gtid; j < p.n_stop; j += gsz) {
+      const uint32_t n = __ldg(p.stop_nodes + j);
+      if (ldv(p.permit + n) != MANTA_NONE) continue;
+      const uint32_t o = __ldg(p.nin_off + n), m = __ldg(p.nin_off + n + 1) - o;
+      const uint32_t r0 = ldv(p.rr + n);
+      for (uint32_t t = 0; t < m; ++t) {
+        const uint32_t idx = (r0 + t) % m;
+        const uint32_t g = __ldg(p.nin + o + idx);
+        const uint32_t td = ldv(p.slot_td + g);
+        if ((td >> 8) == (uint32_t)(k & 0xFFFFFF) && (td & 0xFFu) >= (uint32_t)p.stop_dwell) {
+          p.permit[n] = ldv(p.slot_id + g);
+          p.rr[n] = (idx + 1u) % m;
+          break;
+        }
+      }
+    }
+    if (!grid_sync(ctl, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+    // ================================================================ P2
+    const uint32_t nchg = ldv(&ctl->n_chg);
+    if (nchg) {
+      for (uint32_t i = gtid; i < nchg; i += gsz) {
+        const uint32_t s = __ldcg(p.chg + i);
+        const uint32_t e = __ldcg(p.e + s), ldw = __ldcg(p.ld + s);
+        const EdgeMeta em = p.em[e];
+        const uint32_t stride = stride_of(cells_of(em.cnl));
+        const uint32_t cell = (uint32_t)(int)floorf(__ldcg(p.x + s));
+        const uint32_t lo = ldw & 0xFFu, ln = (ldw >> 16) & 0xFFu;
+        const uint32_t a = em.row0 + lo * stride + cell, b = em.row0 + ln * stride + cell;
+        cur[b] = cur[a];
+        cur[a] = (uint8_t)MANTA_EMPTY;
+        p.ld[s] = (ldw & 0xFF00u) | ln;
+        c_lc++;
+      }
+      if (!grid_sync(ctl, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+    }
+    // ================================================================ P3
+    if (gtid == 0) ctl->n_chg = 0u;
+    const uint32_t tag = (uint32_t)(k + 1);
+    // departure requests on M_k'
+    const uint32_t ndep = ldv(&ctl->n_dep[cb]);
+    for (uint32_t i = gtid; i < ndep; i += gsz) {
+      const uint32_t e = __ldcg(dep + i);
+      const EdgeMeta em = p.em[e];
+      const int C = (int)cells_of(em.cnl);
+      const int need = min(C, L + p.s0c[class_of(em.cnl)]);
+      if (first_up(cur + em.row0, 0, need - 1) >= 0) continue;
+      const uint32_t j = __ldg(p.q_trip + __ldg(p.q_off + e) + __ldcg(p.q_pos + e));
+      p.dep_key[e] = ((unsigned long long)tag << 32) | j;
+    }
+    // vehicles
+    const int64_t wk = k - p.t0;
+    const int win = (wk >= 0 && wk / p.win_steps < p.n_win) ? (int)(wk / p.win_steps) : -1;
+    for (uint32_t i = gtid; i < nact; i += gsz) {
+      const uint32_t s = __ldcg(act + i);
+      const float x = __ldcg(p.x + s), v = __ldcg(p.v + s);
+      const uint32_t vid = __ldcg(p.id + s), rc = __ldcg(p.rc + s), rend = __ldcg(p.rend + s);
+      const uint32_t e = __ldcg(p.e + s), ldw = __ldcg(p.ld + s);
+      const int lane = (int)(ldw & 0xFFu);
+      const uint32_t dwell = (ldw >> 8) & 0xFFu;
+      const EdgeMeta em = p.em[e];
+      const int C = (int)cells_of(em.cnl);
+      const int cls = class_of(em.cnl);
+      const uint32_t stride = stride_of((uint32_t)C);
+      const int cell = (int)floorf(x);
+      const uint32_t gcell = em.row0 + (uint32_t)lane * stride + (uint32_t)cell;
+      const Scan sc = leader_scan(p, cur, k, vid, cell, e, em, lane, rc, rend, c_scan, c_rr);
+      const float a = p.a[cls], b = p.b[cls], T = p.T[cls], s0 = p.s0[cls];
+      const float v0 = em.lim * p.v0f[cls];
+      const float r1 = v / v0, r2 = r1 * r1, r4 = r2 * r2;
+      const bool has_next = rc + 1u < rend;
+      float xn, vn;
+      bool stop_in_place = false;
+      float acc = 0.0f;
+      if (sc.kind == SC_FREE) {
+        acc = a * (1.0f - r4);
+      } else {
+        const float sg = __int2float_rn(sc.cL - cell - L);
+        if (sg <= 0.0f) {
+          stop_in_place = true;
+        } else {
+          const float dv = v - sc.vL;
+          const float dyn = (v * dv) / (2.0f * sqrtf(a * b));
+          float ss;
+          if (p.textbook) ss = s0 + fmaxf(0.0f, v * T + dyn);
+          else ss = (s0 + v * T) + dyn;
+          const float q = ss / sg;
+          acc = a * ((1.0f - r4) - q * q);
+        }
+      }
+      if (stop_in_place) {
+        xn = x; vn = 0.0f;
+      } else {
+        const float dt = p.dt;
+        const float vt = v + acc * dt;
+        float xt, vv;
+        if (vt >= 0.0f) { xt = x + (v * dt + (0.5f * acc) * (dt * dt)); vv = vt; }
+        else { xt = x - (v * v) / (2.0f * acc); vv = 0.0f; }
+        bool has_bound = sc.kind != SC_FREE;
+        int bnd = sc.cL - L;
+        if (has_next && xt >= __int2float_rn(C)) {
+          // at most one node per step: stay within the next edge
+          uint32_t e2 = sc.e2;
+          if (e2 == MANTA_NONE) e2 = __ldg(p.route + rc + 1u) & MANTA_EDGE_MASK;
+          const int cap = C + (int)cells_of(p.em[e2].cnl) - 1;
+          if (!has_bound || cap < bnd) { has_bound = true; bnd = cap; }
+        }
+        if (has_bound && xt > __int2float_rn(bnd)) { xn = fmaxf(x, __int2float_rn(bnd)); vn = 0.0f; c_clamp++; }
+        else { xn = xt; vn = vv; }
+      }
+      uint32_t dwn = 0;
+      if (has_next && sc.reached_own && sc.stop_only) {
+        const int zone = C - 1 - (p.s0c[cls] + 2);
+        if ((int)floorf(xn) >= zone && vn < p.stop_eps) dwn = dwell < 255u ? dwell + 1u : 255u;
+      }
+      if (has_next && sc.reached_own && __ldg(p.ntype + em.dst) == 1) {
+        const uint32_t g = __ldg(p.lane_base + e) + (uint32_t)lane;
+        p.slot_id[g] = vid;
+        p.slot_td[g] = ((uint32_t)(tag & 0xFFFFFF) << 8) | dwn;
+      }
+      c_upd++;
+      const bool crossing = xn >= __int2float_rn(C);
+      const bool arrive = crossing && !has_next;
+      const bool request = crossing && has_next;
+      if (arrive) {
+        atomicAdd(p.exitc + e, 1u);
+        c_arr++;
+      } else if (request) {
+        const uint32_t e2 = sc.e2 != MANTA_NONE ? sc.e2 : (__ldg(p.route + rc + 1u) & MANTA_EDGE_MASK);
+        const int l2 = min(lane, lanes_of(p.em[e2].cnl) - 1);
+        const uint32_t g = __ldg(p.lane_base + e) + (uint32_t)lane;
+        p.req_tgt[g] = __ldg(p.lane_base + e2) + (uint32_t)l2;
+        p.req_key[g] = ((unsigned long long)tag << 32) | vid;
+      } else {
+        p.x[s] = xn; p.v[s] = vn;
+        p.ld[s] = (uint32_t)lane | (dwn << 8);
+        p.pcell[s] = gcell;
+        nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xn)] = speed_code(vn);
+        if (win >= 0) {
+          const size_t o = (size_t)win * p.E + e;
+          atomicAdd(p.ssum + o, (unsigned long long)(vn * 1048576.0f));
+          atomicAdd(p.scnt + o, 1u);
+        }
+      }
+      const uint32_t ia = warp_append(&ctl->n_arr, arrive);
+      if (arrive) {
+        p.arr[ia] = gcell;
+        p.freel[atomicAdd(&ctl->free_count, 1u)] = s;
+      }
+      const uint32_t iq = warp_append(&ctl->n_req, request);
+      if (request) { p.req[iq] = s; p.req_x[iq] = xn; p.req_v[iq] = vn; p.req_dw[iq] = dwn; }
+      const uint32_t in = warp_append(&ctl->n_act[cb ^ 1], !arrive && !request);
+      if (!arrive && !request) act_n[in] = s;
+    }
+    if (!grid_sync(ctl, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+    // ================================================================ P4
+    // crossing requests: the lowest id among requests for the same target lane wins
+    const uint32_t nreq = ldv(&ctl->n_req);
+    for (uint32_t i = gtid; i < nreq; i += gsz) {
+      const uint32_t s = __ldcg(p.req + i);
+      const uint32_t vid = __ldcg(p.id + s), e = __ldcg(p.e + s), ldw = __ldcg(p.ld + s);
+      const int lane = (int)(ldw & 0xFFu);
+      const EdgeMeta em = p.em[e];
+      const uint32_t stride = stride_of(cells_of(em.cnl));
+      const uint32_t gown = __ldg(p.lane_base + e) + (uint32_t)lane;
+      const uint32_t tgt = __ldcg(p.req_tgt + gown);
+      const uint32_t n = em.dst;
+      bool win_it = true;
+      const uint32_t o0 = __ldg(p.nin_off + n), o1 = __ldg(p.nin_off + n + 1);
+      for (uint32_t o = o0; o < o1 && win_it; ++o) {
+        const uint32_t g = __ldg(p.nin + o);
+        if (g == gown) continue;
+        const unsigned long long key = __ldcg(p.req_key + g);
+        if ((uint32_t)(key >> 32) == tag && __ldcg(p.req_tgt + g) == tgt && (uint32_t)key < vid) win_it = false;
+      }
+      const uint32_t rc = __ldcg(p.rc + s);
+      const uint32_t e2 = __ldg(p.route + rc + 1u) & MANTA_EDGE_MASK;
+      const uint32_t lb2 = __ldg(p.lane_base + e2);
+      if (win_it && tgt == lb2) {
+        const unsigned long long dk = __ldcg(p.dep_key + e2);
+        if ((uint32_t)(dk >> 32) == tag && (uint32_t)dk < vid) win_it = false;
+      }
+      const float x = __ldcg(p.x + s);
+      const uint32_t cell = (uint32_t)(int)floorf(x);
+      p.pcell[s] = em.row0 + (uint32_t)lane * stride + cell;
+      float xf, vf;
+      uint32_t ef;
+      if (win_it) {
+        const int C = (int)cells_of(em.cnl);
+        if (__ldg(p.ntype + n) == 1 && ldv(p.permit + n) == vid) p.permit[n] = MANTA_NONE;
+        atomicAdd(p.exitc + e, 1u);
+        atomicAdd(p.entry + e2, 1u);
+        xf = __ldcg(p.req_x + i) - __int2float_rn(C);
+        vf = __ldcg(p.req_v + i);
+        const EdgeMeta em2 = p.em[e2];
+        const uint32_t l2 = tgt - lb2;
+        p.e[s] = e2; p.rc[s] = rc + 1u;
+        p.ld[s] = l2;
+        nxt[em2.row0 + l2 * stride_of(cells_of(em2.cnl)) + (uint32_t)(int)floorf(xf)] = speed_code(vf);
+        ef = e2;
+      } else {
+        const int C = (int)cells_of(em.cnl);
+        xf = fmaxf(x, __int2float_rn(C - 1));
+        vf = 0.0f;
+        p.ld[s] = (uint32_t)lane | (__ldcg(p.req_dw + i) << 8);
+        nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xf)] = speed_code(vf);
+        ef = e;
+      }
+      p.x[s] = xf; p.v[s] = vf;
+      if (win >= 0) {
+        const size_t o = (size_t)win * p.E + ef;
+        atomicAdd(p.ssum + o, (unsigned long long)(vf * 1048576.0f));
+        atomicAdd(p.scnt + o, 1u);
+      }
+      const uint32_t in = warp_append(&ctl->n_act[cb ^ 1], true);
+      act_n[in] = s;
+    }
+    // departures: the queue head wins unless a crossing with a lower id targets lane 0
+    for (uint32_t i = gtid; i < ndep; i += gsz) {
+      const uint32_t e = __ldcg(dep + i);
+      const unsigned long long dk = __ldcg(p.dep_key + e);
+      const uint32_t j = (uint32_t)dk;
+      bool won = (uint32_t)(dk >> 32) == tag;
+      if (won) {
+        const uint32_t lb = __ldg(p.lane_base + e);
+        const uint32_t n = __ldg(p.esrc + e);
+        const uint32_t o0 = __ldg(p.nin_off + n), o1 = __ldg(p.nin_off + n + 1);
+        for (uint32_t o = o0; o < o1; ++o) {
+          const uint32_t g = __ldg(p.nin + o);
+          const unsigned long long key = __ldcg(p.req_key + g);
+          if ((uint32_t)(key >> 32) == tag && __ldcg(p.req_tgt + g) == lb && (uint32_t)key < j) { won = false; break; }
+        }
+      }
+      uint32_t s = MANTA_NONE;
+      bool keep = true;
+      if (won) {
+        const uint32_t wi = atomicAdd(&ctl->n_depwin, 1u);
+        const uint32_t fc = ldv(&ctl->free_count);
+        s = wi < fc ? __ldcg(p.freel + (fc - 1u - wi)) : ldv(&ctl->n_slots) + (wi - fc);
+        const uint32_t r0 = __ldg(p.route_off + j);
+        p.x[s] = 0.0f; p.v[s] = 0.0f; p.id[s] = j; p.rc[s] = r0; p.rend[s] = __ldg(p.route_off + j + 1u);
+        p.e[s] = e; p.ld[s] = 0u; p.pcell[s] = MANTA_NONE;
+        nxt[p.em[e].row0] = speed_code(0.0f);
+        atomicAdd(p.entry + e, 1u);
+        c_dep++;
+        p.q_pos[e] = __ldcg(p.q_pos + e) + 1u;
+        keep = atomicSub(p.pending + e, 1u) > 1u;
+      }
+      const uint32_t ia = warp_append(&ctl->n_act[cb ^ 1], won);
+      if (won) act_n[ia] = s;
+      const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], keep);
+      if (keep) dep_n[id2] = e;
+    }
+    // arrivals leave the current map
+    const uint32_t narr = ldv(&ctl->n_arr);
+    for (uint32_t i = gtid; i < narr; i += gsz) cur[__ldcg(p.arr + i)] = (uint8_t)MANTA_EMPTY;
+    // trips due at step k + 1 join their edge's departure queue
+    {
+      const uint32_t lo = ldv(&ctl->due_pos);
+      uint32_t a = lo, b = p.n_trips;
+      while (a < b) {
+        const uint32_t m = (a + b) >> 1;
+        if ((int64_t)__ldg(p.due_step + m) <= k + 1) a = m + 1u; else b = m;
+      }
+      if (gtid == 0) ctl->due_next = a;
+      for (uint32_t i = lo + gtid; i < a; i += gsz) {
+        const uint32_t e = __ldg(p.due_edge + i);
+        const bool first = atomicAdd(p.pending + e, 1u) == 0u;
+        const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], first);
+        if (first) dep_n[id2] = e;
+      }
+    }
+    if (!grid_sync(ctl, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+  }
+  // flush counters
+  atomicAdd(&s_cnt[CNT_UPD], (unsigned long long)c_upd);
+  atomicAdd(&s_cnt[CNT_SCAN], (unsigned long long)c_scan);
+  atomicAdd(&s_cnt[CNT_CLAMP], (unsigned long long)c_clamp);
+  atomicAdd(&s_cnt[CNT_LC], (unsigned long long)c_lc);
+  atomicAdd(&s_cnt[CNT_LCE], (unsigned long long)c_lce);
+  atomicAdd(&s_cnt[CNT_RR], (unsigned long long)c_rr);
+  atomicAdd(&s_cnt[CNT_DEP], (unsigned long long)c_dep);
+  atomicAdd(&s_cnt[CNT_ARR], (unsigned long long)c_arr);
+  __syncthreads();
+  if (threadIdx.x < CNT_N && s_cnt[threadIdx.x]) atomicAdd(&ctl->cnt[threadIdx.x], s_cnt[threadIdx.x]);
+}
+

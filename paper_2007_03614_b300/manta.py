@@ -1,0 +1,207 @@
+"""Python binding of libmanta.so (argument marshalling only).
+
+Every step of the simulation runs in the library's CUDA kernels; this module
+only converts numpy arrays to pointers and statuses to exceptions.  It raises
+if the native library is missing -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmanta.so")
+
+OK, E_INVALID, E_ROUTE, E_STATE, E_OOM, E_CUDA, E_TIMEOUT, E_DEVICE = 0, -1, -2, -3, -4, -5, -6, -7
+NODE_GREEN, NODE_STOP, NODE_SIGNAL = 0, 1, 2
+
+
+class MantaConfig(C.Structure):
+    _fields_ = [("dt", C.c_float), ("cell_m", C.c_float),
+                ("veh_len_cells", C.c_int32), ("horizon_cells", C.c_int32), ("n_classes", C.c_int32),
+                ("v0f", C.c_float * 8), ("T", C.c_float * 8), ("a", C.c_float * 8),
+                ("b", C.c_float * 8), ("s0", C.c_float * 8),
+                ("lc_x0_m", C.c_float), ("lc_len_scale_m", C.c_float),
+                ("alpha_lo", C.c_float), ("alpha_hi", C.c_float),
+                ("g_low", C.c_float), ("g_high", C.c_float), ("g_speed_split", C.c_float),
+                ("stop_dwell_steps", C.c_int32), ("stop_v_eps", C.c_float),
+                ("stats_window_steps", C.c_int32), ("n_stats_windows", C.c_int32),
+                ("idm_textbook", C.c_int32),
+                ("t0_step", C.c_int64), ("seed", C.c_uint64)]
+
+
+class MantaStats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("loaded", C.c_int64), ("departed", C.c_int64),
+                ("arrived", C.c_int64), ("on_network", C.c_int64), ("waiting", C.c_int64),
+                ("vehicle_updates", C.c_uint64), ("cells_scanned", C.c_uint64),
+                ("clamps", C.c_uint64), ("lane_changes", C.c_uint64),
+                ("lc_evals", C.c_uint64), ("route_reads", C.c_uint64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+# Every entry point declared in include/manta.h.
+EXPORTS = ("manta_default_config", "manta_create", "manta_load_trips", "manta_step", "manta_stats",
+           "manta_edge_counters", "manta_snapshot", "manta_lane_map", "manta_lane_map_bytes",
+           "manta_destroy", "manta_last_error", "manta_selftest_barrier_timeout")
+
+_lib = None
+
+
+class MantaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"manta status {status}: {msg}")
+        self.status = status
+
+
+def load_library():
+    """Load libmanta.so (build it first with paper_2007_03614_b300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2007_03614_b300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        lib.manta_default_config.argtypes = [C.POINTER(MantaConfig)]
+        lib.manta_create.restype = C.c_int
+        lib.manta_create.argtypes = [C.c_int32, C.c_int32] + [P] * 12 + [C.POINTER(MantaConfig), P, C.POINTER(P)]
+        lib.manta_load_trips.restype = C.c_int
+        lib.manta_load_trips.argtypes = [P, C.c_int64, P, P, P]
+        lib.manta_step.restype = C.c_int
+        lib.manta_step.argtypes = [P, C.c_int64]
+        lib.manta_stats.restype = C.c_int
+        lib.manta_stats.argtypes = [P, C.POINTER(MantaStats)]
+        lib.manta_edge_counters.restype = C.c_int
+        lib.manta_edge_counters.argtypes = [P, P, P, P, P, C.c_int32]
+        lib.manta_snapshot.restype = C.c_int
+        lib.manta_snapshot.argtypes = [P, C.c_int64, C.POINTER(C.c_int64), P, P, P, P, P, P, P]
+        lib.manta_lane_map.restype = C.c_int
+        lib.manta_lane_map.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
+        lib.manta_lane_map_bytes.restype = C.c_int64
+        lib.manta_lane_map_bytes.argtypes = [P]
+        lib.manta_destroy.argtypes = [P]
+        lib.manta_last_error.restype = C.c_char_p
+        lib.manta_selftest_barrier_timeout.restype = C.c_int
+        lib.manta_selftest_barrier_timeout.argtypes = [C.c_int32, P]
+        _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise MantaError(rc, _lib.manta_last_error().decode())
+
+
+def default_config(**over) -> MantaConfig:
+    lib = load_library()
+    c = MantaConfig()
+    lib.manta_default_config(C.byref(c))
+    for k, v in over.items():
+        if isinstance(v, (list, tuple, np.ndarray)):
+            arr = getattr(c, k)
+            for i in range(8):
+                arr[i] = float(v[i]) if i < len(v) else float(v[-1])
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)     # torch.cuda.Stream
+
+
+class Sim:
+    """One simulation on the current CUDA device (see include/manta.h)."""
+
+    def __init__(self, net, stream=None, **cfg):
+        lib = load_library()
+        self._lib = lib
+        self.cfg = default_config(**cfg)
+        keep = []
+
+        def arr(a, dt):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(a, dtype=dt))
+            keep.append(a)
+            return a
+
+        self.n_edges = int(len(net.edge_src))
+        self.n_nodes = int(len(net.node_type))
+        h = C.c_void_p()
+        rc = lib.manta_create(self.n_nodes, self.n_edges,
+                              _p(arr(net.edge_src, np.int32)), _p(arr(net.edge_dst, np.int32)),
+                              _p(arr(net.edge_lanes, np.uint8)), _p(arr(net.edge_length_m, np.float32)),
+                              _p(arr(net.edge_speed_limit_mps, np.float32)), _p(arr(net.edge_class, np.uint8)),
+                              _p(arr(net.node_type, np.uint8)), _p(arr(net.node_cycle_steps, np.int32)),
+                              _p(arr(net.node_offset_steps, np.int32)), _p(arr(net.edge_green_start, np.int16)),
+                              _p(arr(net.edge_green_len, np.int16)), _p(arr(net.conn_lane_mask, np.uint32)),
+                              C.byref(self.cfg), _stream_handle(stream), C.byref(h))
+        _check(rc)
+        self._h = h
+        self.n_trips = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.manta_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def load_trips(self, route_off, route_edges, depart_time_s):
+        ro = np.ascontiguousarray(route_off, dtype=np.int64)
+        re = np.ascontiguousarray(route_edges, dtype=np.int32)
+        dt = np.ascontiguousarray(depart_time_s, dtype=np.float32)
+        _check(self._lib.manta_load_trips(self._h, len(dt), _p(ro), _p(re), _p(dt)))
+        self.n_trips = len(dt)
+
+    def step(self, n=1):
+        _check(self._lib.manta_step(self._h, int(n)))
+
+    def stats(self) -> dict:
+        s = MantaStats()
+        _check(self._lib.manta_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def edge_counters(self, window=0) -> dict:
+        E = self.n_edges
+        out = dict(entries=np.zeros(E, np.uint32), exits=np.zeros(E, np.uint32),
+                   speed_sum=np.zeros(E, np.uint64), speed_cnt=np.zeros(E, np.uint32))
+        _check(self._lib.manta_edge_counters(self._h, _p(out["entries"]), _p(out["exits"]),
+                                             _p(out["speed_sum"]), _p(out["speed_cnt"]), int(window)))
+        return out
+
+    def snapshot(self) -> dict:
+        n = max(self.n_trips, 1)
+        out = dict(x=np.zeros(n, np.float32), v=np.zeros(n, np.float32), edge=np.zeros(n, np.int32),
+                   lane=np.zeros(n, np.uint8), id=np.zeros(n, np.uint32), dwell=np.zeros(n, np.uint8),
+                   route_pos=np.zeros(n, np.int32))
+        cnt = C.c_int64()
+        _check(self._lib.manta_snapshot(self._h, n, C.byref(cnt), *[_p(out[k]) for k in
+                                                                   ("x", "v", "edge", "lane", "id", "dwell",
+                                                                    "route_pos")]))
+        return {k: a[:cnt.value] for k, a in out.items()}
+
+    def lane_map(self) -> np.ndarray:
+        nb = int(self._lib.manta_lane_map_bytes(self._h))
+        buf = np.zeros(max(nb, 1), np.uint8)
+        cnt = C.c_int64()
+        _check(self._lib.manta_lane_map(self._h, _p(buf), buf.size, C.byref(cnt)))
+        return buf[:cnt.value]
+
+
+def selftest_barrier_timeout(limit_ms=100, stream=None) -> int:
+    """Runs the bounded-wait self test; returns the status (E_TIMEOUT expected)."""
+    lib = load_library()
+    return int(lib.manta_selftest_barrier_timeout(int(limit_ms), _stream_handle(stream)))

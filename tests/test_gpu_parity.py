@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA library against the CPU oracle, through the C ABI.
+
+Bar: bit-exact (validation = product build, -fmad=false): trajectories
+(x, v as binary32 bit patterns, edge, lane, dwell, route position, id),
+scalar counters, per-edge entry/exit counts, per-edge speed sums and the lane
+map itself.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import nets
+from oracle import oracle as O
+from paper_2007_03614_b300 import manta, synth
+from paper_2007_03614_b300.build import build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build()
+    manta.load_library()
+
+
+def _compare(o, g, where=""):
+    a, b = o.snapshot(), g.snapshot()
+    assert len(a["id"]) == len(b["id"]), (where, len(a["id"]), len(b["id"]))
+    for key in ("id", "edge", "lane", "dwell", "route_pos"):
+        if not np.array_equal(a[key], b[key]):
+            i = int(np.nonzero(a[key] != b[key])[0][0])
+            raise AssertionError(f"{where}: {key} differs first at vehicle {a['id'][i]}: {a[key][i]} vs {b[key][i]}")
+    for key in ("x", "v"):
+        ua, ub = a[key].view(np.uint32), b[key].view(np.uint32)
+        if not np.array_equal(ua, ub):
+            i = int(np.nonzero(ua != ub)[0][0])
+            raise AssertionError(f"{where}: {key} differs first at vehicle {a['id'][i]}: {a[key][i]!r} vs {b[key][i]!r}")
+
+
+def _compare_all(o, g, windows=(0,), where=""):
+    _compare(o, g, where)
+    so, sg = o.stats(), g.stats()
+    for key in so:
+        assert so[key] == sg[key], (where, key, so[key], sg[key])
+    assert np.array_equal(o.lane_map(), g.lane_map()), where
+    for w in windows:
+        eo, eg = o.edge_counters(w), g.edge_counters(w)
+        for key in eo:
+            assert np.array_equal(eo[key], eg[key]), (where, w, key)
+
+
+def _pair(net, tr, **cfg):
+    o = O.OracleSim(net, **cfg)
+    g = manta.Sim(net, **cfg)
+    nets.load(o, tr)
+    nets.load(g, tr)
+    return o, g
+
+
+def test_tiny_workload_bit_exact():
+    """10x10 grid, 2 lanes, fixed-time signals, 1,000 trips over 10 min, 30 min simulated."""
+    net = synth.tiny_network()
+    tr = synth.tiny_trips(net)
+    o, g = _pair(net, tr)
+    for k in range(0, 3600, 25):
+        o.step(25)
+        g.step(25)
+        _compare(o, g, f"step {k + 25}")
+        if (k + 25) % 600 == 0:
+            _compare_all(o, g, windows=range(6), where=f"step {k + 25}")
+    st = g.stats()
+    assert st["arrived"] == 1000 and st["on_network"] == 0
+
+
+def test_tiny_all_stop_signs_bit_exact():
+    """Red-light case of Section IV-C: every node a flashing red (stop + permit)."""
+    net = synth.lattice(10, 10, arterial_every=1, len_median_m=100.0, len_sigma=0.0, len_min_m=100.0,
+                        len_max_m=100.0, speed_mps=(13.889,) * 3, lanes=(2, 2, 2), all_stop=True)
+    tr = synth.tiny_trips(net)
+    o, g = _pair(net, tr)
+    for k in range(0, 2400, 50):
+        o.step(50)
+        g.step(50)
+        _compare(o, g, f"step {k + 50}")
+    _compare_all(o, g, windows=range(4))
+    assert g.stats()["arrived"] > 0
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+@pytest.mark.parametrize("ci", [0, 1, 2])
+def test_small_mixed_networks_every_step(seed, ci):
+    """Random-walk routes on a 3x3 lattice with stop, signal and green nodes:
+    every step compared (merges, queues, permits, lane changes)."""
+    from test_oracle_bruteforce import CFGS, _scenario
+    net, tr = _scenario(seed, n_trips=40)
+    cfg = dict(CFGS[ci])
+    cfg["seed"] = 100 + seed
+    o, g = _pair(net, tr, **cfg)
+    for k in range(600):
+        o.step(1)
+        g.step(1)
+        _compare(o, g, f"seed {seed} cfg {ci} step {k}")
+    _compare_all(o, g)
+
+
+def test_edge_cases():
+    # no trips at all
+    net = nets.line(3)
+    o, g = _pair(net, nets.trips([], []))
+    o.step(10)
+    g.step(10)
+    _compare_all(o, g)
+    # single-edge routes, departures beyond the run, a trip due before t0, many trips on one edge
+    net = nets.line(2, length=60.0, lanes=2)
+    routes = [[0]] * 30 + [[0, 1]] * 30 + [[1]] * 5
+    times = list(np.linspace(-50.0, 40.0, 30)) + list(np.linspace(0.0, 20.0, 30)) + [1e6] * 5
+    tr = nets.trips(routes, times)
+    o, g = _pair(net, tr, t0_step=10)
+    for k in range(300):
+        o.step(1)
+        g.step(1)
+        _compare(o, g, f"step {k}")
+    _compare_all(o, g)
+    # zero steps is a no-op
+    g.step(0)
+    _compare_all(o, g)
+
+
+def test_error_statuses():
+    net = nets.line(2)
+    g = manta.Sim(net)
+    with pytest.raises(manta.MantaError) as ei:
+        g.step(1)                                   # no trips yet
+    assert ei.value.status == manta.E_STATE
+    with pytest.raises(manta.MantaError) as ei:
+        g.load_trips(np.array([0, 2], np.int64), np.array([1, 0], np.int32), np.array([0.0], np.float32))
+    assert ei.value.status == manta.E_ROUTE       # 1 -> 0 is not contiguous
+    with pytest.raises(manta.MantaError) as ei:
+        g.load_trips(np.array([0, 0], np.int64), np.zeros(0, np.int32), np.array([0.0], np.float32))
+    assert ei.value.status == manta.E_ROUTE       # empty route
+    g.load_trips(np.array([0, 2], np.int64), np.array([0, 1], np.int32), np.array([0.0], np.float32))
+    with pytest.raises(manta.MantaError) as ei:
+        g.load_trips(np.array([0, 2], np.int64), np.array([0, 1], np.int32), np.array([0.0], np.float32))
+    assert ei.value.status == manta.E_STATE
+    g.step(100)
+    assert g.stats()["arrived"] == 1
+
+
+def test_barrier_wait_runs_out_and_context_survives():
+    """A grid barrier whose last block never arrives: every waiter gives up
+    after ~0.1 s and returns MANTA_E_TIMEOUT; the context keeps working."""
+    assert manta.selftest_barrier_timeout(100) == manta.E_TIMEOUT
+    net = nets.line(2)
+    tr = nets.trips([[0, 1]], [0.0])
+    o, g = _pair(net, tr)
+    o.step(50)
+    g.step(50)
+    _compare_all(o, g)
+
+
+# ------------------------------------------------------------------ metro --
+@pytest.fixture(scope="module")
+def metro():
+    net = synth.metro_network()
+    tr = synth.metro_trips(net)
+    return net, tr
+
+
+def _subset(tr, lo_s, hi_s):
+    sel = np.nonzero((tr.depart_time_s >= lo_s) & (tr.depart_time_s < hi_s))[0]
+    routes = [tr.route_edges[tr.route_off[i]:tr.route_off[i + 1]] for i in sel]
+    off = np.zeros(len(sel) + 1, np.int64)
+    off[1:] = np.cumsum([len(r) for r in routes])
+    return synth.Trips(route_off=off, route_edges=np.concatenate(routes).astype(np.int32),
+                       depart_time_s=tr.depart_time_s[sel])
+
+
+def test_metro_network_window_bit_exact(metro):
+    """Full metro-shaped network (~550k edges), the trips departing 07:30-07:35,
+    600 steps from an empty network at 07:30: bit-exact at checkpoints."""
+    net, tr = metro
+    sub = _subset(tr, 7.5 * 3600, 7.5 * 3600 + 300)
+    assert sub.n_trips > 20000
+    t0 = int(7.5 * 3600 / 0.5)
+    o, g = _pair(net, sub, t0_step=t0, n_stats_windows=4)
+    for k in range(0, 600, 100):
+        o.step(100)
+        g.step(100)
+        _compare(o, g, f"metro step {k + 100}")
+    _compare_all(o, g, windows=(0,))
+    assert g.stats()["on_network"] > 10000
+
+
+def test_metro_full_morning_properties(metro):
+    """The full 3.2M-trip table at the size the benchmark runs: conservation,
+    lane-map occupancy equal to the on-network count, and fronts at least L
+    apart in every lane, after 3 simulated hours from 05:00."""
+    net, tr = metro
+    g = manta.Sim(net, t0_step=36000)
+    nets.load(g, tr)
+    g.step(21600)
+    st = g.stats()
+    assert st["departed"] == st["arrived"] + st["on_network"]
+    assert st["loaded"] == st["departed"] + st["waiting"]
+    m = g.lane_map()
+    occ = np.nonzero(m != 0xFF)[0]
+    assert len(occ) == st["on_network"]
+    ec = g.edge_counters(0)
+    assert int(ec["entries"].sum()) - int(ec["exits"].sum()) == st["on_network"]
+    # lane rows in canonical order: consecutive fronts within a row differ by >= L
+    cells = np.maximum(np.floor(net.edge_length_m.astype(np.float64) + 0.5).astype(np.int64), 5 + 2 + 1)
+    row_len = np.repeat(cells, net.edge_lanes.astype(np.int64))
+    row_start = np.concatenate([[0], np.cumsum(row_len)[:-1]])
+    row_of = np.searchsorted(row_start, occ, side="right") - 1
+    same = row_of[1:] == row_of[:-1]
+    assert np.all(np.diff(occ)[same] >= 5)
+    assert st["on_network"] > 100000
