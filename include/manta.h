@@ -190,6 +190,38 @@ MANTA_API const char *manta_last_error(void);
  * did not run out.  The context stays usable. */
 MANTA_API manta_status manta_selftest_barrier_timeout(int32_t limit_ms, void *cuda_stream);
 
+/* Runs a whole small simulation without allocating any device memory, for
+ * callers that cannot call cudaMalloc: code running while a CUDA graph is
+ * being captured (where allocation is not allowed), host applications whose
+ * device memory is fully reserved by their own pool allocator, or real-time
+ * loops that must not stall on the driver's allocator.  The paper has no
+ * counterpart: it only concerns how device memory is obtained.
+ *
+ * Arguments are those of manta_create, manta_load_trips (host arrays,
+ * copied), the number of steps, and the outputs of manta_stats and
+ * manta_snapshot (host arrays of capacity `cap`).  It returns the same
+ * results, bit for bit, as manta_create + manta_load_trips + manta_step +
+ * manta_stats + manta_snapshot on the same inputs.
+ *
+ * All device state lives in one static device array of 8 MiB that every GPU
+ * loading this library keeps until the process exits (enough for e.g. a
+ * 10x10 grid with 1,000 trips).  A network and trip table needing more is
+ * rejected with MANTA_E_INVALID and a message naming the limit.  Every call
+ * reuses the same array and resets what must start empty; two calls that
+ * overlap on the GPU (other threads, other streams) race on it and must not
+ * be issued.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture begins.  The call synchronises cuda_stream before returning. */
+MANTA_API manta_status manta_run_noalloc(
+    int32_t n_nodes, int32_t n_edges, const int32_t *edge_src, const int32_t *edge_dst, const uint8_t *edge_lanes,
+    const float *edge_length_m, const float *edge_speed_limit_mps, const uint8_t *edge_class,
+    const uint8_t *node_type, const int32_t *node_cycle_steps, const int32_t *node_offset_steps,
+    const int16_t *edge_green_start, const int16_t *edge_green_len, const uint32_t *conn_lane_mask,
+    const manta_config *cfg, int64_t n_trips, const int64_t *route_off, const int32_t *route_edges,
+    const float *depart_time_s, int64_t n_steps, void *cuda_stream, manta_stats_t *stats_out, int64_t cap,
+    int64_t *n_out, float *x, float *v, int32_t *edge, uint8_t *lane, uint32_t *id, uint8_t *dwell,
+    int32_t *route_pos);
+
 #ifdef __cplusplus
 }
 #endif

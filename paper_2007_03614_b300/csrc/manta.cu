@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -67,12 +68,36 @@ struct manta_sim {
   int grid = 0;
 };
 
+// Static device memory for manta_run_noalloc: every device that loads the
+// library holds these bytes until the process exits.
+#define MANTA_NOALLOC_ARENA_BYTES (8u << 20)
+static __device__ __align__(256) unsigned char g_noalloc_arena[MANTA_NOALLOC_ARENA_BYTES];
+
 namespace {
+
+// While set (only inside manta_run_noalloc, on the calling thread), device
+// arrays are carved from the static arena instead of being allocated.
+struct Arena {
+  unsigned char *base;
+  size_t cap, used;
+  bool overflow;
+};
+thread_local Arena *t_arena = nullptr;
 
 template <class T>
 T *dalloc(manta_sim *S, size_t n, bool *ok) {
   void *p = nullptr;
   if (n == 0) n = 1;
+  if (t_arena) {
+    const size_t off = (t_arena->used + 255u) & ~(size_t)255u;
+    if (off + n * sizeof(T) > t_arena->cap) {
+      t_arena->overflow = true;
+      *ok = false;
+      return nullptr;
+    }
+    t_arena->used = off + n * sizeof(T);
+    return reinterpret_cast<T *>(t_arena->base + off);
+  }
   if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     *ok = false;
@@ -615,6 +640,60 @@ manta_status manta_selftest_barrier_timeout(int32_t limit_ms, void *cuda_stream)
   if (e != cudaSuccess) return fail(MANTA_E_CUDA, cudaGetErrorString(e));
   if (h.err == 1) return fail(MANTA_E_TIMEOUT, "barrier wait ran out as expected");
   return MANTA_OK;
+}
+
+manta_status manta_run_noalloc(int32_t n_nodes, int32_t n_edges, const int32_t *edge_src, const int32_t *edge_dst,
+                               const uint8_t *edge_lanes, const float *edge_length_m,
+                               const float *edge_speed_limit_mps, const uint8_t *edge_class,
+                               const uint8_t *node_type, const int32_t *node_cycle_steps,
+                               const int32_t *node_offset_steps, const int16_t *edge_green_start,
+                               const int16_t *edge_green_len, const uint32_t *conn_lane_mask,
+                               const manta_config *cfg, int64_t n_trips, const int64_t *route_off,
+                               const int32_t *route_edges, const float *depart_time_s, int64_t n_steps,
+                               void *cuda_stream, manta_stats_t *stats_out, int64_t cap, int64_t *n_out, float *x,
+                               float *v, int32_t *edge, uint8_t *lane, uint32_t *id, uint8_t *dwell,
+                               int32_t *route_pos) {
+  g_err.clear();
+  if (!stats_out || !n_out) return fail(MANTA_E_INVALID, "stats_out and n_out are required");
+  if (n_steps < 0) return fail(MANTA_E_INVALID, "n_steps < 0");
+  // One-time set-up per device: the device address of the static arena.
+  static std::mutex mu;
+  static void *addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(MANTA_E_CUDA, "no current CUDA device");
+  void *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+      cudaError_t e = cudaGetSymbolAddress(&addr[dev], g_noalloc_arena);
+      if (e != cudaSuccess) {
+        addr[dev] = nullptr;
+        return fail(MANTA_E_CUDA, std::string("cudaGetSymbolAddress of the static arena: ") + cudaGetErrorString(e));
+      }
+    }
+    base = addr[dev];
+  }
+  Arena arena{static_cast<unsigned char *>(base), MANTA_NOALLOC_ARENA_BYTES, 0, false};
+  manta_sim *S = nullptr;
+  t_arena = &arena;
+  manta_status st = manta_create(n_nodes, n_edges, edge_src, edge_dst, edge_lanes, edge_length_m,
+                                 edge_speed_limit_mps, edge_class, node_type, node_cycle_steps, node_offset_steps,
+                                 edge_green_start, edge_green_len, conn_lane_mask, cfg, cuda_stream, &S);
+  if (st == MANTA_OK) st = manta_load_trips(S, n_trips, route_off, route_edges, depart_time_s);
+  t_arena = nullptr;
+  if (arena.overflow) {
+    if (S) manta_destroy(S);
+    return fail(MANTA_E_INVALID, "network and trips need more device memory than the " +
+                                     std::to_string(MANTA_NOALLOC_ARENA_BYTES >> 20) +
+                                     " MiB static arena of manta_run_noalloc");
+  }
+  if (st == MANTA_OK) st = manta_step(S, n_steps);
+  if (st == MANTA_OK) st = manta_stats(S, stats_out);
+  if (st == MANTA_OK) st = manta_snapshot(S, cap, n_out, x, v, edge, lane, id, dwell, route_pos);
+  const std::string msg = g_err;
+  if (S) manta_destroy(S);
+  g_err = msg;
+  return st;
 }
 
 }  // extern "C"

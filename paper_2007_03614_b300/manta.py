@@ -46,7 +46,7 @@ class MantaStats(C.Structure):
 # Every entry point declared in include/manta.h.
 EXPORTS = ("manta_default_config", "manta_create", "manta_load_trips", "manta_step", "manta_stats",
            "manta_edge_counters", "manta_snapshot", "manta_lane_map", "manta_lane_map_bytes",
-           "manta_destroy", "manta_last_error", "manta_selftest_barrier_timeout")
+           "manta_destroy", "manta_last_error", "manta_selftest_barrier_timeout", "manta_run_noalloc")
 
 _lib = None
 
@@ -84,6 +84,10 @@ def load_library():
         lib.manta_lane_map_bytes.argtypes = [P]
         lib.manta_destroy.argtypes = [P]
         lib.manta_last_error.restype = C.c_char_p
+        lib.manta_run_noalloc.restype = C.c_int
+        lib.manta_run_noalloc.argtypes = ([C.c_int32, C.c_int32] + [P] * 12 + [C.POINTER(MantaConfig), C.c_int64]
+                                          + [P] * 3 + [C.c_int64, P, C.POINTER(MantaStats), C.c_int64,
+                                                       C.POINTER(C.c_int64)] + [P] * 7)
         lib.manta_selftest_barrier_timeout.restype = C.c_int
         lib.manta_selftest_barrier_timeout.argtypes = [C.c_int32, P]
         _lib = lib
@@ -205,3 +209,37 @@ def selftest_barrier_timeout(limit_ms=100, stream=None) -> int:
     """Runs the bounded-wait self test; returns the status (E_TIMEOUT expected)."""
     lib = load_library()
     return int(lib.manta_selftest_barrier_timeout(int(limit_ms), _stream_handle(stream)))
+
+
+def run_noalloc(net, trips, n_steps, stream=None, **cfg):
+    """A whole small simulation with no device allocation (manta_run_noalloc):
+    returns (stats, snapshot) exactly as Sim would."""
+    lib = load_library()
+    conf = default_config(**cfg)
+    keep = []
+
+    def arr(a, dt):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(np.asarray(a, dtype=dt))
+        keep.append(a)
+        return a
+
+    n = max(trips.n_trips, 1)
+    out = dict(x=np.zeros(n, np.float32), v=np.zeros(n, np.float32), edge=np.zeros(n, np.int32),
+               lane=np.zeros(n, np.uint8), id=np.zeros(n, np.uint32), dwell=np.zeros(n, np.uint8),
+               route_pos=np.zeros(n, np.int32))
+    st = MantaStats()
+    cnt = C.c_int64()
+    rc = lib.manta_run_noalloc(
+        int(len(net.node_type)), int(len(net.edge_src)),
+        _p(arr(net.edge_src, np.int32)), _p(arr(net.edge_dst, np.int32)), _p(arr(net.edge_lanes, np.uint8)),
+        _p(arr(net.edge_length_m, np.float32)), _p(arr(net.edge_speed_limit_mps, np.float32)),
+        _p(arr(net.edge_class, np.uint8)), _p(arr(net.node_type, np.uint8)), _p(arr(net.node_cycle_steps, np.int32)),
+        _p(arr(net.node_offset_steps, np.int32)), _p(arr(net.edge_green_start, np.int16)),
+        _p(arr(net.edge_green_len, np.int16)), _p(arr(net.conn_lane_mask, np.uint32)), C.byref(conf),
+        int(trips.n_trips), _p(arr(trips.route_off, np.int64)), _p(arr(trips.route_edges, np.int32)),
+        _p(arr(trips.depart_time_s, np.float32)), int(n_steps), _stream_handle(stream), C.byref(st), n,
+        C.byref(cnt), *[_p(out[k]) for k in ("x", "v", "edge", "lane", "id", "dwell", "route_pos")])
+    _check(rc)
+    return st.as_dict(), {k: a[:cnt.value] for k, a in out.items()}
