@@ -144,6 +144,19 @@ def run_gpu(args):
     net, tr = workload()
     stream = torch.cuda.Stream()
     chunk = args.chunk
+    if args.profile_case:
+        # a small case for counter captures: the trips departing 07:30-08:00 on
+        # the full network, 1200 warm-up steps from an empty network at 07:30
+        lo = 7.5 * 3600
+        off, edges, dep = _sample(tr, lo, lo + 1800)
+        sim = manta.Sim(net, stream=stream, t0_step=int(lo / 0.5), n_stats_windows=8)
+        sim.load_trips(off, edges, dep)
+        sim.step(1200)
+        for _ in range(args.steps):
+            sim.step(chunk)
+        st = sim.stats()
+        print(json.dumps({"profile_case": True, "stats": st, "phase_ms": [float(x) for x in sim.phase_times_ms()]}))
+        return
     # ---- device-resident run (the headline value) ----
     sim = manta.Sim(net, stream=stream, t0_step=T0_STEP)
     sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
@@ -171,6 +184,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     s1 = sim.stats()
+    phase_ms = [round(float(x), 2) for x in sim.phase_times_ms()]
     elapsed = sum(times)
     d = {k: s1[k] - s0[k] for k in ("vehicle_updates", "cells_scanned", "route_reads", "lc_evals", "clamps",
                                     "lane_changes", "departed", "arrived")}
@@ -236,6 +250,7 @@ def run_gpu(args):
         "gpu_launches": args.steps * ((chunk + 2047) // 2048),
         "morning_wall_s": morning,
         "counters": d,
+        "phase_ms_all_chunks": phase_ms,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(bytes_alg / max(1, args.steps))},
@@ -319,6 +334,8 @@ def main():
     ap.add_argument("--ref-chunk", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="small case for ncu: 07:30-08:00 trips, 1200-step warm-up launch, then --steps launches")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("need --steps >= 1 and --warmup >= 0")

@@ -174,6 +174,13 @@ MANTA_API manta_status manta_snapshot(manta_sim *sim, int64_t cap, int64_t *n_ou
  * is too small. */
 MANTA_API manta_status manta_lane_map(manta_sim *sim, uint8_t *out, int64_t cap, int64_t *n_out);
 
+/* Synchronises and returns the cumulative device time, in milliseconds, of
+ * the four phases of the step kernel as seen by its first block: [0] lane-
+ * change decisions, [1] lane-change apply, [2] leader scans / IDM / map
+ * writes, [3] merges, departures and arrivals.  Each includes the wait at
+ * the grid barrier that ends it.  A profiling aid. */
+MANTA_API manta_status manta_phase_times(manta_sim *sim, double *ms4);
+
 /* Bytes of the canonical lane map (sum over edges of cells x lanes). */
 MANTA_API int64_t manta_lane_map_bytes(const manta_sim *sim);
 

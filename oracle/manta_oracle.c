@@ -471,8 +471,11 @@ typedef struct {
  * most H cells, looking for the first occupied byte (Section II-D: the
  * leader is found by looking up neighbouring cells).  Nodes on the way act
  * as a stationary virtual leader at their stop line when they hold the
- * vehicle: red signal, stop sign without permit, wrong lane for the next
- * edge (own node); red signal or stop sign (later nodes).               */
+ * vehicle: red signal or stop sign without permit (own node); red signal or
+ * stop sign (later nodes).  A lane not allowed for the next edge does not
+ * hold the vehicle: it only makes the lane change mandatory (Eq. 2), and a
+ * vehicle still in such a lane at the node continues into lane
+ * min(l, lanes - 1) of the next edge.               */
 static scan_t leader_scan(osim *S, int64_t id) {
   const oracle_config *cf = &S->cfg;
   veh_t *V = &S->V[id];
@@ -505,10 +508,9 @@ static scan_t leader_scan(osim *S, int64_t id) {
     if (S->ntype[n] == NODE_SIGNAL && !is_green(S, se, S->k)) blocked = 1;
     if (own) {
       int stop_np = (S->ntype[n] == NODE_STOP) && (S->permit[n] != (uint32_t)id);
-      int wrong = !((S->rmask[r] >> sl) & 1);
       res.reached_own = 1;
-      res.stop_only = stop_np && !wrong;
-      if (stop_np || wrong) blocked = 1;
+      res.stop_only = stop_np;
+      if (stop_np) blocked = 1;
     } else if (S->ntype[n] == NODE_STOP) {
       blocked = 1;
     }

@@ -43,7 +43,8 @@ __global__ void prime_kernel(Params p, uint32_t hi, int cb) {
 __global__ void barrier_selftest_kernel(Ctl *ctl, uint64_t limit_ns) {
   __shared__ int s_ok;
   if (blockIdx.x == 0) return;   // this block never arrives
-  grid_sync(ctl, limit_ns, &s_ok);
+  unsigned target = 0;
+  grid_sync(ctl, target, limit_ns, &s_ok);
 }
 
 }  // namespace
@@ -445,21 +446,20 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   int32_t *d_due = dalloc<int32_t>(S, due_step.size(), &ok);
   uint32_t *d_due_e = dalloc<uint32_t>(S, due_edge.size(), &ok);
   const size_t NT = (size_t)std::max<int64_t>(n, 1);
-  P.x = dalloc<float>(S, NT, &ok); P.v = dalloc<float>(S, NT, &ok);
-  P.id = dalloc<uint32_t>(S, NT, &ok); P.rc = dalloc<uint32_t>(S, NT, &ok);
-  P.rend = dalloc<uint32_t>(S, NT, &ok); P.e = dalloc<uint32_t>(S, NT, &ok);
-  P.ld = dalloc<uint32_t>(S, NT, &ok); P.pcell = dalloc<uint32_t>(S, NT, &ok);
+  P.veh = dalloc<Veh>(S, NT, &ok);
   P.act0 = dalloc<uint32_t>(S, NT, &ok); P.act1 = dalloc<uint32_t>(S, NT, &ok);
   P.freel = dalloc<uint32_t>(S, NT, &ok); P.chg = dalloc<uint32_t>(S, NT, &ok);
   P.req = dalloc<uint32_t>(S, NT, &ok); P.arr = dalloc<uint32_t>(S, NT, &ok);
   P.req_x = dalloc<float>(S, NT, &ok); P.req_v = dalloc<float>(S, NT, &ok); P.req_dw = dalloc<uint32_t>(S, NT, &ok);
+  P.req_g = dalloc<uint32_t>(S, NT, &ok); P.req_t = dalloc<uint32_t>(S, NT, &ok);
+  P.req_e2 = dalloc<uint32_t>(S, NT, &ok); P.req_n = dalloc<uint32_t>(S, NT, &ok);
   if (!ok) return fail(MANTA_E_OOM, "device allocation failed in manta_load_trips");
   bool cp = upload(S, d_route, route) && upload(S, d_roff, roff) && upload(S, d_qoff, q_off) &&
             upload(S, d_qtrip, order) && upload(S, d_due, due_step) && upload(S, d_due_e, due_edge);
   Ctl c0;
   memset(&c0, 0, sizeof(c0));
   c0.due_pos = prime_hi;
-  c0.due_next = prime_hi;
+  c0.due_hi = prime_hi;
   cp = cp && cudaMemcpyAsync(P.ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
   if (!cp) return fail(MANTA_E_CUDA, "upload failed in manta_load_trips");
   P.route = d_route; P.route_off = d_roff; P.q_off = d_qoff; P.q_trip = d_qtrip;
@@ -492,7 +492,10 @@ manta_status manta_step(manta_sim *S, int64_t n_steps) {
     P.k0 = S->k;
     P.n_steps = chunk;
     void *args[] = {&P};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)manta_step_kernel, dim3(S->grid), dim3(kBlock), args, 0,
+    // the grid barrier's arrival counter starts from zero in every launch
+    cudaError_t e = cudaMemsetAsync(&S->P.ctl->bar_count, 0, sizeof(unsigned), S->stream);
+    if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("barrier reset: ") + cudaGetErrorString(e));
+    e = cudaLaunchCooperativeKernel((const void *)manta_step_kernel, dim3(S->grid), dim3(kBlock), args, 0,
                                                 S->stream);
     if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
     S->k += chunk;
@@ -526,7 +529,7 @@ manta_status manta_stats(manta_sim *S, manta_stats_t *out) {
   if (st != MANTA_OK) return st;
   out->departed = (int64_t)c.cnt[CNT_DEP];
   out->arrived = (int64_t)c.cnt[CNT_ARR];
-  out->on_network = c.n_act[S->k & 1];
+  out->on_network = (int64_t)c.cnt[CNT_DEP] - (int64_t)c.cnt[CNT_ARR];
   out->waiting = S->n_trips - out->departed;
   out->vehicle_updates = c.cnt[CNT_UPD];
   out->cells_scanned = c.cnt[CNT_SCAN];
@@ -565,36 +568,45 @@ manta_status manta_snapshot(manta_sim *S, int64_t cap, int64_t *n_out, float *x,
   Ctl c;
   manta_status st = sync_and_check(S, &c);
   if (st != MANTA_OK) return st;
-  const uint32_t n = c.n_act[S->k & 1];
-  *n_out = n;
-  if ((int64_t)n > cap) return fail(MANTA_E_INVALID, "snapshot capacity too small");
-  if (n == 0) return MANTA_OK;
+  const uint32_t len = c.n_act[S->k & 1];
+  const int64_t live = (int64_t)c.cnt[CNT_DEP] - (int64_t)c.cnt[CNT_ARR];
+  *n_out = live;
+  if (live > cap) return fail(MANTA_E_INVALID, "snapshot capacity too small");
+  if (live == 0) return MANTA_OK;
   const Params &P = S->P;
-  std::vector<uint32_t> act(n);
-  if (cudaMemcpy(act.data(), (S->k & 1) ? P.act1 : P.act0, 4ull * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+  std::vector<uint32_t> act(len);
+  if (cudaMemcpy(act.data(), c.act_sel[S->k & 1] ? P.act1 : P.act0, 4ull * len, cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(MANTA_E_CUDA, "copy of the active list failed");
+  act.erase(std::remove(act.begin(), act.end(), MANTA_NONE), act.end());
+  if ((int64_t)act.size() != live) return fail(MANTA_E_DEVICE, "active list and counters disagree");
+  const uint32_t n = (uint32_t)live;
   const size_t NT = (size_t)std::max<int64_t>(S->n_trips, 1);
-  std::vector<float> hx(NT), hv(NT);
-  std::vector<uint32_t> hid(NT), hrc(NT), he(NT), hld(NT);
-  bool ok = cudaMemcpy(hx.data(), P.x, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess &&
-            cudaMemcpy(hv.data(), P.v, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess &&
-            cudaMemcpy(hid.data(), P.id, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess &&
-            cudaMemcpy(hrc.data(), P.rc, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess &&
-            cudaMemcpy(he.data(), P.e, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess &&
-            cudaMemcpy(hld.data(), P.ld, 4 * NT, cudaMemcpyDeviceToHost) == cudaSuccess;
-  if (!ok) return fail(MANTA_E_CUDA, "copy of vehicle state failed");
-  std::sort(act.begin(), act.end(), [&](uint32_t a, uint32_t b) { return hid[a] < hid[b]; });
+  std::vector<Veh> hv(NT);
+  if (cudaMemcpy(hv.data(), P.veh, sizeof(Veh) * NT, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(MANTA_E_CUDA, "copy of vehicle state failed");
+  std::sort(act.begin(), act.end(), [&](uint32_t a, uint32_t b) { return hv[a].id < hv[b].id; });
   for (uint32_t i = 0; i < n; ++i) {
-    const uint32_t s = act[i];
-    if (x) x[i] = hx[s];
-    if (v) v[i] = hv[s];
-    if (edge) edge[i] = (int32_t)he[s];
-    if (lane) lane[i] = (uint8_t)(hld[s] & 0xFFu);
-    if (id) id[i] = hid[s];
-    if (dwell) dwell[i] = (uint8_t)((hld[s] >> 8) & 0xFFu);
-    if (route_pos) route_pos[i] = (int32_t)(hrc[s] - S->route_off_h[hid[s]]);
+    const Veh &w = hv[act[i]];
+    if (x) x[i] = w.x;
+    if (v) v[i] = w.v;
+    if (edge) edge[i] = (int32_t)w.e;
+    if (lane) lane[i] = (uint8_t)(w.ld & 0xFFu);
+    if (id) id[i] = w.id;
+    if (dwell) dwell[i] = (uint8_t)((w.ld >> 8) & 0xFFu);
+    if (route_pos) route_pos[i] = (int32_t)(w.rc - S->route_off_h[w.id]);
   }
   return MANTA_OK;
+}
+
+manta_status manta_phase_times(manta_sim *S, double *ms4) {
+  g_err.clear();
+  if (!S || !ms4) return fail(MANTA_E_INVALID, "NULL argument");
+  for (int q = 0; q < 4; ++q) ms4[q] = 0.0;
+  if (!S->loaded) return MANTA_OK;
+  Ctl c;
+  manta_status st = sync_and_check(S, &c);
+  for (int q = 0; q < 4; ++q) ms4[q] = (double)c.phase_ns[q] * 1e-6;
+  return st;
 }
 
 int64_t manta_lane_map_bytes(const manta_sim *S) { return S ? (int64_t)S->canon_bytes : 0; }

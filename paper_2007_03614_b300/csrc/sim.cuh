@@ -6,13 +6,17 @@
 //                 padding bytes stay 0xFF.  One byte per 1 m cell: 0xFF empty,
 //                 else the speed code of the vehicle whose front is there.
 //   edge tables   EdgeMeta (16 B) and EdgeSig (8 B) per edge, read-only.
-//   vehicle SoA   by slot: x, v, id, rc (route cursor), rend, e, ld (lane |
-//                 dwell << 8 | lane-change target << 16), pcell (its cell in
-//                 the other map buffer, cleared at the start of the next step).
-//   lists         active slots (double buffered), free slots, lane changers,
-//                 crossing requesters, arrivals, departure edges (double
-//                 buffered); appended with warp-aggregated atomics (the order
-//                 of a list never changes a result).
+//   vehicles      48-byte records by slot (Veh): position, speed, id, route
+//                 cursor and end, edge, lane/dwell/target, the cell it left in
+//                 the other map buffer (cleared next step), and a copy of the
+//                 current edge's record.
+//   lists         active slots (a vehicle keeps its list position while on
+//                 the network, arrivals leave holes, departures append, and a
+//                 compaction pass into the other buffer runs when holes pass
+//                 a quarter of the list), free slots, lane changers, crossing
+//                 requesters, arrivals, departure edges (double buffered);
+//                 appended with warp-aggregated atomics (the order of a list
+//                 never changes a result).
 //   request slots per lane: key = (step + 1) << 32 | vehicle id and target lane,
 //                 read by competitors; the lowest id wins (no atomics).
 #pragma once
@@ -40,18 +44,37 @@ enum {
   CNT_UPD = 0, CNT_SCAN, CNT_CLAMP, CNT_LC, CNT_LCE, CNT_RR, CNT_DEP, CNT_ARR, CNT_N
 };
 
+// One vehicle, 48 bytes, fetched with three independent 16-byte loads; it
+// carries a copy of its current edge's record so that no phase needs a
+// dependent edge-table load before it can address the lane map.
+struct __align__(16) Veh {
+  float x;         // front position in cells from the start of the edge
+  float v;         // speed, m/s
+  uint32_t id;     // trip index
+  uint32_t rc;     // index of the current edge in the route array
+  uint32_t rend;   // one past the last route entry of the trip
+  uint32_t e;      // current edge
+  uint32_t ld;     // lane | dwell << 8 | lane-change target << 16
+  uint32_t pcell;  // its cell in the other map buffer (cleared next step), or none
+  EdgeMeta em;     // record of edge e
+};
+
 struct Ctl {
   unsigned bar_count;
   unsigned bar_gen;
   int err;          // 0 ok, 1 barrier wait ran out, 2 index check failed
   int err_info;
-  uint32_t n_act[2];
+  uint32_t n_act[2];      // active-list length (live slots and holes) at even / odd steps
+  uint32_t act_sel[2];    // which buffer holds the active list at even / odd steps
+  uint32_t n_holes[2];    // holes (arrived vehicles) in that list
+  uint32_t n_compact;     // entries written by a compaction pass
   uint32_t n_dep[2];
   uint32_t n_req, n_arr, n_chg, n_depwin;
   uint32_t free_count, n_slots;
-  uint32_t due_pos, due_next;
+  uint32_t due_pos, due_hi;   // trips [due_pos, due_hi) of the due list join queues this step
   uint32_t pad[2];
   unsigned long long cnt[CNT_N];
+  unsigned long long phase_ns[4];   // device time of phases P1..P4 as seen by block 0
 };
 
 struct Params {
@@ -74,13 +97,12 @@ struct Params {
   const uint32_t *due_edge;
   // lane map
   uint8_t *atlas0, *atlas1;
-  // vehicle SoA by slot
-  float *x, *v;
-  uint32_t *id, *rc, *rend, *e, *ld, *pcell;
+  // vehicle records by slot
+  Veh *veh;
   // lists
   uint32_t *act0, *act1, *freel, *chg, *req, *arr, *dep0, *dep1;
   float *req_x, *req_v;
-  uint32_t *req_dw;
+  uint32_t *req_dw, *req_g, *req_t, *req_e2, *req_n;
   // departure queues
   uint32_t *pending, *q_pos;
   unsigned long long *dep_key;

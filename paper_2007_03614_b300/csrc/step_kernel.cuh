@@ -1,9 +1,10 @@
-// step_kernel.cu -- the persistent per-timestep update (sm_103a).
+// step_kernel.cuh -- the persistent per-timestep update (sm_103a).
 //
 // One cooperative launch runs n_steps steps.  Per step k the grid goes
 // through four phases separated by grid barriers with bounded waits:
 //   P1  clear last step's cells in the spare map buffer; lane-change decision
-//       on M_k (Section II-D, Eqs. 2-4); stop-sign permits for this step
+//       on M_k (Section II-D, Eqs. 2-4); stop-sign permits for this step;
+//       the departure-step range of the trips that join queues at k + 1
 //   P2  lane-change apply in place, M_k -> M_k' (skipped when nobody changes)
 //   P3  leader scan along the route on M_k', IDM (Eq. 1), ballistic update,
 //       clamp; write M_{k+1} for vehicles that stay on their edge; crossing
@@ -13,10 +14,21 @@
 // Arithmetic is binary32 with the operation order of the definition; the
 // library is compiled with -fmad=false -prec-div=true -prec-sqrt=true so
 // every operation is one correctly rounded IEEE op.
+//
+// The path is latency-bound on dependent global loads (vehicle record ->
+// edge record -> lane-map row -> route entry -> next edge record -> next
+// row), so the code issues independent loads together: vehicle records are
+// one 32-byte record, lane-map scans issue four 16-byte loads per round trip,
+// and the next route edge and its edge record are fetched while the current
+// row is being scanned.
 #include <stdint.h>
 #include "sim.cuh"
 
+#ifndef MANTA_MIN_BLOCKS_PER_SM
+#define MANTA_MIN_BLOCKS_PER_SM 2
+#endif
 constexpr int kBlock = 256;
+constexpr int kMinBlocksPerSM = MANTA_MIN_BLOCKS_PER_SM;
 
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
@@ -34,35 +46,35 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
 __device__ __forceinline__ uint32_t ldv(const uint32_t *p) { return *(const volatile uint32_t *)p; }
 __device__ __forceinline__ int ldvi(const int *p) { return *(const volatile int *)p; }
 
-// Grid barrier with a bounded wait.  Thread 0 of each block arrives; the last
-// arriver releases the generation word.  A waiter that passes the wall-clock
-// limit sets the sticky error word and the block leaves the kernel.
-__device__ __noinline__ bool grid_sync(Ctl *ctl, uint64_t limit_ns, int *s_ok) {
+// Grid barrier with a bounded wait.  The arrival counter only grows within a
+// launch (the host zeroes it before every launch): barrier number b of the
+// launch completes when the counter reaches b * gridDim.x, so arriving is one
+// fire-and-forget release-add and waiting is an acquire-load spin by thread 0
+// of each block.  A waiter that passes the wall-clock limit sets the sticky
+// error word and adds kBarrierAbort to the counter, which releases every other
+// waiter at once; all blocks then leave the kernel.
+constexpr unsigned kBarrierAbort = 1u << 30;
+
+__device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned &target, uint64_t limit_ns, int *s_ok) {
   __syncthreads();
+  target += gridDim.x;
   if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned gen = ld_acquire(&ctl->bar_gen);
-    __threadfence();
-    const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      ctl->bar_count = 0u;
-      __threadfence();
-      st_release(&ctl->bar_gen, gen + 1u);
-    } else {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_count) : "memory");
+    unsigned c = ld_acquire(&ctl->bar_count);
+    if (c < target) {
       const uint64_t t0 = globaltimer();
       uint32_t spins = 0;
-      while (ld_acquire(&ctl->bar_gen) == gen) {
+      while ((c = ld_acquire(&ctl->bar_count)) < target) {
         if ((++spins & 63u) == 0u && globaltimer() - t0 > limit_ns) {
           atomicCAS(&ctl->err, 0, 1);
-          ok = 0;
+          atomicAdd(&ctl->bar_count, kBarrierAbort);
+          c = kBarrierAbort;
           break;
         }
-        if (spins > 64u) __nanosleep(40);
+        if (spins > 1024u) __nanosleep(64);
       }
     }
-    __threadfence();
-    if (ldvi(&ctl->err) != 0) ok = 0;
-    *s_ok = ok;
+    *s_ok = c < kBarrierAbort;
   }
   __syncthreads();
   return *s_ok != 0;
@@ -93,7 +105,7 @@ __device__ __forceinline__ float irwin_hall(uint64_t seed, uint32_t id, int64_t 
   return __int2float_rn(acc - 100663296) * 5.9604644775390625e-8f;
 }
 
-// ---------------------------------------------------------------- lane map
+// ---------------------------------------------------------------- records
 __device__ __forceinline__ uint32_t cells_of(uint32_t cnl) { return cnl & 0xFFFFFFu; }
 __device__ __forceinline__ int lanes_of(uint32_t cnl) { return (int)((cnl >> 24) & 0xFu); }
 __device__ __forceinline__ int class_of(uint32_t cnl) { return (int)(cnl >> 28); }
@@ -104,23 +116,59 @@ __device__ __forceinline__ uint8_t speed_code(float v) {
 }
 __device__ __forceinline__ float speed_decode(uint32_t c) { return __uint2float_rn(c) * 0.125f; }
 
+__device__ __forceinline__ EdgeMeta load_em(const Params &p, uint32_t e) {
+  const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p.em) + e);
+  EdgeMeta m;
+  m.row0 = q.x; m.cnl = q.y; m.lim = __uint_as_float(q.z); m.dst = q.w;
+  return m;
+}
+__device__ __forceinline__ Veh load_veh(const Params &p, uint32_t s) {
+  const uint4 *a = reinterpret_cast<const uint4 *>(p.veh + s);
+  const uint4 q0 = __ldcg(a), q1 = __ldcg(a + 1), q2 = __ldcg(a + 2);
+  Veh w;
+  w.x = __uint_as_float(q0.x); w.v = __uint_as_float(q0.y); w.id = q0.z; w.rc = q0.w;
+  w.rend = q1.x; w.e = q1.y; w.ld = q1.z; w.pcell = q1.w;
+  w.em.row0 = q2.x; w.em.cnl = q2.y; w.em.lim = __uint_as_float(q2.z); w.em.dst = q2.w;
+  return w;
+}
+// position, speed, lane state (edge unchanged)
+__device__ __forceinline__ void store_veh_state(const Params &p, uint32_t s, const Veh &w) {
+  uint4 *a = reinterpret_cast<uint4 *>(p.veh + s);
+  a[0] = make_uint4(__float_as_uint(w.x), __float_as_uint(w.v), w.id, w.rc);
+  a[1] = make_uint4(w.rend, w.e, w.ld, w.pcell);
+}
+__device__ __forceinline__ void store_veh(const Params &p, uint32_t s, const Veh &w) {
+  store_veh_state(p, s, w);
+  reinterpret_cast<uint4 *>(p.veh + s)[2] = make_uint4(w.em.row0, w.em.cnl, __float_as_uint(w.em.lim), w.em.dst);
+}
+
+// ---------------------------------------------------------------- lane map
 // bit 7 of each byte of the result is set iff that byte of w is not 0xFF
 __device__ __forceinline__ uint32_t occupied_bits(uint32_t w) {
   const uint32_t t = ~w;
   return (t | ((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu)) & 0x80808080u;
 }
 
-// First occupied cell in row[lo..hi] (inclusive) or -1.  16-byte loads over
-// the 16-byte aligned row; bytes outside [lo, hi] are masked off.
-__device__ __forceinline__ int first_up(const uint8_t *row, int lo, int hi) {
-  if (lo > hi) return -1;
-  for (int c = lo & ~15; c <= hi; c += 16) {
-    const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(row + c));
-    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+// A run of four 16-byte chunks of a row, loaded in one round trip.
+struct Batch {
+  uint4 q[4];
+};
+__device__ __forceinline__ void load_batch(const uint8_t *row, int c, int hi, Batch &b) {
+  const uint4 none = make_uint4(~0u, ~0u, ~0u, ~0u);
+  b.q[0] = __ldcg(reinterpret_cast<const uint4 *>(row + c));
+  b.q[1] = (c + 16 <= hi) ? __ldcg(reinterpret_cast<const uint4 *>(row + c + 16)) : none;
+  b.q[2] = (c + 32 <= hi) ? __ldcg(reinterpret_cast<const uint4 *>(row + c + 32)) : none;
+  b.q[3] = (c + 48 <= hi) ? __ldcg(reinterpret_cast<const uint4 *>(row + c + 48)) : none;
+}
+// first occupied cell in [lo, hi] within the batch starting at cell c, or -1
+__device__ __forceinline__ int check_batch(const Batch &b, int c, int lo, int hi) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int base = c + 4 * j;
-      uint32_t m = occupied_bits(w[j]);
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t w[4] = {b.q[j].x, b.q[j].y, b.q[j].z, b.q[j].w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int base = c + 16 * j + 4 * t;
+      uint32_t m = occupied_bits(w[t]);
       if (base < lo) m = (lo - base >= 4) ? 0u : (m & (0xFFFFFFFFu << (8 * (lo - base))));
       if (base + 3 > hi) m = (base > hi) ? 0u : (m & (0xFFFFFFFFu >> (8 * (base + 3 - hi))));
       if (m) return base + ((__ffs(m) - 1) >> 3);
@@ -128,22 +176,50 @@ __device__ __forceinline__ int first_up(const uint8_t *row, int lo, int hi) {
   }
   return -1;
 }
+// First occupied cell of row[lo..hi] (inclusive), continuing from a batch
+// already loaded at lo & ~15; -1 if none.  Rows are 16-byte aligned and padded.
+__device__ __forceinline__ int scan_from(const uint8_t *row, int lo, int hi, Batch &b) {
+  int c = lo & ~15;
+  for (;;) {
+    const int r = check_batch(b, c, lo, hi);
+    if (r >= 0) return r;
+    c += 64;
+    if (c > hi) return -1;
+    load_batch(row, c, hi, b);
+  }
+}
+__device__ __forceinline__ int first_up(const uint8_t *row, int lo, int hi) {
+  if (lo > hi) return -1;
+  Batch b;
+  load_batch(row, lo & ~15, hi, b);
+  return scan_from(row, lo, hi, b);
+}
 
-// Last occupied cell in row[lo..hi] (scanning downward from hi) or -1.
+// Last occupied cell in row[lo..hi] (scanning downward from hi) or -1;
+// four 16-byte chunks per round trip.
 __device__ __forceinline__ int first_down(const uint8_t *row, int hi, int lo) {
   if (lo > hi) return -1;
-  for (int c = hi & ~15; c + 15 >= lo; c -= 16) {
-    const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(row + c));
-    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  const uint4 none = make_uint4(~0u, ~0u, ~0u, ~0u);
+  for (int c = hi & ~15; c + 15 >= lo; c -= 64) {
+    uint4 q[4];
+    q[0] = __ldcg(reinterpret_cast<const uint4 *>(row + c));
 #pragma unroll
-    for (int j = 3; j >= 0; --j) {
-      const int base = c + 4 * j;
-      uint32_t m = occupied_bits(w[j]);
-      if (base < lo) m = (lo - base >= 4) ? 0u : (m & (0xFFFFFFFFu << (8 * (lo - base))));
-      if (base + 3 > hi) m = (base > hi) ? 0u : (m & (0xFFFFFFFFu >> (8 * (base + 3 - hi))));
-      if (m) return base + ((31 - __clz(m)) >> 3);
+    for (int j = 1; j < 4; ++j)
+      q[j] = (c - 16 * j >= 0 && c - 16 * j + 15 >= lo) ? __ldcg(reinterpret_cast<const uint4 *>(row + c - 16 * j)) : none;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int cc = c - 16 * j;
+      const uint32_t w[4] = {q[j].x, q[j].y, q[j].z, q[j].w};
+#pragma unroll
+      for (int t = 3; t >= 0; --t) {
+        const int base = cc + 4 * t;
+        uint32_t m = occupied_bits(w[t]);
+        if (base < lo) m = (lo - base >= 4) ? 0u : (m & (0xFFFFFFFFu << (8 * (lo - base))));
+        if (base + 3 > hi) m = (base > hi) ? 0u : (m & (0xFFFFFFFFu >> (8 * (base + 3 - hi))));
+        if (m) return base + ((31 - __clz(m)) >> 3);
+      }
     }
-    if (c == 0) break;
+    if (c < 64) break;
   }
   return -1;
 }
@@ -179,17 +255,31 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t *counter, bool pred) {
 
 // ------------------------------------------------------------ lane change
 // Target lane or -1 (Section II-D: mandatory vs discretionary; Eq. 2; Eqs. 3-4).
-__device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, uint32_t vid, float x, float v, const EdgeMeta &em,
-                         int lane, uint32_t rc, uint32_t rend, uint64_t &c_lce) {
+// The route entry (lane mask toward the next edge), the Eq. 2 probability and
+// the first chunks of the own and target lane rows are fetched together.
+__device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const Veh &w, uint64_t &c_lce) {
+  const EdgeMeta &em = w.em;
   const int nl = lanes_of(em.cnl);
-  if (nl < 2) return -1;
+  const int lane = (int)(w.ld & 0xFFu);
   const int dir = (k & 1) ? -1 : 1;
   const int lt = lane + dir;
   if (lt < 0 || lt >= nl) return -1;
   const int C = (int)cells_of(em.cnl), L = p.L, H = p.H;
-  const int cell = (int)floorf(x);
-  const bool has_next = rc + 1u < rend;
-  const uint32_t mask = has_next ? (__ldg(p.route + rc) >> MANTA_EDGE_BITS) : 0xFFu;
+  const int cell = (int)floorf(w.x);
+  const float v = w.v;
+  const bool has_next = w.rc + 1u < w.rend;
+  const uint32_t stride = stride_of((uint32_t)C);
+  const uint8_t *trow = cur + em.row0 + (uint32_t)lt * stride;
+  const uint8_t *orow = cur + em.row0 + (uint32_t)lane * stride;
+  const int hi = min(cell + H, C - 1);
+  const int lo_t = max(0, cell - L + 1);     // target-lane cells from the lateral-overlap window on
+  const uint32_t ent = has_next ? __ldg(p.route + w.rc) : 0xFFFFFFFFu;
+  const float mprob = __ldg(p.mtab + (C - 1 - cell));
+  Batch bt, bo;
+  load_batch(trow, lo_t & ~15, hi, bt);
+  const bool own_scan = cell + 1 <= hi;
+  if (own_scan) load_batch(orow, (cell + 1) & ~15, hi, bo);
+  const uint32_t mask = ent >> MANTA_EDGE_BITS;
   const bool ok_l = (mask >> lane) & 1u, ok_lt = (mask >> lt) & 1u;
   bool mandatory = false;
   if (has_next && !ok_l) {
@@ -204,30 +294,30 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, uint32_
   } else if (!ok_lt) {
     return -1;
   }
-  const uint32_t stride = stride_of((uint32_t)C);
-  const uint8_t *trow = cur + em.row0 + (uint32_t)lt * stride;
-  const int hi = min(cell + H, C - 1);
+  int c1, ca;
   if (mandatory) {
-    const float u1 = uni(p.seed, vid, k, 0);
-    if (!(u1 < __ldg(p.mtab + (C - 1 - cell)))) return -1;
+    const float u1 = uni(p.seed, w.id, k, 0);
+    if (!(u1 < mprob)) return -1;
+    c1 = scan_from(trow, lo_t, hi, bt);
+    ca = c1;
   } else {
-    const uint8_t *orow = cur + em.row0 + (uint32_t)lane * stride;
-    const int co = first_up(orow, cell + 1, hi);
+    if (!own_scan) return -1;
+    const int co = scan_from(orow, cell + 1, hi, bo);
     if (co < 0) return -1;
     if (!(speed_decode(cell_byte(orow, co)) < v)) return -1;
     const int own_gap = co - L - cell;
-    const int ca = first_up(trow, cell + L, hi);
+    c1 = scan_from(trow, lo_t, hi, bt);
+    ca = (c1 >= 0 && c1 <= cell + L - 1) ? first_up(trow, cell + L, hi) : c1;
     if (ca >= 0 && !(ca - L - cell > own_gap)) return -1;
   }
   c_lce++;
-  if (first_up(trow, max(0, cell - L + 1), min(C - 1, cell + L - 1)) >= 0) return -1;   // lateral overlap
-  const int ca = first_up(trow, cell + L, hi);
+  if (c1 >= 0 && c1 <= cell + L - 1) return -1;     // lateral overlap
   const int cb = first_down(trow, cell - L, max(0, cell - H));
   const float g = v < p.g_split ? p.g_low : p.g_high;
-  const float alpha = p.alpha_lo + (p.alpha_hi - p.alpha_lo) * uni(p.seed, vid, 0, 3);
+  const float alpha = p.alpha_lo + (p.alpha_hi - p.alpha_lo) * uni(p.seed, w.id, 0, 3);
   if (ca >= 0) {
     const float va = speed_decode(cell_byte(trow, ca));
-    const float eps_a = irwin_hall(p.seed, vid, k, 1);
+    const float eps_a = irwin_hall(p.seed, w.id, k, 1);
     float t = g + alpha * v;          // Eq. 3, alpha_a = alpha_i
     t = t + alpha * (v - va);
     const float glead = fmaxf(g, t) + eps_a;
@@ -235,13 +325,38 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, uint32_
   }
   if (cb >= 0) {
     const float vb = speed_decode(cell_byte(trow, cb));
-    const float eps_b = irwin_hall(p.seed, vid, k, 2);
+    const float eps_b = irwin_hall(p.seed, w.id, k, 2);
     float t = g + alpha * v;          // Eq. 4, alpha_b = alpha_i
     t = t + alpha * (v - vb);
     const float glag = fmaxf(g, t) + eps_b;
     if (!(__int2float_rn(cell - L - cb) >= glag)) return -1;
   }
   return lt;
+}
+
+// Lowest id among the other crossing requests for target lane `tgt` posted
+// this step (tag) by the in-lanes [o0, o1) of a node, excluding lane `skip`;
+// MANTA_NONE if there is none.  Eight in-lanes per round trip.
+__device__ __forceinline__ uint32_t min_competitor(const Params &p, uint32_t o0, uint32_t o1, uint32_t skip,
+                                                   uint32_t tgt, uint32_t tag) {
+  uint32_t best = MANTA_NONE;
+  for (uint32_t o = o0; o < o1; o += 8u) {
+    uint32_t g[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) g[j] = (o + j < o1) ? __ldg(p.nin + o + j) : MANTA_NONE;
+    unsigned long long key[8];
+    uint32_t tg[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const bool use = g[j] != MANTA_NONE && g[j] != skip;
+      key[j] = use ? __ldcg(p.req_key + g[j]) : 0ull;
+      tg[j] = use ? __ldcg(p.req_tgt + g[j]) : MANTA_NONE;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if ((uint32_t)(key[j] >> 32) == tag && tg[j] == tgt && (uint32_t)key[j] < best) best = (uint32_t)key[j];
+  }
+  return best;
 }
 
 // ------------------------------------------------------------ leader scan
@@ -256,46 +371,62 @@ struct Scan {
 };
 
 // Walk the lane map along the route from the cell ahead, at most H cells,
-// stopping at the first occupied byte or at a node that holds the vehicle.
-__device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, uint32_t vid, int cell, uint32_t e,
-                            const EdgeMeta &em0, int lane, uint32_t rc, uint32_t rend, uint64_t &c_scan,
-                            uint64_t &c_rr) {
+// stopping at the first occupied byte or at a node that holds the vehicle
+// (red signal; stop sign without the permit, or any stop sign beyond the own
+// node).  A lane not allowed for the next edge does not hold the vehicle.
+// The next segment's route entry and edge record are fetched while the
+// current row is scanned.
+__device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, const Veh &w, int cell,
+                            uint64_t &c_scan, uint64_t &c_rr) {
   Scan s;
   s.kind = SC_FREE; s.cL = 0; s.vL = 0.0f; s.reached_own = false; s.stop_only = false; s.e2 = MANTA_NONE;
   const int limit = cell + p.H;
-  int base = 0, pos = cell + 1, sl = lane;
-  uint32_t r = rc, se = e;
-  EdgeMeta sm = em0;
+  int base = 0, pos = cell + 1, sl = (int)(w.ld & 0xFFu);
+  uint32_t r = w.rc, se = w.e;
+  EdgeMeta sm = w.em;
   bool own = true;
   for (;;) {
     const int segC = (int)cells_of(sm.cnl);
     const int hi_pos = min(limit, base + segC - 1);
-    if (pos <= hi_pos) {
-      const uint8_t *row = cur + sm.row0 + (uint32_t)sl * stride_of((uint32_t)segC);
-      const int c = first_up(row, pos - base, hi_pos - base);
+    const int B = base + segC;
+    const bool reach = (B <= limit) && (r + 1u < w.rend);
+    uint32_t nent = 0;
+    if (reach) nent = __ldg(p.route + r + 1u);
+    const uint8_t *row = cur + sm.row0 + (uint32_t)sl * stride_of((uint32_t)segC);
+    Batch b;
+    const bool scan = pos <= hi_pos;
+    if (scan) load_batch(row, (pos - base) & ~15, hi_pos - base, b);
+    uint8_t nt = 0;
+    EdgeSig sig;
+    sig.cyc = 0; sig.off = 0; sig.gs = 0; sig.gl = 0;
+    EdgeMeta sm2;
+    sm2.row0 = 0; sm2.cnl = 0; sm2.lim = 0.0f; sm2.dst = 0;
+    if (reach) {
+      nt = __ldg(p.ntype + sm.dst);
+      sig = load_sig(p, se);
+      sm2 = load_em(p, nent & MANTA_EDGE_MASK);
+    }
+    if (scan) {
+      const int c = scan_from(row, pos - base, hi_pos - base, b);
       if (c >= 0) {
         s.kind = SC_LEADER; s.cL = base + c; s.vL = speed_decode(cell_byte(row, c));
         c_scan += (uint64_t)(s.cL - cell);
         return s;
       }
     }
-    const int B = base + segC;
     if (B > limit) { c_scan += (uint64_t)p.H; return s; }
-    if (r + 1u >= rend) { c_scan += (uint64_t)(B - 1 - cell); return s; }
+    if (r + 1u >= w.rend) { c_scan += (uint64_t)(B - 1 - cell); return s; }
     c_rr++;
     const uint32_t n = sm.dst;
-    const uint32_t cur_ent = __ldg(p.route + r);
-    const uint32_t e2 = __ldg(p.route + r + 1u) & MANTA_EDGE_MASK;
-    const uint8_t nt = __ldg(p.ntype + n);
+    const uint32_t e2 = nent & MANTA_EDGE_MASK;
     bool blocked = false;
-    if (nt == 2 && !is_green(load_sig(p, se), k)) blocked = true;
+    if (nt == 2 && !is_green(sig, k)) blocked = true;
     if (own) {
-      const bool stop_np = (nt == 1) && (ldv(p.permit + n) != vid);
-      const bool wrong = !(((cur_ent >> MANTA_EDGE_BITS) >> sl) & 1u);
+      const bool stop_np = (nt == 1) && (ldv(p.permit + n) != w.id);
       s.reached_own = true;
-      s.stop_only = stop_np && !wrong;
+      s.stop_only = stop_np;
       s.e2 = e2;
-      if (stop_np || wrong) blocked = true;
+      if (stop_np) blocked = true;
     } else if (nt == 1) {
       blocked = true;
     }
@@ -305,58 +436,80 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, uint
       return s;
     }
     ++r; base = B; pos = B; se = e2;
-    sm = p.em[e2];
+    sm = sm2;
     sl = min(sl, lanes_of(sm.cnl) - 1);
     own = false;
   }
 }
 
 // ------------------------------------------------------------ the kernel
-__global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
+__global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Params p) {
   __shared__ int s_ok;
   __shared__ unsigned long long s_cnt[CNT_N];
   Ctl *ctl = p.ctl;
   if (threadIdx.x < CNT_N) s_cnt[threadIdx.x] = 0ull;
   __syncthreads();
   uint64_t c_upd = 0, c_scan = 0, c_clamp = 0, c_lc = 0, c_lce = 0, c_rr = 0, c_dep = 0, c_arr = 0;
+  uint64_t ph[4] = {0, 0, 0, 0};
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t gsz = gridDim.x * blockDim.x;
   const int L = p.L;
   bool alive = ldvi(&ctl->err) == 0;
+  unsigned bar_target = 0;
+  uint64_t tp = timer ? globaltimer() : 0;
   for (int it = 0; it < p.n_steps && alive; ++it) {
     const int64_t k = p.k0 + it;
     const int cb = (int)(k & 1);
     uint8_t *cur = cb ? p.atlas1 : p.atlas0;
     uint8_t *nxt = cb ? p.atlas0 : p.atlas1;
-    uint32_t *act = cb ? p.act1 : p.act0;
-    uint32_t *act_n = cb ? p.act0 : p.act1;
+    const uint32_t sel = ldv(&ctl->act_sel[cb]);
+    const uint32_t holes = ldv(&ctl->n_holes[cb]);
     uint32_t *dep = cb ? p.dep1 : p.dep0;
     uint32_t *dep_n = cb ? p.dep0 : p.dep1;
-    const uint32_t nact = ldv(&ctl->n_act[cb]);
+    uint32_t nact = ldv(&ctl->n_act[cb]);
+    // compact the active list into the other buffer when holes pass a quarter of it
+    const bool compact = holes > 0u && 4u * holes > nact;
+    const uint32_t *act_in = sel ? p.act1 : p.act0;
+    uint32_t *act = compact ? (sel ? p.act0 : p.act1) : (sel ? p.act1 : p.act0);
     // ================================================================ P1
     if (gtid == 0) {
-      ctl->due_pos = ctl->due_next;
       ctl->n_req = 0u;
       ctl->n_arr = 0u;
-      ctl->n_act[cb ^ 1] = 0u;
+      ctl->n_holes[cb ^ 1] = compact ? 0u : holes;
+      ctl->act_sel[cb ^ 1] = compact ? (sel ^ 1u) : sel;
       ctl->n_dep[cb ^ 1] = 0u;
       const uint32_t fc = ctl->free_count, w = ctl->n_depwin;
       if (w <= fc) ctl->free_count = fc - w;
       else { ctl->n_slots += w - fc; ctl->free_count = 0u; }
       ctl->n_depwin = 0u;
     }
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+      // trips with departure step <= k + 1 not yet queued: [due_pos, due_hi)
+      const uint32_t lo0 = ldv(&ctl->due_hi);
+      uint32_t lo = lo0;
+      for (;;) {
+        const uint32_t i = lo + (threadIdx.x & 31);
+        const bool le = i < p.n_trips && (int64_t)__ldg(p.due_step + i) <= k + 1;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, le);
+        lo += (uint32_t)__popc(bal);
+        if (bal != 0xFFFFFFFFu) break;
+      }
+      if (threadIdx.x == 0) { ctl->due_pos = lo0; ctl->due_hi = lo; }
+    }
     for (uint32_t i = gtid; i < nact; i += gsz) {
-      const uint32_t s = __ldcg(act + i);
-      const uint32_t pc = __ldcg(p.pcell + s);
-      if (pc != MANTA_NONE) nxt[pc] = (uint8_t)MANTA_EMPTY;
-      const uint32_t e = __ldcg(p.e + s);
-      const EdgeMeta em = p.em[e];
+      const uint32_t s = __ldcg(act_in + i);
+      if (compact) {
+        const uint32_t at = warp_append(&ctl->n_compact, s != MANTA_NONE);
+        if (s != MANTA_NONE) act[at] = s;
+      }
+      if (s == MANTA_NONE) continue;
+      const Veh w = load_veh(p, s);
+      if (w.pcell != MANTA_NONE) nxt[w.pcell] = (uint8_t)MANTA_EMPTY;
       int tgt = -1;
-      if (lanes_of(em.cnl) >= 2) {
-        const uint32_t ldw = __ldcg(p.ld + s);
-        tgt = lc_decide(p, cur, k, __ldcg(p.id + s), __ldcg(p.x + s), __ldcg(p.v + s), em, (int)(ldw & 0xFFu),
-                        __ldcg(p.rc + s), __ldcg(p.rend + s), c_lce);
-        if (tgt >= 0) p.ld[s] = (ldw & 0xFFFFu) | ((uint32_t)tgt << 16);
+      if (lanes_of(w.em.cnl) >= 2) {
+        tgt = lc_decide(p, cur, k, w, c_lce);
+        if (tgt >= 0) p.veh[s].ld = (w.ld & 0xFF00FFFFu) | ((uint32_t)tgt << 16);
       }
       const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
       if (tgt >= 0) p.chg[at] = s;
@@ -377,33 +530,39 @@ __global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
         }
       }
     }
-    if (!grid_sync(ctl, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+    if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+    if (timer) { const uint64_t t = globaltimer(); ph[0] += t - tp; tp = t; }
     // ================================================================ P2
     const uint32_t nchg = ldv(&ctl->n_chg);
     if (nchg) {
       for (uint32_t i = gtid; i < nchg; i += gsz) {
         const uint32_t s = __ldcg(p.chg + i);
-        const uint32_t e = __ldcg(p.e + s), ldw = __ldcg(p.ld + s);
-        const EdgeMeta em = p.em[e];
+        const Veh w = load_veh(p, s);
+        const EdgeMeta &em = w.em;
         const uint32_t stride = stride_of(cells_of(em.cnl));
-        const uint32_t cell = (uint32_t)(int)floorf(__ldcg(p.x + s));
-        const uint32_t lo = ldw & 0xFFu, ln = (ldw >> 16) & 0xFFu;
+        const uint32_t cell = (uint32_t)(int)floorf(w.x);
+        const uint32_t lo = w.ld & 0xFFu, ln = (w.ld >> 16) & 0xFFu;
         const uint32_t a = em.row0 + lo * stride + cell, b = em.row0 + ln * stride + cell;
         cur[b] = cur[a];
         cur[a] = (uint8_t)MANTA_EMPTY;
-        p.ld[s] = (ldw & 0xFF00u) | ln;
+        p.veh[s].ld = (w.ld & 0x0000FF00u) | ln;
         c_lc++;
       }
-      if (!grid_sync(ctl, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+      if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
     }
+    if (timer) { const uint64_t t = globaltimer(); ph[1] += t - tp; tp = t; }
     // ================================================================ P3
-    if (gtid == 0) ctl->n_chg = 0u;
+    if (compact) nact = ldv(&ctl->n_compact);
+    if (gtid == 0) {
+      ctl->n_chg = 0u;
+      ctl->n_act[cb ^ 1] = nact;   // departures of this step append after it
+    }
     const uint32_t tag = (uint32_t)(k + 1);
     // departure requests on M_k'
     const uint32_t ndep = ldv(&ctl->n_dep[cb]);
     for (uint32_t i = gtid; i < ndep; i += gsz) {
       const uint32_t e = __ldcg(dep + i);
-      const EdgeMeta em = p.em[e];
+      const EdgeMeta em = load_em(p, e);
       const int C = (int)cells_of(em.cnl);
       const int need = min(C, L + p.s0c[class_of(em.cnl)]);
       if (first_up(cur + em.row0, 0, need - 1) >= 0) continue;
@@ -413,24 +572,33 @@ __global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
     // vehicles
     const int64_t wk = k - p.t0;
     const int win = (wk >= 0 && wk / p.win_steps < p.n_win) ? (int)(wk / p.win_steps) : -1;
+    // two-stage prefetch: slot of the vehicle after next, record of the next one
+    uint32_t s_nx = gtid + gsz < nact ? __ldcg(act + gtid + gsz) : MANTA_NONE;
+    uint32_t s_cu = gtid < nact ? __ldcg(act + gtid) : MANTA_NONE;
+    Veh w_nx;
+    if (s_cu != MANTA_NONE) w_nx = load_veh(p, s_cu);
     for (uint32_t i = gtid; i < nact; i += gsz) {
-      const uint32_t s = __ldcg(act + i);
-      const float x = __ldcg(p.x + s), v = __ldcg(p.v + s);
-      const uint32_t vid = __ldcg(p.id + s), rc = __ldcg(p.rc + s), rend = __ldcg(p.rend + s);
-      const uint32_t e = __ldcg(p.e + s), ldw = __ldcg(p.ld + s);
-      const int lane = (int)(ldw & 0xFFu);
-      const uint32_t dwell = (ldw >> 8) & 0xFFu;
-      const EdgeMeta em = p.em[e];
+      const uint32_t s = s_cu;
+      Veh w = w_nx;
+      const uint32_t s_nn = i + 2u * gsz < nact ? __ldcg(act + i + 2u * gsz) : MANTA_NONE;
+      if (i + gsz < nact && s_nx != MANTA_NONE) w_nx = load_veh(p, s_nx);
+      s_cu = s_nx;
+      s_nx = s_nn;
+      if (s == MANTA_NONE) continue;
+      const float x = w.x, v = w.v;
+      const int lane = (int)(w.ld & 0xFFu);
+      const uint32_t dwell = (w.ld >> 8) & 0xFFu;
+      const EdgeMeta em = w.em;
       const int C = (int)cells_of(em.cnl);
       const int cls = class_of(em.cnl);
       const uint32_t stride = stride_of((uint32_t)C);
       const int cell = (int)floorf(x);
       const uint32_t gcell = em.row0 + (uint32_t)lane * stride + (uint32_t)cell;
-      const Scan sc = leader_scan(p, cur, k, vid, cell, e, em, lane, rc, rend, c_scan, c_rr);
+      const Scan sc = leader_scan(p, cur, k, w, cell, c_scan, c_rr);
       const float a = p.a[cls], b = p.b[cls], T = p.T[cls], s0 = p.s0[cls];
       const float v0 = em.lim * p.v0f[cls];
       const float r1 = v / v0, r2 = r1 * r1, r4 = r2 * r2;
-      const bool has_next = rc + 1u < rend;
+      const bool has_next = w.rc + 1u < w.rend;
       float xn, vn;
       bool stop_in_place = false;
       float acc = 0.0f;
@@ -463,8 +631,8 @@ __global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
         if (has_next && xt >= __int2float_rn(C)) {
           // at most one node per step: stay within the next edge
           uint32_t e2 = sc.e2;
-          if (e2 == MANTA_NONE) e2 = __ldg(p.route + rc + 1u) & MANTA_EDGE_MASK;
-          const int cap = C + (int)cells_of(p.em[e2].cnl) - 1;
+          if (e2 == MANTA_NONE) e2 = __ldg(p.route + w.rc + 1u) & MANTA_EDGE_MASK;
+          const int cap = C + (int)cells_of(load_em(p, e2).cnl) - 1;
           if (!has_bound || cap < bnd) { has_bound = true; bnd = cap; }
         }
         if (has_bound && xt > __int2float_rn(bnd)) { xn = fmaxf(x, __int2float_rn(bnd)); vn = 0.0f; c_clamp++; }
@@ -476,8 +644,8 @@ __global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
         if ((int)floorf(xn) >= zone && vn < p.stop_eps) dwn = dwell < 255u ? dwell + 1u : 255u;
       }
       if (has_next && sc.reached_own && __ldg(p.ntype + em.dst) == 1) {
-        const uint32_t g = __ldg(p.lane_base + e) + (uint32_t)lane;
-        p.slot_id[g] = vid;
+        const uint32_t g = __ldg(p.lane_base + w.e) + (uint32_t)lane;
+        p.slot_id[g] = w.id;
         p.slot_td[g] = ((uint32_t)(tag & 0xFFFFFF) << 8) | dwn;
       }
       c_upd++;
@@ -485,97 +653,93 @@ __global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
       const bool arrive = crossing && !has_next;
       const bool request = crossing && has_next;
       if (arrive) {
-        atomicAdd(p.exitc + e, 1u);
+        atomicAdd(p.exitc + w.e, 1u);
         c_arr++;
-      } else if (request) {
-        const uint32_t e2 = sc.e2 != MANTA_NONE ? sc.e2 : (__ldg(p.route + rc + 1u) & MANTA_EDGE_MASK);
-        const int l2 = min(lane, lanes_of(p.em[e2].cnl) - 1);
-        const uint32_t g = __ldg(p.lane_base + e) + (uint32_t)lane;
-        p.req_tgt[g] = __ldg(p.lane_base + e2) + (uint32_t)l2;
-        p.req_key[g] = ((unsigned long long)tag << 32) | vid;
-      } else {
-        p.x[s] = xn; p.v[s] = vn;
-        p.ld[s] = (uint32_t)lane | (dwn << 8);
-        p.pcell[s] = gcell;
+      }
+      uint32_t rq_g = 0, rq_t = 0, rq_e2 = 0;
+      if (request) {
+        rq_e2 = sc.e2 != MANTA_NONE ? sc.e2 : (__ldg(p.route + w.rc + 1u) & MANTA_EDGE_MASK);
+        const int l2 = min(lane, lanes_of(load_em(p, rq_e2).cnl) - 1);
+        rq_g = __ldg(p.lane_base + w.e) + (uint32_t)lane;
+        rq_t = __ldg(p.lane_base + rq_e2) + (uint32_t)l2;
+        p.req_tgt[rq_g] = rq_t;
+        p.req_key[rq_g] = ((unsigned long long)tag << 32) | w.id;
+      } else if (!arrive) {
+        w.x = xn; w.v = vn;
+        w.ld = (uint32_t)lane | (dwn << 8);
+        w.pcell = gcell;
+        store_veh_state(p, s, w);
         nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xn)] = speed_code(vn);
         if (win >= 0) {
-          const size_t o = (size_t)win * p.E + e;
+          const size_t o = (size_t)win * p.E + w.e;
           atomicAdd(p.ssum + o, (unsigned long long)(vn * 1048576.0f));
           atomicAdd(p.scnt + o, 1u);
         }
       }
-      const uint32_t ia = warp_append(&ctl->n_arr, arrive);
       if (arrive) {
+        act[i] = MANTA_NONE;
+        const uint32_t ia = atomicAdd(&ctl->n_arr, 1u);
         p.arr[ia] = gcell;
         p.freel[atomicAdd(&ctl->free_count, 1u)] = s;
+        atomicAdd(&ctl->n_holes[cb ^ 1], 1u);
       }
-      const uint32_t iq = warp_append(&ctl->n_req, request);
-      if (request) { p.req[iq] = s; p.req_x[iq] = xn; p.req_v[iq] = vn; p.req_dw[iq] = dwn; }
-      const uint32_t in = warp_append(&ctl->n_act[cb ^ 1], !arrive && !request);
-      if (!arrive && !request) act_n[in] = s;
+      if (request) {
+        const uint32_t iq = atomicAdd(&ctl->n_req, 1u);
+        p.req[iq] = s; p.req_x[iq] = xn; p.req_v[iq] = vn; p.req_dw[iq] = dwn;
+        p.req_g[iq] = rq_g; p.req_t[iq] = rq_t; p.req_e2[iq] = rq_e2; p.req_n[iq] = em.dst;
+      }
     }
-    if (!grid_sync(ctl, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+    if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+    if (timer) { const uint64_t t = globaltimer(); ph[2] += t - tp; tp = t; }
     // ================================================================ P4
     // crossing requests: the lowest id among requests for the same target lane wins
     const uint32_t nreq = ldv(&ctl->n_req);
     for (uint32_t i = gtid; i < nreq; i += gsz) {
       const uint32_t s = __ldcg(p.req + i);
-      const uint32_t vid = __ldcg(p.id + s), e = __ldcg(p.e + s), ldw = __ldcg(p.ld + s);
-      const int lane = (int)(ldw & 0xFFu);
-      const EdgeMeta em = p.em[e];
-      const uint32_t stride = stride_of(cells_of(em.cnl));
-      const uint32_t gown = __ldg(p.lane_base + e) + (uint32_t)lane;
-      const uint32_t tgt = __ldcg(p.req_tgt + gown);
-      const uint32_t n = em.dst;
-      bool win_it = true;
+      const uint32_t gown = __ldcg(p.req_g + i), tgt = __ldcg(p.req_t + i);
+      const uint32_t e2 = __ldcg(p.req_e2 + i), n = __ldcg(p.req_n + i);
       const uint32_t o0 = __ldg(p.nin_off + n), o1 = __ldg(p.nin_off + n + 1);
-      for (uint32_t o = o0; o < o1 && win_it; ++o) {
-        const uint32_t g = __ldg(p.nin + o);
-        if (g == gown) continue;
-        const unsigned long long key = __ldcg(p.req_key + g);
-        if ((uint32_t)(key >> 32) == tag && __ldcg(p.req_tgt + g) == tgt && (uint32_t)key < vid) win_it = false;
-      }
-      const uint32_t rc = __ldcg(p.rc + s);
-      const uint32_t e2 = __ldg(p.route + rc + 1u) & MANTA_EDGE_MASK;
       const uint32_t lb2 = __ldg(p.lane_base + e2);
-      if (win_it && tgt == lb2) {
-        const unsigned long long dk = __ldcg(p.dep_key + e2);
-        if ((uint32_t)(dk >> 32) == tag && (uint32_t)dk < vid) win_it = false;
-      }
-      const float x = __ldcg(p.x + s);
-      const uint32_t cell = (uint32_t)(int)floorf(x);
-      p.pcell[s] = em.row0 + (uint32_t)lane * stride + cell;
+      const unsigned long long dk = __ldcg(p.dep_key + e2);
+      const EdgeMeta em2 = load_em(p, e2);
+      Veh w = load_veh(p, s);
+      const int lane = (int)(w.ld & 0xFFu);
+      const EdgeMeta em = w.em;
+      const uint32_t stride = stride_of(cells_of(em.cnl));
+      bool win_it = min_competitor(p, o0, o1, gown, tgt, tag) > w.id;
+      if (win_it && tgt == lb2 && (uint32_t)(dk >> 32) == tag && (uint32_t)dk < w.id) win_it = false;
+      const uint32_t cell = (uint32_t)(int)floorf(w.x);
+      w.pcell = em.row0 + (uint32_t)lane * stride + cell;
       float xf, vf;
       uint32_t ef;
       if (win_it) {
         const int C = (int)cells_of(em.cnl);
-        if (__ldg(p.ntype + n) == 1 && ldv(p.permit + n) == vid) p.permit[n] = MANTA_NONE;
-        atomicAdd(p.exitc + e, 1u);
+        if (__ldg(p.ntype + n) == 1 && ldv(p.permit + n) == w.id) p.permit[n] = MANTA_NONE;
+        atomicAdd(p.exitc + w.e, 1u);
         atomicAdd(p.entry + e2, 1u);
         xf = __ldcg(p.req_x + i) - __int2float_rn(C);
         vf = __ldcg(p.req_v + i);
-        const EdgeMeta em2 = p.em[e2];
         const uint32_t l2 = tgt - lb2;
-        p.e[s] = e2; p.rc[s] = rc + 1u;
-        p.ld[s] = l2;
+        w.e = e2; w.rc = w.rc + 1u;
+        w.ld = l2;
+        w.em = em2;
         nxt[em2.row0 + l2 * stride_of(cells_of(em2.cnl)) + (uint32_t)(int)floorf(xf)] = speed_code(vf);
         ef = e2;
       } else {
         const int C = (int)cells_of(em.cnl);
-        xf = fmaxf(x, __int2float_rn(C - 1));
+        xf = fmaxf(w.x, __int2float_rn(C - 1));
         vf = 0.0f;
-        p.ld[s] = (uint32_t)lane | (__ldcg(p.req_dw + i) << 8);
+        w.ld = (uint32_t)lane | (__ldcg(p.req_dw + i) << 8);
         nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xf)] = speed_code(vf);
-        ef = e;
+        ef = w.e;
       }
-      p.x[s] = xf; p.v[s] = vf;
+      w.x = xf; w.v = vf;
+      store_veh(p, s, w);
       if (win >= 0) {
         const size_t o = (size_t)win * p.E + ef;
         atomicAdd(p.ssum + o, (unsigned long long)(vf * 1048576.0f));
         atomicAdd(p.scnt + o, 1u);
       }
-      const uint32_t in = warp_append(&ctl->n_act[cb ^ 1], true);
-      act_n[in] = s;
     }
     // departures: the queue head wins unless a crossing with a lower id targets lane 0
     for (uint32_t i = gtid; i < ndep; i += gsz) {
@@ -584,14 +748,9 @@ __global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
       const uint32_t j = (uint32_t)dk;
       bool won = (uint32_t)(dk >> 32) == tag;
       if (won) {
-        const uint32_t lb = __ldg(p.lane_base + e);
         const uint32_t n = __ldg(p.esrc + e);
-        const uint32_t o0 = __ldg(p.nin_off + n), o1 = __ldg(p.nin_off + n + 1);
-        for (uint32_t o = o0; o < o1; ++o) {
-          const uint32_t g = __ldg(p.nin + o);
-          const unsigned long long key = __ldcg(p.req_key + g);
-          if ((uint32_t)(key >> 32) == tag && __ldcg(p.req_tgt + g) == lb && (uint32_t)key < j) { won = false; break; }
-        }
+        won = min_competitor(p, __ldg(p.nin_off + n), __ldg(p.nin_off + n + 1), MANTA_NONE, __ldg(p.lane_base + e),
+                             tag) > j;
       }
       uint32_t s = MANTA_NONE;
       bool keep = true;
@@ -599,17 +758,19 @@ __global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
         const uint32_t wi = atomicAdd(&ctl->n_depwin, 1u);
         const uint32_t fc = ldv(&ctl->free_count);
         s = wi < fc ? __ldcg(p.freel + (fc - 1u - wi)) : ldv(&ctl->n_slots) + (wi - fc);
-        const uint32_t r0 = __ldg(p.route_off + j);
-        p.x[s] = 0.0f; p.v[s] = 0.0f; p.id[s] = j; p.rc[s] = r0; p.rend[s] = __ldg(p.route_off + j + 1u);
-        p.e[s] = e; p.ld[s] = 0u; p.pcell[s] = MANTA_NONE;
-        nxt[p.em[e].row0] = speed_code(0.0f);
+        const EdgeMeta em = load_em(p, e);
+        Veh w;
+        w.x = 0.0f; w.v = 0.0f; w.id = j; w.rc = __ldg(p.route_off + j); w.rend = __ldg(p.route_off + j + 1u);
+        w.e = e; w.ld = 0u; w.pcell = MANTA_NONE; w.em = em;
+        store_veh(p, s, w);
+        nxt[em.row0] = speed_code(0.0f);
         atomicAdd(p.entry + e, 1u);
         c_dep++;
         p.q_pos[e] = __ldcg(p.q_pos + e) + 1u;
         keep = atomicSub(p.pending + e, 1u) > 1u;
       }
       const uint32_t ia = warp_append(&ctl->n_act[cb ^ 1], won);
-      if (won) act_n[ia] = s;
+      if (won) act[ia] = s;
       const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], keep);
       if (keep) dep_n[id2] = e;
     }
@@ -618,21 +779,17 @@ __global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
     for (uint32_t i = gtid; i < narr; i += gsz) cur[__ldcg(p.arr + i)] = (uint8_t)MANTA_EMPTY;
     // trips due at step k + 1 join their edge's departure queue
     {
-      const uint32_t lo = ldv(&ctl->due_pos);
-      uint32_t a = lo, b = p.n_trips;
-      while (a < b) {
-        const uint32_t m = (a + b) >> 1;
-        if ((int64_t)__ldg(p.due_step + m) <= k + 1) a = m + 1u; else b = m;
-      }
-      if (gtid == 0) ctl->due_next = a;
-      for (uint32_t i = lo + gtid; i < a; i += gsz) {
+      const uint32_t lo = ldv(&ctl->due_pos), hi = ldv(&ctl->due_hi);
+      for (uint32_t i = lo + gtid; i < hi; i += gsz) {
         const uint32_t e = __ldg(p.due_edge + i);
         const bool first = atomicAdd(p.pending + e, 1u) == 0u;
         const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], first);
         if (first) dep_n[id2] = e;
       }
     }
-    if (!grid_sync(ctl, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+    if (gtid == 0) ctl->n_compact = 0u;
+    if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
+    if (timer) { const uint64_t t = globaltimer(); ph[3] += t - tp; tp = t; }
   }
   // flush counters
   atomicAdd(&s_cnt[CNT_UPD], (unsigned long long)c_upd);
@@ -645,5 +802,6 @@ __global__ void __launch_bounds__(kBlock) manta_step_kernel(Params p) {
   atomicAdd(&s_cnt[CNT_ARR], (unsigned long long)c_arr);
   __syncthreads();
   if (threadIdx.x < CNT_N && s_cnt[threadIdx.x]) atomicAdd(&ctl->cnt[threadIdx.x], s_cnt[threadIdx.x]);
+  if (timer)
+    for (int q = 0; q < 4; ++q) ctl->phase_ns[q] += ph[q];
 }
-

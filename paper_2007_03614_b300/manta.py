@@ -12,7 +12,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmanta.so")
+# MANTA_LIBRARY may point at another build of the same library (e.g. a tuning variant).
+LIB_PATH = os.environ.get("MANTA_LIBRARY") or os.path.join(_HERE, "libmanta.so")
 
 OK, E_INVALID, E_ROUTE, E_STATE, E_OOM, E_CUDA, E_TIMEOUT, E_DEVICE = 0, -1, -2, -3, -4, -5, -6, -7
 NODE_GREEN, NODE_STOP, NODE_SIGNAL = 0, 1, 2
@@ -46,7 +47,8 @@ class MantaStats(C.Structure):
 # Every entry point declared in include/manta.h.
 EXPORTS = ("manta_default_config", "manta_create", "manta_load_trips", "manta_step", "manta_stats",
            "manta_edge_counters", "manta_snapshot", "manta_lane_map", "manta_lane_map_bytes",
-           "manta_destroy", "manta_last_error", "manta_selftest_barrier_timeout", "manta_run_noalloc")
+           "manta_destroy", "manta_last_error", "manta_selftest_barrier_timeout", "manta_run_noalloc",
+           "manta_phase_times")
 
 _lib = None
 
@@ -88,6 +90,8 @@ def load_library():
         lib.manta_run_noalloc.argtypes = ([C.c_int32, C.c_int32] + [P] * 12 + [C.POINTER(MantaConfig), C.c_int64]
                                           + [P] * 3 + [C.c_int64, P, C.POINTER(MantaStats), C.c_int64,
                                                        C.POINTER(C.c_int64)] + [P] * 7)
+        lib.manta_phase_times.restype = C.c_int
+        lib.manta_phase_times.argtypes = [P, P]
         lib.manta_selftest_barrier_timeout.restype = C.c_int
         lib.manta_selftest_barrier_timeout.argtypes = [C.c_int32, P]
         _lib = lib
@@ -196,6 +200,11 @@ class Sim:
                                                                    ("x", "v", "edge", "lane", "id", "dwell",
                                                                     "route_pos")]))
         return {k: a[:cnt.value] for k, a in out.items()}
+
+    def phase_times_ms(self) -> np.ndarray:
+        out = np.zeros(4, np.float64)
+        _check(self._lib.manta_phase_times(self._h, _p(out)))
+        return out
 
     def lane_map(self) -> np.ndarray:
         nb = int(self._lib.manta_lane_map_bytes(self._h))

@@ -41,7 +41,7 @@ class _Net(C.Structure):
                 ("edge_green_start", C.POINTER(C.c_int16)), ("edge_green_len", C.POINTER(C.c_int16)),
                 ("n_conn", C.c_int64), ("conn_lane_mask", C.POINTER(C.c_uint32)),
                 ("node_i", C.POINTER(C.c_int32)), ("node_j", C.POINTER(C.c_int32)),
-                ("edge_dir", C.POINTER(C.c_uint8))]
+                ("edge_dir", C.POINTER(C.c_uint8)), ("node_trip_ok", C.POINTER(C.c_uint8))]
 
 
 class _LatticeParams(C.Structure):
@@ -52,7 +52,8 @@ class _LatticeParams(C.Structure):
                 ("len_min_m", C.c_double), ("len_max_m", C.c_double),
                 ("speed_mps", C.c_float * 3), ("lanes", C.c_uint8 * 3),
                 ("signal_cycle_steps", C.c_int32), ("signal_green_steps", C.c_int32),
-                ("signals_at", C.c_int32), ("all_stop", C.c_int32), ("seed", C.c_uint64)]
+                ("signals_at", C.c_int32), ("all_stop", C.c_int32), ("limited_access", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 class _Trips(C.Structure):
@@ -115,6 +116,7 @@ class Network:
     node_i: np.ndarray | None = None
     node_j: np.ndarray | None = None
     edge_dir: np.ndarray | None = None
+    node_trip_ok: np.ndarray | None = None
     meta: dict = field(default_factory=dict)
 
     @property
@@ -148,7 +150,7 @@ def lattice(nx, ny, *, arterial_every=0, freeway_every=0, local_keep=1.0,
             len_median_m=100.0, len_sigma=0.0, len_min_m=20.0, len_max_m=2000.0,
             speed_mps=(11.111, 19.444, 29.167), lanes=(1, 2, 4),
             signal_cycle_steps=120, signal_green_steps=60, signals_at=0, all_stop=False,
-            seed=1) -> Network:
+            limited_access=False, seed=1) -> Network:
     lib = _load()
     p = _LatticeParams()
     p.nx, p.ny = nx, ny
@@ -160,6 +162,7 @@ def lattice(nx, ny, *, arterial_every=0, freeway_every=0, local_keep=1.0,
         p.lanes[i] = lanes[i]
     p.signal_cycle_steps, p.signal_green_steps = signal_cycle_steps, signal_green_steps
     p.signals_at, p.all_stop, p.seed = signals_at, int(all_stop), seed
+    p.limited_access = int(limited_access)
     h = lib.synth_lattice(C.byref(p))
     n = h.contents
     try:
@@ -177,7 +180,7 @@ def lattice(nx, ny, *, arterial_every=0, freeway_every=0, local_keep=1.0,
             edge_green_len=_copy(n.edge_green_len, E, np.int16),
             conn_lane_mask=_copy(n.conn_lane_mask, n.n_conn, np.uint32),
             node_i=_copy(n.node_i, N, np.int32), node_j=_copy(n.node_j, N, np.int32),
-            edge_dir=_copy(n.edge_dir, E, np.uint8))
+            edge_dir=_copy(n.edge_dir, E, np.uint8), node_trip_ok=_copy(n.node_trip_ok, N, np.uint8))
     finally:
         lib.synth_net_free(h)
     net.meta = dict(kind="lattice", nx=nx, ny=ny, seed=seed)
@@ -201,6 +204,8 @@ def make_trips(net: Network, n_trips, *, od_model="uniform", zones=(20, 25), poo
     cn.edge_src, cn.edge_dst = ptr(net.edge_src, C.c_int32), ptr(net.edge_dst, C.c_int32)
     cn.edge_length_m = ptr(net.edge_length_m.astype(np.float32), C.c_float)
     cn.edge_speed_mps = ptr(net.edge_speed_limit_mps.astype(np.float32), C.c_float)
+    tok = net.node_trip_ok if net.node_trip_ok is not None else np.ones(net.n_nodes, np.uint8)
+    cn.node_trip_ok = ptr(tok.astype(np.uint8), C.c_uint8)
     ni = net.node_i if net.node_i is not None else np.zeros(net.n_nodes, np.int32)
     nj = net.node_j if net.node_j is not None else np.zeros(net.n_nodes, np.int32)
     cn.node_i, cn.node_j = ptr(ni.astype(np.int32), C.c_int32), ptr(nj.astype(np.int32), C.c_int32)
@@ -249,22 +254,30 @@ METRO_SIDE = 482
 
 
 def metro_network(seed=2, side=METRO_SIDE) -> Network:
-    """Metro-shaped synthetic network: perturbed-free lattice with local (1 lane,
-    40 km/h), arterial every 8th line (2 lanes, 70 km/h) and freeway every 32nd
-    line (4 lanes, 105 km/h); lognormal lengths (median 120 m, sigma 0.8);
-    local segments thinned to about 550k directed edges; fixed-time signals at
-    arterial crossings."""
-    return lattice(side, side, arterial_every=8, freeway_every=32, local_keep=0.545,
+    """Metro-shaped synthetic network: lattice with local (1 lane, 40 km/h),
+    arterial every 8th line (2 lanes, 70 km/h) and limited-access freeway
+    every 32nd line (4 lanes, 105 km/h; local streets pass over it, arterials
+    and freeways meet it at interchanges); lognormal lengths (median 120 m,
+    sigma 0.8); local segments thinned to about 550k directed edges;
+    fixed-time signals at arterial crossings; no trip starts or ends on a
+    freeway."""
+    return lattice(side, side, arterial_every=8, freeway_every=32, local_keep=0.57,
                    len_median_m=120.0, len_sigma=0.8, len_min_m=20.0, len_max_m=2000.0,
                    speed_mps=(11.111, 19.444, 29.167), lanes=(1, 2, 4),
-                   signals_at=1, seed=seed)
+                   signals_at=1, limited_access=True, seed=seed)
+
+
+# Decay length of the gravity model: 5.4 km makes the mean route length on the
+# metro-shaped network about 11.5 km, the mean trip distance the paper reports
+# for its routes (Section IV-B, 11.3 km).
+METRO_BETA_KM = 5.4
 
 
 def metro_trips(net: Network, n_trips=3_200_000, seed=2, t_lo_s=5 * 3600.0, t_hi_s=12 * 3600.0,
                 n_threads=None) -> Trips:
-    """Gravity OD over 20x25 zones (lognormal masses, exp(-d/10 km)), origins from
-    a pool of 16 nodes per zone, destinations uniform in the zone; departures
-    normal(08:00, 75 min) truncated to [05:00, 12:00)."""
+    """Gravity OD over 20x25 zones (lognormal masses, exp(-d / 5.4 km)), origins
+    from a pool of 16 nodes per zone, destinations uniform in the zone;
+    departures normal(08:00, 75 min) truncated to [05:00, 12:00)."""
     return make_trips(net, n_trips, od_model="gravity", zones=(20, 25), pool_per_zone=16,
-                      spacing_km=0.15, beta_km=10.0, depart="normal", t_lo_s=t_lo_s, t_hi_s=t_hi_s,
+                      spacing_km=0.15, beta_km=METRO_BETA_KM, depart="normal", t_lo_s=t_lo_s, t_hi_s=t_hi_s,
                       mean_s=8 * 3600.0, sd_s=75 * 60.0, seed=seed, n_threads=n_threads)

@@ -60,6 +60,7 @@ typedef struct {
   uint32_t *conn_lane_mask;
   int32_t *node_i, *node_j;       /* lattice coordinates of each kept node */
   uint8_t *edge_dir;              /* 0 +i, 1 +j, 2 -i, 3 -j                */
+  uint8_t *node_trip_ok;          /* 1 if trips may start or end at the node */
 } synth_net;
 
 typedef struct {
@@ -72,6 +73,8 @@ typedef struct {
   int32_t signal_cycle_steps, signal_green_steps;
   int32_t signals_at;     /* 0 none, 1 arterial x arterial (incl. freeway rows excluded), 2 interior nodes */
   int32_t all_stop;       /* 1: every node is a flashing red (stop) node       */
+  int32_t limited_access; /* 1: local streets pass over freeways (no junction);
+                             only arterial and freeway crossings are interchanges */
   uint64_t seed;
 } synth_lattice_params;
 
@@ -87,7 +90,7 @@ SYNTH_API void synth_net_free(synth_net *n) {
   free(n->edge_length_m); free(n->edge_speed_mps); free(n->node_type);
   free(n->node_cycle); free(n->node_offset); free(n->edge_green_start);
   free(n->edge_green_len); free(n->conn_lane_mask); free(n->node_i); free(n->node_j);
-  free(n->edge_dir); free(n);
+  free(n->edge_dir); free(n->node_trip_ok); free(n);
 }
 
 SYNTH_API synth_net *synth_lattice(const synth_lattice_params *p) {
@@ -111,7 +114,59 @@ SYNTH_API synth_net *synth_lattice(const synth_lattice_params *p) {
     if (L > p->len_max_m) L = p->len_max_m;
     slen[s] = (float)L;
   }
-  /* largest connected component by BFS over kept segments */
+  /* Per node and direction (0 +i, 1 +j, 2 -i, 3 -j): neighbour node and
+     segment.  With limited access a local street crossing a freeway becomes
+     one overpass segment that skips the freeway node. */
+  const int64_t NSEG = NH + NV + 2 * (int64_t)nx * ny / 1 + 1;
+  slen = (float *)realloc(slen, sizeof(float) * (size_t)NSEG);
+  scls = (uint8_t *)realloc(scls, (size_t)NSEG);
+  int64_t nseg = NH + NV;
+  int64_t *nbn = (int64_t *)malloc(sizeof(int64_t) * 4 * (size_t)NN);
+  int64_t *nbs = (int64_t *)malloc(sizeof(int64_t) * 4 * (size_t)NN);
+  for (int64_t v = 0; v < NN; ++v) {
+    int32_t i = (int32_t)(v % nx), j = (int32_t)(v / nx);
+    int64_t sg[4], nb[4];
+    sg[0] = i + 1 < nx ? (int64_t)j * (nx - 1) + i : -1;       nb[0] = v + 1;
+    sg[1] = j + 1 < ny ? NH + (int64_t)j * nx + i : -1;        nb[1] = v + nx;
+    sg[2] = i > 0 ? (int64_t)j * (nx - 1) + (i - 1) : -1;      nb[2] = v - 1;
+    sg[3] = j > 0 ? NH + (int64_t)(j - 1) * nx + i : -1;       nb[3] = v - nx;
+    for (int d = 0; d < 4; ++d) {
+      const int ok = sg[d] >= 0 && keep[sg[d]];
+      nbn[v * 4 + d] = ok ? nb[d] : -1;
+      nbs[v * 4 + d] = ok ? sg[d] : -1;
+    }
+  }
+  uint8_t *trip_ok = (uint8_t *)malloc((size_t)NN);
+  for (int64_t v = 0; v < NN; ++v) {
+    int32_t i = (int32_t)(v % nx), j = (int32_t)(v / nx);
+    trip_ok[v] = !(p->limited_access && (seg_class(p, i) == 2 || seg_class(p, j) == 2));
+  }
+  if (p->limited_access) {
+    for (int64_t v = 0; v < NN; ++v) {
+      int32_t i = (int32_t)(v % nx), j = (int32_t)(v / nx);
+      /* freeway row j crossed by a local column i, or freeway column i crossed by a local row j */
+      for (int axis = 0; axis < 2; ++axis) {
+        const int fw = axis == 0 ? seg_class(p, j) == 2 : seg_class(p, i) == 2;
+        const int loc = axis == 0 ? seg_class(p, i) == 0 : seg_class(p, j) == 0;
+        if (!fw || !loc) continue;
+        const int dp = axis == 0 ? 1 : 0, dm = dp + 2;        /* +j/-j across a row, +i/-i across a column */
+        const int64_t up = nbn[v * 4 + dp], dn = nbn[v * 4 + dm];
+        const int64_t su = nbs[v * 4 + dp], sd = nbs[v * 4 + dm];
+        nbn[v * 4 + dp] = nbn[v * 4 + dm] = -1;
+        nbs[v * 4 + dp] = nbs[v * 4 + dm] = -1;
+        if (up >= 0) { nbn[up * 4 + dm] = -1; nbs[up * 4 + dm] = -1; }
+        if (dn >= 0) { nbn[dn * 4 + dp] = -1; nbs[dn * 4 + dp] = -1; }
+        if (up >= 0 && dn >= 0) {
+          const int64_t o = nseg++;
+          slen[o] = slen[su] + slen[sd];
+          scls[o] = 0;
+          nbn[dn * 4 + dp] = up; nbs[dn * 4 + dp] = o;
+          nbn[up * 4 + dm] = dn; nbs[up * 4 + dm] = o;
+        }
+      }
+    }
+  }
+  /* largest connected component by BFS */
   int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * (size_t)NN);
   int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)NN);
   for (int64_t v = 0; v < NN; ++v) comp[v] = -1;
@@ -120,14 +175,11 @@ SYNTH_API synth_net *synth_lattice(const synth_lattice_params *p) {
     if (comp[s0] >= 0) continue;
     int64_t qh = 0, qt = 0; queue[qt++] = (int32_t)s0; comp[s0] = ncomp;
     while (qh < qt) {
-      int32_t v = queue[qh++]; int32_t i = v % nx, j = v / nx;
-      int64_t segs[4]; int32_t nb[4];
-      segs[0] = i + 1 < nx ? (int64_t)j * (nx - 1) + i : -1;       nb[0] = v + 1;
-      segs[1] = j + 1 < ny ? NH + (int64_t)j * nx + i : -1;        nb[1] = v + nx;
-      segs[2] = i > 0 ? (int64_t)j * (nx - 1) + (i - 1) : -1;      nb[2] = v - 1;
-      segs[3] = j > 0 ? NH + (int64_t)(j - 1) * nx + i : -1;       nb[3] = v - nx;
-      for (int d = 0; d < 4; ++d)
-        if (segs[d] >= 0 && keep[segs[d]] && comp[nb[d]] < 0) { comp[nb[d]] = ncomp; queue[qt++] = nb[d]; }
+      int32_t v = queue[qh++];
+      for (int d = 0; d < 4; ++d) {
+        const int64_t w = nbn[(int64_t)v * 4 + d];
+        if (w >= 0 && comp[w] < 0) { comp[w] = ncomp; queue[qt++] = (int32_t)w; }
+      }
     }
     if (qt > best_size) { best_size = qt; best = ncomp; }
     ++ncomp;
@@ -150,24 +202,21 @@ SYNTH_API synth_net *synth_lattice(const synth_lattice_params *p) {
       out->node_type = (uint8_t *)calloc((size_t)nn, 1);
       out->node_cycle = (int32_t *)calloc((size_t)nn, 4); out->node_offset = (int32_t *)calloc((size_t)nn, 4);
       out->node_i = (int32_t *)malloc(4 * (size_t)nn); out->node_j = (int32_t *)malloc(4 * (size_t)nn);
+      out->node_trip_ok = (uint8_t *)malloc((size_t)nn);
     }
     int64_t e = 0;
     for (int64_t v = 0; v < NN; ++v) {
       if (nid[v] < 0) continue;
       int32_t i = (int32_t)(v % nx), j = (int32_t)(v / nx);
-      if (pass == 1) { out->node_i[nid[v]] = i; out->node_j[nid[v]] = j; }
-      int64_t segs[4]; int64_t nb[4];
-      segs[0] = i + 1 < nx ? (int64_t)j * (nx - 1) + i : -1;       nb[0] = v + 1;
-      segs[1] = j + 1 < ny ? NH + (int64_t)j * nx + i : -1;        nb[1] = v + nx;
-      segs[2] = i > 0 ? (int64_t)j * (nx - 1) + (i - 1) : -1;      nb[2] = v - 1;
-      segs[3] = j > 0 ? NH + (int64_t)(j - 1) * nx + i : -1;       nb[3] = v - nx;
+      if (pass == 1) { out->node_i[nid[v]] = i; out->node_j[nid[v]] = j; out->node_trip_ok[nid[v]] = trip_ok[v]; }
       for (int d = 0; d < 4; ++d) {
-        if (segs[d] < 0 || !keep[segs[d]] || nid[nb[d]] < 0) continue;
+        const int64_t w = nbn[v * 4 + d], sgi = nbs[v * 4 + d];
+        if (w < 0 || nid[w] < 0) continue;
         if (pass == 1) {
-          int c = scls[segs[d]];
-          out->edge_src[e] = nid[v]; out->edge_dst[e] = nid[nb[d]];
+          int c = scls[sgi];
+          out->edge_src[e] = nid[v]; out->edge_dst[e] = nid[w];
           out->edge_class[e] = (uint8_t)c; out->edge_lanes[e] = p->lanes[c];
-          out->edge_speed_mps[e] = p->speed_mps[c]; out->edge_length_m[e] = slen[segs[d]];
+          out->edge_speed_mps[e] = p->speed_mps[c]; out->edge_length_m[e] = slen[sgi];
           out->edge_dir[e] = (uint8_t)d;
         }
         ++e;
@@ -225,6 +274,7 @@ SYNTH_API synth_net *synth_lattice(const synth_lattice_params *p) {
     }
     free(out_off);
     free(keep); free(slen); free(scls); free(comp); free(queue); free(nid);
+    free(nbn); free(nbs); free(trip_ok);
     return out;
   }
   return NULL;
@@ -410,10 +460,15 @@ SYNTH_API synth_trips *synth_make_trips(const synth_net *net, const synth_trip_p
   t->depart_time_s = (float *)malloc(sizeof(float) * (size_t)(nt ? nt : 1));
   rng_t r = { p->seed * 0xD1B54A32D192ED03ULL + 777 };
   const int32_t nn = net->n_nodes;
+  /* trip ends only at nodes flagged for it (not on limited-access freeways) */
+  int32_t *ends = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);
+  int32_t n_ends = 0;
+  for (int32_t n = 0; n < nn; ++n)
+    if (!net->node_trip_ok || net->node_trip_ok[n]) ends[n_ends++] = n;
   if (p->od_model == 0) {
     for (int64_t k = 0; k < nt; ++k) {
-      int32_t o = (int32_t)rng_below(&r, (uint64_t)nn), d;
-      do { d = (int32_t)rng_below(&r, (uint64_t)nn); } while (d == o && nn > 1);
+      int32_t o = ends[rng_below(&r, (uint64_t)n_ends)], d;
+      do { d = ends[rng_below(&r, (uint64_t)n_ends)]; } while (d == o && n_ends > 1);
       t->origin[k] = o; t->dest[k] = d;
     }
   } else {
@@ -423,7 +478,8 @@ SYNTH_API synth_trips *synth_make_trips(const synth_net *net, const synth_trip_p
     const int32_t ZX = p->zones_x, ZY = p->zones_y, NZ = ZX * ZY;
     int32_t *zone = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);
     int64_t *zoff = (int64_t *)calloc((size_t)NZ + 1, sizeof(int64_t));
-    for (int32_t n = 0; n < nn; ++n) {
+    for (int32_t q = 0; q < n_ends; ++q) {
+      const int32_t n = ends[q];
       int32_t zx = (int32_t)((int64_t)net->node_i[n] * ZX / (maxi + 1));
       int32_t zy = (int32_t)((int64_t)net->node_j[n] * ZY / (maxj + 1));
       zone[n] = zy * ZX + zx; zoff[zone[n] + 1]++;
@@ -432,7 +488,7 @@ SYNTH_API synth_trips *synth_make_trips(const synth_net *net, const synth_trip_p
     int32_t *znodes = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);
     int64_t *zf = (int64_t *)malloc(sizeof(int64_t) * (size_t)NZ);
     memcpy(zf, zoff, sizeof(int64_t) * (size_t)NZ);
-    for (int32_t n = 0; n < nn; ++n) znodes[zf[zone[n]]++] = n;
+    for (int32_t q = 0; q < n_ends; ++q) znodes[zf[zone[ends[q]]]++] = ends[q];
     free(zf);
     /* origin pools: pool_per_zone nodes drawn uniformly from each zone */
     int32_t P = p->pool_per_zone;
@@ -465,7 +521,7 @@ SYNTH_API synth_trips *synth_make_trips(const synth_net *net, const synth_trip_p
       int32_t d;
       int tries = 0;
       do { d = znodes[zoff[zb] + (int64_t)rng_below(&r, (uint64_t)cnt)]; } while (d == o && ++tries < 64);
-      if (d == o) d = (o + 1) % nn;
+      if (d == o) d = ends[(rng_below(&r, (uint64_t)n_ends))];
       t->origin[k] = o; t->dest[k] = d;
     }
     free(zone); free(zoff); free(znodes); free(pool); free(mass); free(cx); free(cy); free(cum);
@@ -481,6 +537,7 @@ SYNTH_API synth_trips *synth_make_trips(const synth_net *net, const synth_trip_p
     }
     t->depart_time_s[k] = (float)s;
   }
+  free(ends);
   route_all(nn, net->n_edges, net->edge_src, net->edge_dst, net->edge_length_m, net->edge_speed_mps, t,
             p->n_threads);
   return t;

@@ -228,10 +228,9 @@ class Naive:
             blocked = self.ntype[n] == 2 and not self.green(e, k)
             if si == 0:
                 stop_np = self.ntype[n] == 1 and self.permit[n] != v.id
-                wrong = not ((self.mask[(e, nxt)] >> l) & 1)
                 out["reached_own"] = True
-                out["stop_only"] = stop_np and not wrong
-                blocked = blocked or stop_np or wrong
+                out["stop_only"] = stop_np
+                blocked = blocked or stop_np
             elif self.ntype[n] == 1:
                 blocked = True
             if blocked:

@@ -401,21 +401,28 @@ def test_mandatory_change_probability_eq2():
         assert int(sn["lane"][0]) == (0 if expect else 1)
 
 
-def test_wrong_lane_holds_at_stop_line():
-    """A vehicle in a lane that may not take its next turn stops at the end of
-    the edge instead of crossing (virtual leader at the stop line)."""
-    edges = [(0, 1, 2, 100.0, 13.889, 0), (1, 2, 1, 200.0, 13.889, 0)]
-    net = nets.network(3, edges, conn=[1])
+def test_wrong_lane_is_a_late_merge_not_a_stop():
+    """A vehicle that reaches the node still in a lane not allowed for its next
+    edge is not held there (that would deadlock two vehicles needing each
+    other's lanes): it enters lane min(l, lanes - 1) of the next edge."""
+    edges = [(0, 1, 2, 100.0, 13.889, 0), (1, 2, 2, 200.0, 13.889, 0)]
+    net = nets.network(3, edges, conn=[1])          # only lane 0 may continue
     tr = nets.trips([[0, 1], [0, 1]], [1e7, 1e7])
     s = O.OracleSim(net)
     nets.load(s, tr)
-    s.place(0, 0, 1, 50.0, 10.0)
-    s.place(1, 0, 0, 90.0, 0.0)     # blocks lane 0 around the end for a while
-    for _ in range(30):
+    s.place(0, 0, 1, 60.0, 10.0)                    # lane 1 (wrong), moving
+    s.place(1, 0, 0, 60.0, 10.0)                    # lane 0 alongside all the way: no room to change
+    crossed_from = None
+    for _ in range(20):
+        prev = s.snapshot()
         s.step(1)
+        s.check()
         sn = s.snapshot()
         byid = {int(i): j for j, i in enumerate(sn["id"])}
+        pj = {int(i): j for j, i in enumerate(prev["id"])}
         j = byid[0]
-        if sn["lane"][j] == 1:
-            assert sn["edge"][j] == 0 and sn["x"][j] <= 99.0
-        s.check()
+        assert sn["v"][j] > 0.0                      # never held at the stop line
+        if sn["edge"][j] == 1 and crossed_from is None:
+            crossed_from = int(prev["lane"][pj[0]])
+    assert crossed_from == 1                         # still in the disallowed lane at the node
+    assert sn["edge"][byid[0]] == 1 and sn["lane"][byid[0]] == 1
