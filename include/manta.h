@@ -143,6 +143,16 @@ MANTA_API manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int3
 MANTA_API manta_status manta_load_trips(manta_sim *sim, int64_t n_trips, const int64_t *route_off,
                               const int32_t *route_edges, const float *depart_time_s);
 
+/* Incident lane closure: lane `lane` of `edge` is closed during absolute steps
+ * [k0, k1) (a later call for the same lane replaces the window).  While
+ * closed, the lane holds a stationary obstacle from mid-edge (cell C_e / 2)
+ * on, so vehicles behind it stop short of it unless they change lanes (the
+ * closure makes that change mandatory, with the Eq. 2 probability taken at the
+ * distance to the obstacle); no vehicle changes into the lane, enters it from
+ * upstream or departs onto it.  Must be called before manta_load_trips.
+ * Errors: MANTA_E_INVALID, MANTA_E_STATE (trips already loaded), MANTA_E_CUDA. */
+MANTA_API manta_status manta_set_lane_closure(manta_sim *sim, int32_t edge, int32_t lane, int64_t k0, int64_t k1);
+
 /* Enqueues n_steps >= 0 time steps (Section II-D update) on the stream and
  * returns.  A device error from earlier work is reported here only if it is
  * already known on the host; otherwise at the next synchronising call.

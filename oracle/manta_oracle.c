@@ -96,6 +96,8 @@ typedef struct {
   int64_t *conn_off; uint32_t *conn;       /* lane masks per (in, out) pair    */
   int64_t *inl_off; int64_t *inl;          /* in-lanes of each node, (edge, lane) order */
   uint32_t *permit; int32_t *rr;
+  int64_t *clo_k0, *clo_k1;                /* closure window [k0, k1) of each lane, empty if k0 >= k1 */
+  int stepped;
   float *mtab; int32_t mtab_n;             /* Eq. 2 probability by distance in cells */
   /* trips */
   int64_t NT;
@@ -160,6 +162,13 @@ static int is_green(const osim *S, int32_t e, int64_t k) {
   return m >= S->gs[e] && m < (int64_t)S->gs[e] + S->gl[e];
 }
 
+/* Incident lane closure: lane l of edge e is closed at step k; from mid-edge
+ * (cell C_e / 2) on it holds a stationary obstacle. */
+static int lane_closed(const osim *S, int32_t e, int32_t l, int64_t k) {
+  int64_t g = S->lane_base[e] + l;
+  return S->clo_k0[g] <= k && k < S->clo_k1[g];
+}
+
 static void set_err(char *err, int errlen, const char *msg) {
   if (err && errlen > 0) { strncpy(err, msg, (size_t)errlen - 1); err[errlen - 1] = 0; }
 }
@@ -171,6 +180,7 @@ OR_API void oracle_destroy(osim *S) {
   free(S->lane_base); free(S->row_off); free(S->map_cur); free(S->map_nxt);
   free(S->out_off); free(S->out_e); free(S->conn_off); free(S->conn);
   free(S->inl_off); free(S->inl); free(S->permit); free(S->rr); free(S->mtab);
+  free(S->clo_k0); free(S->clo_k1);
   free(S->route_off); free(S->route); free(S->rmask); free(S->dstep); free(S->V);
   free(S->q_off); free(S->q_trip); free(S->q_head); free(S->on);
   free(S->entry); free(S->exitc); free(S->ssum); free(S->scnt); free(S->lc_tgt); free(S->best);
@@ -278,6 +288,7 @@ OR_API osim *oracle_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge
     free(f);
   }
   S->permit = malloc(4 * (size_t)N); S->rr = calloc((size_t)N, 4);
+  S->clo_k0 = calloc((size_t)(lanes ? lanes : 1), 8); S->clo_k1 = calloc((size_t)(lanes ? lanes : 1), 8);
   for (int32_t n = 0; n < N; ++n) S->permit[n] = NONE_ID;
   /* Eq. 2: m(x) = 1 for x <= x0, exp(-((x - x0)/lambda)^2) beyond; x = distance
      in metres to the end of the edge.  Evaluated once here in double. */
@@ -392,12 +403,27 @@ static int32_t lc_decide(osim *S, int64_t id) {
   const int32_t dir = (k & 1) ? -1 : 1;
   const int32_t lt = l + dir;
   if (lt < 0 || lt >= nl) return -1;
+  if (lane_closed(S, e, lt, k)) return -1;              /* never into a closed lane */
   const int32_t cell = (int32_t)floorf(V->x);
   const int has_next = (V->r + 1 < S->route_off[id + 1]);
-  const uint32_t mask = has_next ? S->rmask[V->r] : 0xFFu;
+  uint32_t mask = has_next ? S->rmask[V->r] : 0xFFu;
+  if (has_next) {
+    /* lanes whose continuation on the next edge is closed are not allowed either */
+    const int32_t e2 = S->route[V->r + 1];
+    uint32_t open = 0;
+    for (int32_t q = 0; q < nl; ++q) {
+      const int32_t q2 = q < S->nl[e2] - 1 ? q : S->nl[e2] - 1;
+      if (!lane_closed(S, e2, q2, k)) open |= 1u << q;
+    }
+    if (mask & open) mask &= open;
+  }
   const int ok_l = (mask >> l) & 1, ok_lt = (mask >> lt) & 1;
+  const int32_t obst = Ce / 2;
+  const int closed_here = lane_closed(S, e, l, k) && cell < obst;
   int mandatory = 0;
-  if (has_next && !ok_l) {
+  if (closed_here) {
+    mandatory = 2;                                       /* leave the closed lane before the obstacle */
+  } else if (has_next && !ok_l) {
     /* distance to the nearest allowed lane on each side */
     int32_t dp = 99, dm = 99;
     for (int32_t q = l + 1; q < nl; ++q) if ((mask >> q) & 1) { dp = q - l; break; }
@@ -411,8 +437,8 @@ static int32_t lc_decide(osim *S, int64_t id) {
   const float v = V->v;
   uint8_t *tr = row(S, S->map_cur, e, lt);
   if (mandatory) {
-    /* Eq. 2 probability at the distance to the end of the edge */
-    int32_t dist = Ce - 1 - cell;
+    /* Eq. 2 probability at the distance to the end of the edge (or to the obstacle) */
+    int32_t dist = mandatory == 2 ? obst - 1 - cell : Ce - 1 - cell;
     float u1 = rng_u(cf->seed, (uint64_t)id, k, 0);
     if (!(u1 < S->mtab[dist])) return -1;
   } else {
@@ -489,8 +515,15 @@ static scan_t leader_scan(osim *S, int64_t id) {
   for (;;) {
     const int64_t segC = S->C[se];
     const uint8_t *rw = row(S, S->map_cur, se, sl);
+    /* a closed own lane holds an obstacle from mid-edge on, for vehicles behind it */
+    const int64_t obst = (own && lane_closed(S, se, sl, S->k) && cell < segC / 2) ? segC / 2 : -1;
     while (p < base + segC) {
       if (p > limit) { res.kind = SC_FREE; S->st.cells_scanned += (uint64_t)H; return res; }
+      if (p == obst) {
+        res.kind = SC_VIRTUAL; res.cL = obst + L - 1; res.vL = 0.0f;
+        S->st.cells_scanned += (uint64_t)(obst - 1 - cell);
+        return res;
+      }
       uint8_t byte = rw[p - base];
       if (byte != EMPTY) {
         res.kind = SC_LEADER; res.cL = p; res.vL = speed_decode(byte);
@@ -506,6 +539,10 @@ static scan_t leader_scan(osim *S, int64_t id) {
     const int32_t n = S->dst[se], e2 = S->route[r + 1];
     int blocked = 0;
     if (S->ntype[n] == NODE_SIGNAL && !is_green(S, se, S->k)) blocked = 1;
+    {
+      const int32_t l2 = sl < S->nl[e2] - 1 ? sl : S->nl[e2] - 1;
+      if (lane_closed(S, e2, l2, S->k)) blocked = 1;       /* no entry into a closed lane */
+    }
     if (own) {
       int stop_np = (S->ntype[n] == NODE_STOP) && (S->permit[n] != (uint32_t)id);
       res.reached_own = 1;
@@ -534,6 +571,7 @@ OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
   const oracle_config *cf = &S->cfg;
   const int32_t L = cf->veh_len_cells;
   const float dt = cf->dt;
+  S->stepped = 1;
   upd_t *U = malloc(sizeof(upd_t) * (size_t)(S->NT ? S->NT : 1));
   int64_t *dep = malloc(sizeof(int64_t) * (size_t)S->E);  /* requesting trip per edge, -1 none */
   for (int64_t it = 0; it < n_steps; ++it) {
@@ -556,6 +594,7 @@ OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
       if (S->q_head[e] >= S->q_off[e + 1]) continue;
       int64_t j = S->q_trip[S->q_head[e]];
       if (S->dstep[j] > k) continue;
+      if (lane_closed(S, e, 0, k)) continue;
       int32_t need = L + (int32_t)ceilf(cf->s0[S->cls[e]]);
       if (need > S->C[e]) need = S->C[e];
       uint8_t *rw = row(S, S->map_cur, e, 0);
@@ -819,3 +858,13 @@ OR_API int oracle_check(osim *S, char *msg, int len) {
 }
 
 OR_API int64_t oracle_map_bytes(osim *S) { return S->map_bytes; }
+
+/* Close lane `lane` of edge `edge` during steps [k0, k1) (replaces an earlier
+ * window of that lane).  Only before the first step. */
+OR_API int oracle_set_lane_closure(osim *S, int32_t edge, int32_t lane, int64_t k0, int64_t k1) {
+  if (!S || edge < 0 || edge >= S->E || lane < 0 || lane >= S->nl[edge] || k1 < k0) return -1;
+  if (S->stepped) return -3;
+  int64_t g = S->lane_base[edge] + lane;
+  S->clo_k0[g] = k0; S->clo_k1[g] = k1;
+  return 0;
+}

@@ -105,6 +105,8 @@ def _load():
         lib.oracle_check.restype = C.c_int
         lib.oracle_check.argtypes = [P, C.c_char_p, C.c_int]
         lib.oracle_destroy.argtypes = [P]
+        lib.oracle_set_lane_closure.restype = C.c_int
+        lib.oracle_set_lane_closure.argtypes = [P, C.c_int32, C.c_int32, C.c_int64, C.c_int64]
         lib.oracle_splitmix64.restype = C.c_uint64
         lib.oracle_splitmix64.argtypes = [C.c_uint64]
         lib.oracle_rng_u.restype = C.c_float
@@ -217,6 +219,11 @@ class OracleSim:
         rc = self._lib.oracle_place(self._h, int(trip), int(route_pos), int(lane), float(x), float(v))
         if rc != 0:
             raise OracleError(f"place {rc}")
+
+    def set_lane_closure(self, edge, lane, k0, k1):
+        rc = self._lib.oracle_set_lane_closure(self._h, int(edge), int(lane), int(k0), int(k1))
+        if rc != 0:
+            raise OracleError(f"set_lane_closure {rc}")
 
     def check(self):
         msg = C.create_string_buffer(256)

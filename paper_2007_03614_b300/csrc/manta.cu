@@ -66,6 +66,8 @@ struct manta_sim {
   int64_t k = 0, n_trips = 0;
   uint32_t prime_hi = 0;
   std::vector<uint32_t> route_off_h;
+  std::vector<EdgeMeta> em_h;
+  std::vector<long long> clo_k0, clo_k1;
   int grid = 0;
 };
 
@@ -348,6 +350,16 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
     manta_destroy(S);
     return fail(MANTA_E_CUDA, "upload failed in manta_create: " + m);
   }
+  S->em_h = em;
+  S->clo_k0.assign(lanes_total ? lanes_total : 1, 0);
+  S->clo_k1.assign(lanes_total ? lanes_total : 1, 0);
+  long long *d_ck0 = dalloc<long long>(S, lanes_total, &ok);
+  long long *d_ck1 = dalloc<long long>(S, lanes_total, &ok);
+  if (!ok || !upload(S, d_ck0, S->clo_k0) || !upload(S, d_ck1, S->clo_k1)) {
+    manta_destroy(S);
+    return fail(MANTA_E_OOM, "device allocation failed in manta_create");
+  }
+  P.clo_k0 = d_ck0; P.clo_k1 = d_ck1;
   P.em = d_em; P.es = d_es; P.ntype = d_nt; P.esrc = d_esrc; P.lane_base = d_lb;
   P.nin_off = d_nin_off; P.nin = d_nin; P.stop_nodes = d_stops; P.mtab = d_mtab;
   P.dt = cfg->dt; P.L = cfg->veh_len_cells; P.H = cfg->horizon_cells;
@@ -437,8 +449,14 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
     due_edge[i] = first_edge(dorder[i]);
     if (d <= S->k) prime_hi = (uint32_t)(i + 1);
   }
+  // bit q: the edge after route entry q has a closure window (read by lane changes)
+  std::vector<uint32_t> nclo(((size_t)nr + 31) / 32 + 1, 0u);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t q = roff[j]; q + 1 < (int64_t)roff[j + 1]; ++q)
+      if (S->em_h[route[q + 1] & MANTA_EDGE_MASK].dst & MANTA_CLOSABLE) nclo[q >> 5] |= 1u << (q & 31);
   Params &P = S->P;
   bool ok = true;
+  uint32_t *d_nclo = dalloc<uint32_t>(S, nclo.size(), &ok);
   uint32_t *d_route = dalloc<uint32_t>(S, route.size(), &ok);
   uint32_t *d_roff = dalloc<uint32_t>(S, roff.size(), &ok);
   uint32_t *d_qoff = dalloc<uint32_t>(S, q_off.size(), &ok);
@@ -454,7 +472,7 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   P.req_g = dalloc<uint32_t>(S, NT, &ok); P.req_t = dalloc<uint32_t>(S, NT, &ok);
   P.req_e2 = dalloc<uint32_t>(S, NT, &ok); P.req_n = dalloc<uint32_t>(S, NT, &ok);
   if (!ok) return fail(MANTA_E_OOM, "device allocation failed in manta_load_trips");
-  bool cp = upload(S, d_route, route) && upload(S, d_roff, roff) && upload(S, d_qoff, q_off) &&
+  bool cp = upload(S, d_nclo, nclo) && upload(S, d_route, route) && upload(S, d_roff, roff) && upload(S, d_qoff, q_off) &&
             upload(S, d_qtrip, order) && upload(S, d_due, due_step) && upload(S, d_due_e, due_edge);
   Ctl c0;
   memset(&c0, 0, sizeof(c0));
@@ -462,6 +480,7 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   c0.due_hi = prime_hi;
   cp = cp && cudaMemcpyAsync(P.ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
   if (!cp) return fail(MANTA_E_CUDA, "upload failed in manta_load_trips");
+  P.nclo = d_nclo;
   P.route = d_route; P.route_off = d_roff; P.q_off = d_qoff; P.q_trip = d_qtrip;
   P.due_step = d_due; P.due_edge = d_due_e; P.n_trips = (uint32_t)n;
   S->route_off_h = std::move(roff);
@@ -477,6 +496,24 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   if (cudaStreamSynchronize(S->stream) != cudaSuccess)
     return fail(MANTA_E_CUDA, std::string("manta_load_trips: ") + cudaGetErrorString(cudaGetLastError()));
   S->loaded = true;
+  return MANTA_OK;
+}
+
+manta_status manta_set_lane_closure(manta_sim *S, int32_t edge, int32_t lane, int64_t k0, int64_t k1) {
+  g_err.clear();
+  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
+  if (S->loaded) return fail(MANTA_E_STATE, "lane closures must be set before manta_load_trips");
+  if (edge < 0 || edge >= S->E || lane < 0 || lane >= (int32_t)S->lanes[edge] || k1 < k0)
+    return fail(MANTA_E_INVALID, "bad lane closure");
+  const uint32_t g = S->lane_base[edge] + (uint32_t)lane;
+  S->clo_k0[g] = k0;
+  S->clo_k1[g] = k1;
+  S->em_h[edge].dst |= MANTA_CLOSABLE;
+  bool ok = cudaMemcpyAsync((void *)(S->P.clo_k0 + g), &S->clo_k0[g], sizeof(long long), cudaMemcpyHostToDevice, S->stream) == cudaSuccess &&
+            cudaMemcpyAsync((void *)(S->P.clo_k1 + g), &S->clo_k1[g], sizeof(long long), cudaMemcpyHostToDevice, S->stream) == cudaSuccess &&
+            cudaMemcpyAsync((void *)(S->P.em + edge), &S->em_h[edge], sizeof(EdgeMeta), cudaMemcpyHostToDevice, S->stream) == cudaSuccess &&
+            cudaStreamSynchronize(S->stream) == cudaSuccess;
+  if (!ok) return fail(MANTA_E_CUDA, "upload of a lane closure failed");
   return MANTA_OK;
 }
 

@@ -31,8 +31,9 @@ struct EdgeMeta {
   uint32_t row0;   // byte offset of lane 0, cell 0 in a lane-map buffer
   uint32_t cnl;    // cells | lanes << 24 | class << 28
   float lim;       // speed limit, m/s
-  uint32_t dst;    // head node
+  uint32_t dst;    // head node | MANTA_CLOSABLE if a lane of the edge has a closure window
 };
+#define MANTA_CLOSABLE 0x80000000u
 
 struct EdgeSig {   // signal window of this in-edge at its head node
   int16_t cyc;     // 0: head node is not a signal
@@ -68,6 +69,7 @@ struct Ctl {
   uint32_t act_sel[2];    // which buffer holds the active list at even / odd steps
   uint32_t n_holes[2];    // holes (arrived vehicles) in that list
   uint32_t n_compact;     // entries written by a compaction pass
+  uint32_t next3;          // next batch of the active list for phase P3
   uint32_t n_dep[2];
   uint32_t n_req, n_arr, n_chg, n_depwin;
   uint32_t free_count, n_slots;
@@ -88,6 +90,9 @@ struct Params {
   const uint32_t *nin;
   const uint32_t *stop_nodes;
   const float *mtab;           // Eq. 2 probability by distance in cells
+  const long long *clo_k0;     // closure window [k0, k1) of each lane (empty when k0 >= k1)
+  const long long *clo_k1;
+  const uint32_t *nclo;        // bit q: the edge after route entry q has a closure window
   // trips, read-only
   const uint32_t *route;       // edge | (lane mask toward the next route edge) << 24
   const uint32_t *route_off;

@@ -116,6 +116,13 @@ __device__ __forceinline__ uint8_t speed_code(float v) {
 }
 __device__ __forceinline__ float speed_decode(uint32_t c) { return __uint2float_rn(c) * 0.125f; }
 
+__device__ __forceinline__ uint32_t node_of(const EdgeMeta &m) { return m.dst & ~MANTA_CLOSABLE; }
+__device__ __forceinline__ bool closable(const EdgeMeta &m) { return (m.dst & MANTA_CLOSABLE) != 0u; }
+// lane g (global lane index) is closed at step k
+__device__ __forceinline__ bool lane_closed(const Params &p, uint32_t g, int64_t k) {
+  return __ldg(p.clo_k0 + g) <= k && k < __ldg(p.clo_k1 + g);
+}
+
 __device__ __forceinline__ EdgeMeta load_em(const Params &p, uint32_t e) {
   const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p.em) + e);
   EdgeMeta m;
@@ -160,21 +167,28 @@ __device__ __forceinline__ void load_batch(const uint8_t *row, int c, int hi, Ba
   b.q[2] = (c + 32 <= hi) ? __ldcg(reinterpret_cast<const uint4 *>(row + c + 32)) : none;
   b.q[3] = (c + 48 <= hi) ? __ldcg(reinterpret_cast<const uint4 *>(row + c + 48)) : none;
 }
-// first occupied cell in [lo, hi] within the batch starting at cell c, or -1
+// First occupied cell in [lo, hi] within the batch starting at cell c, or -1.
+// Branch-free: every word is tested and the lowest hit kept by selects; only
+// the first 16-byte chunk can hold cells below lo (lo lies in it for the first
+// batch of a scan, below it for later batches), and a first hit beyond hi
+// means there is none in range.
 __device__ __forceinline__ int check_batch(const Batch &b, int c, int lo, int hi) {
+  const uint32_t w[16] = {b.q[0].x, b.q[0].y, b.q[0].z, b.q[0].w, b.q[1].x, b.q[1].y, b.q[1].z, b.q[1].w,
+                          b.q[2].x, b.q[2].y, b.q[2].z, b.q[2].w, b.q[3].x, b.q[3].y, b.q[3].z, b.q[3].w};
+  int fk = -1;
+  uint32_t fm = 0u;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint32_t w[4] = {b.q[j].x, b.q[j].y, b.q[j].z, b.q[j].w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int base = c + 16 * j + 4 * t;
-      uint32_t m = occupied_bits(w[t]);
-      if (base < lo) m = (lo - base >= 4) ? 0u : (m & (0xFFFFFFFFu << (8 * (lo - base))));
-      if (base + 3 > hi) m = (base > hi) ? 0u : (m & (0xFFFFFFFFu >> (8 * (base + 3 - hi))));
-      if (m) return base + ((__ffs(m) - 1) >> 3);
+  for (int k = 15; k >= 0; --k) {
+    uint32_t m = occupied_bits(w[k]);
+    if (k < 4) {
+      const int d = lo - (c + 4 * k);
+      m = d <= 0 ? m : (d >= 4 ? 0u : (m & (0xFFFFFFFFu << (8 * d))));
     }
+    fk = m ? k : fk;
+    fm = m ? m : fm;
   }
-  return -1;
+  const int first = c + 4 * fk + ((__ffs(fm) - 1) >> 3);
+  return (fk < 0 || first > hi) ? -1 : first;
 }
 // First occupied cell of row[lo..hi] (inclusive), continuing from a batch
 // already loaded at lo & ~15; -1 if none.  Rows are 16-byte aligned and padded.
@@ -196,7 +210,7 @@ __device__ __forceinline__ int first_up(const uint8_t *row, int lo, int hi) {
 }
 
 // Last occupied cell in row[lo..hi] (scanning downward from hi) or -1;
-// four 16-byte chunks per round trip.
+// four 16-byte chunks per round trip, each block tested branch-free.
 __device__ __forceinline__ int first_down(const uint8_t *row, int hi, int lo) {
   if (lo > hi) return -1;
   const uint4 none = make_uint4(~0u, ~0u, ~0u, ~0u);
@@ -206,19 +220,23 @@ __device__ __forceinline__ int first_down(const uint8_t *row, int hi, int lo) {
 #pragma unroll
     for (int j = 1; j < 4; ++j)
       q[j] = (c - 16 * j >= 0 && c - 16 * j + 15 >= lo) ? __ldcg(reinterpret_cast<const uint4 *>(row + c - 16 * j)) : none;
+    // word k covers cells c - 16 * (k / 4) + 4 * (k % 4) ...; keep the highest hit within [lo, hi]
+    int best = -1;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int cc = c - 16 * j;
+    for (int j = 3; j >= 0; --j) {
       const uint32_t w[4] = {q[j].x, q[j].y, q[j].z, q[j].w};
 #pragma unroll
-      for (int t = 3; t >= 0; --t) {
-        const int base = cc + 4 * t;
+      for (int t = 0; t < 4; ++t) {
+        const int base = c - 16 * j + 4 * t;
         uint32_t m = occupied_bits(w[t]);
-        if (base < lo) m = (lo - base >= 4) ? 0u : (m & (0xFFFFFFFFu << (8 * (lo - base))));
-        if (base + 3 > hi) m = (base > hi) ? 0u : (m & (0xFFFFFFFFu >> (8 * (base + 3 - hi))));
-        if (m) return base + ((31 - __clz(m)) >> 3);
+        const int dl = lo - base, dh = base + 3 - hi;
+        m = dl <= 0 ? m : (dl >= 4 ? 0u : (m & (0xFFFFFFFFu << (8 * dl))));
+        m = dh <= 0 ? m : (dh >= 4 ? 0u : (m & (0xFFFFFFFFu >> (8 * dh))));
+        const int hit = base + ((31 - __clz(m)) >> 3);
+        best = m ? hit : best;
       }
     }
+    if (best >= 0) return best;
     if (c < 64) break;
   }
   return -1;
@@ -257,7 +275,7 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t *counter, bool pred) {
 // Target lane or -1 (Section II-D: mandatory vs discretionary; Eq. 2; Eqs. 3-4).
 // The route entry (lane mask toward the next edge), the Eq. 2 probability and
 // the first chunks of the own and target lane rows are fetched together.
-__device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const Veh &w, uint64_t &c_lce) {
+__device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const Veh &w, uint32_t &c_lce) {
   const EdgeMeta &em = w.em;
   const int nl = lanes_of(em.cnl);
   const int lane = (int)(w.ld & 0xFFu);
@@ -274,15 +292,36 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
   const int hi = min(cell + H, C - 1);
   const int lo_t = max(0, cell - L + 1);     // target-lane cells from the lateral-overlap window on
   const uint32_t ent = has_next ? __ldg(p.route + w.rc) : 0xFFFFFFFFu;
+  const bool next_clo = has_next && ((__ldg(p.nclo + (w.rc >> 5)) >> (w.rc & 31)) & 1u);
   const float mprob = __ldg(p.mtab + (C - 1 - cell));
   Batch bt, bo;
   load_batch(trow, lo_t & ~15, hi, bt);
   const bool own_scan = cell + 1 <= hi;
   if (own_scan) load_batch(orow, (cell + 1) & ~15, hi, bo);
-  const uint32_t mask = ent >> MANTA_EDGE_BITS;
+  uint32_t mask = ent >> MANTA_EDGE_BITS;
+  int obst = -1;
+  bool closed_here = false;
+  if (closable(em)) {
+    const uint32_t lb = __ldg(p.lane_base + w.e);
+    if (lane_closed(p, lb + (uint32_t)lt, k)) return -1;      // never into a closed lane
+    obst = C / 2;
+    closed_here = cell < obst && lane_closed(p, lb + (uint32_t)lane, k);
+  }
+  if (next_clo) {
+    // lanes whose continuation on the next edge is closed are not allowed either
+    const uint32_t e2 = __ldg(p.route + w.rc + 1u) & MANTA_EDGE_MASK;
+    const int nl2 = lanes_of(load_em(p, e2).cnl);
+    const uint32_t lb2 = __ldg(p.lane_base + e2);
+    uint32_t open = 0;
+    for (int q = 0; q < nl; ++q)
+      if (!lane_closed(p, lb2 + (uint32_t)min(q, nl2 - 1), k)) open |= 1u << q;
+    if (mask & open) mask &= open;
+  }
   const bool ok_l = (mask >> lane) & 1u, ok_lt = (mask >> lt) & 1u;
   bool mandatory = false;
-  if (has_next && !ok_l) {
+  if (closed_here) {
+    mandatory = true;
+  } else if (has_next && !ok_l) {
     int dp = 99, dm = 99;
     for (int q = lane + 1; q < nl; ++q)
       if ((mask >> q) & 1u) { dp = q - lane; break; }
@@ -297,7 +336,9 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
   int c1, ca;
   if (mandatory) {
     const float u1 = uni(p.seed, w.id, k, 0);
-    if (!(u1 < mprob)) return -1;
+    // Eq. 2 at the distance to the end of the edge, or to the obstacle of a closed lane
+    const float mp = closed_here ? __ldg(p.mtab + (obst - 1 - cell)) : mprob;
+    if (!(u1 < mp)) return -1;
     c1 = scan_from(trow, lo_t, hi, bt);
     ca = c1;
   } else {
@@ -377,7 +418,7 @@ struct Scan {
 // The next segment's route entry and edge record are fetched while the
 // current row is scanned.
 __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, const Veh &w, int cell,
-                            uint64_t &c_scan, uint64_t &c_rr) {
+                            uint32_t &c_scan, uint32_t &c_rr) {
   Scan s;
   s.kind = SC_FREE; s.cL = 0; s.vL = 0.0f; s.reached_own = false; s.stop_only = false; s.e2 = MANTA_NONE;
   const int limit = cell + p.H;
@@ -385,6 +426,25 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, cons
   uint32_t r = w.rc, se = w.e;
   EdgeMeta sm = w.em;
   bool own = true;
+  // a closed own lane holds a stationary obstacle from mid-edge on (cell C / 2)
+  int obst = -1;
+  if (closable(sm)) {
+    const int half = (int)cells_of(sm.cnl) / 2;
+    if (cell < half && lane_closed(p, __ldg(p.lane_base + w.e) + (uint32_t)sl, k)) obst = half;
+  }
+  if (obst >= 0 && obst <= limit) {
+    // only the cells before the obstacle can hold the leader
+    const uint8_t *row = cur + sm.row0 + (uint32_t)sl * stride_of(cells_of(sm.cnl));
+    const int c = first_up(row, cell + 1, obst - 1);
+    if (c >= 0) {
+      s.kind = SC_LEADER; s.cL = c; s.vL = speed_decode(cell_byte(row, c));
+      c_scan += (uint32_t)(c - cell);
+    } else {
+      s.kind = SC_VIRTUAL; s.cL = obst + p.L - 1; s.vL = 0.0f;
+      c_scan += (uint32_t)(obst - 1 - cell);
+    }
+    return s;
+  }
   for (;;) {
     const int segC = (int)cells_of(sm.cnl);
     const int hi_pos = min(limit, base + segC - 1);
@@ -402,7 +462,7 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, cons
     EdgeMeta sm2;
     sm2.row0 = 0; sm2.cnl = 0; sm2.lim = 0.0f; sm2.dst = 0;
     if (reach) {
-      nt = __ldg(p.ntype + sm.dst);
+      nt = __ldg(p.ntype + node_of(sm));
       sig = load_sig(p, se);
       sm2 = load_em(p, nent & MANTA_EDGE_MASK);
     }
@@ -410,17 +470,19 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, cons
       const int c = scan_from(row, pos - base, hi_pos - base, b);
       if (c >= 0) {
         s.kind = SC_LEADER; s.cL = base + c; s.vL = speed_decode(cell_byte(row, c));
-        c_scan += (uint64_t)(s.cL - cell);
+        c_scan += (uint32_t)(s.cL - cell);
         return s;
       }
     }
-    if (B > limit) { c_scan += (uint64_t)p.H; return s; }
-    if (r + 1u >= w.rend) { c_scan += (uint64_t)(B - 1 - cell); return s; }
+    if (B > limit) { c_scan += (uint32_t)p.H; return s; }
+    if (r + 1u >= w.rend) { c_scan += (uint32_t)(B - 1 - cell); return s; }
     c_rr++;
-    const uint32_t n = sm.dst;
+    const uint32_t n = node_of(sm);
     const uint32_t e2 = nent & MANTA_EDGE_MASK;
     bool blocked = false;
     if (nt == 2 && !is_green(sig, k)) blocked = true;
+    if (closable(sm2) && lane_closed(p, __ldg(p.lane_base + e2) + (uint32_t)min(sl, lanes_of(sm2.cnl) - 1), k))
+      blocked = true;                    // no entry into a closed lane
     if (own) {
       const bool stop_np = (nt == 1) && (ldv(p.permit + n) != w.id);
       s.reached_own = true;
@@ -432,7 +494,7 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, cons
     }
     if (blocked) {
       s.kind = SC_VIRTUAL; s.cL = B + p.L - 1; s.vL = 0.0f;
-      c_scan += (uint64_t)(B - 1 - cell);
+      c_scan += (uint32_t)(B - 1 - cell);
       return s;
     }
     ++r; base = B; pos = B; se = e2;
@@ -446,11 +508,16 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, cons
 __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Params p) {
   __shared__ int s_ok;
   __shared__ unsigned long long s_cnt[CNT_N];
+  __shared__ float s_sab2[8];                       // 2 sqrt(a b) per road class (Eq. 1)
+  __shared__ Veh s_lcq[kBlock / 32][64];            // per-warp queue of lane-change candidates
   Ctl *ctl = p.ctl;
   if (threadIdx.x < CNT_N) s_cnt[threadIdx.x] = 0ull;
+  if (threadIdx.x < 8) s_sab2[threadIdx.x] = 2.0f * sqrtf(p.a[threadIdx.x] * p.b[threadIdx.x]);
   __syncthreads();
-  uint64_t c_upd = 0, c_scan = 0, c_clamp = 0, c_lc = 0, c_lce = 0, c_rr = 0, c_dep = 0, c_arr = 0;
-  uint64_t ph[4] = {0, 0, 0, 0};
+  // per-thread counters fit 32 bits over one launch (at most 2048 steps)
+  uint32_t c_upd = 0, c_scan = 0, c_clamp = 0, c_lc = 0, c_lce = 0, c_rr = 0, c_dep = 0, c_arr = 0;
+  __shared__ unsigned long long ph[4];
+  if (threadIdx.x < 4) ph[threadIdx.x] = 0ull;
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t gsz = gridDim.x * blockDim.x;
@@ -474,6 +541,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
     uint32_t *act = compact ? (sel ? p.act0 : p.act1) : (sel ? p.act1 : p.act0);
     // ================================================================ P1
     if (gtid == 0) {
+      ctl->next3 = 0u;
       ctl->n_req = 0u;
       ctl->n_arr = 0u;
       ctl->n_holes[cb ^ 1] = compact ? 0u : holes;
@@ -497,22 +565,50 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       }
       if (threadIdx.x == 0) { ctl->due_pos = lo0; ctl->due_hi = lo; }
     }
-    for (uint32_t i = gtid; i < nact; i += gsz) {
-      const uint32_t s = __ldcg(act_in + i);
-      if (compact) {
-        const uint32_t at = warp_append(&ctl->n_compact, s != MANTA_NONE);
-        if (s != MANTA_NONE) act[at] = s;
+    {
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      Veh *q = s_lcq[wid];
+      int qn = 0;   // warp-uniform queue length
+      for (uint32_t base = gtid - (uint32_t)lane; base < nact; base += gsz) {
+        const uint32_t i = base + (uint32_t)lane;
+        const uint32_t s = i < nact ? __ldcg(act_in + i) : MANTA_NONE;
+        if (compact) {
+          const uint32_t at = warp_append(&ctl->n_compact, s != MANTA_NONE);
+          if (s != MANTA_NONE) act[at] = s;
+        }
+        Veh w;
+        bool cand = false;
+        if (s != MANTA_NONE) {
+          w = load_veh(p, s);
+          if (w.pcell != MANTA_NONE) nxt[w.pcell] = (uint8_t)MANTA_EMPTY;
+          cand = lanes_of(w.em.cnl) >= 2;
+          if (cand) w.pcell = s;          // the queue entry carries the slot in pcell
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
+        if (cand) q[qn + __popc(bal & ((1u << lane) - 1u))] = w;
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+          // a full warp of lane-change decisions
+          const Veh c = q[lane];
+          const int tgt = lc_decide(p, cur, k, c, c_lce);
+          if (tgt >= 0) p.veh[c.pcell].ld = (c.ld & 0xFF00FFFFu) | ((uint32_t)tgt << 16);
+          const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
+          if (tgt >= 0) p.chg[at] = c.pcell;
+          __syncwarp();
+          if (lane < qn - 32) q[lane] = q[32 + lane];
+          qn -= 32;
+          __syncwarp();
+        }
       }
-      if (s == MANTA_NONE) continue;
-      const Veh w = load_veh(p, s);
-      if (w.pcell != MANTA_NONE) nxt[w.pcell] = (uint8_t)MANTA_EMPTY;
-      int tgt = -1;
-      if (lanes_of(w.em.cnl) >= 2) {
-        tgt = lc_decide(p, cur, k, w, c_lce);
-        if (tgt >= 0) p.veh[s].ld = (w.ld & 0xFF00FFFFu) | ((uint32_t)tgt << 16);
+      if (lane < qn) {
+        const Veh c = q[lane];
+        const int tgt = lc_decide(p, cur, k, c, c_lce);
+        if (tgt >= 0) p.veh[c.pcell].ld = (c.ld & 0xFF00FFFFu) | ((uint32_t)tgt << 16);
+        const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
+        if (tgt >= 0) p.chg[at] = c.pcell;
       }
-      const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
-      if (tgt >= 0) p.chg[at] = s;
+      __syncwarp();
     }
     for (uint32_t j = gtid; j < p.n_stop; j += gsz) {
       const uint32_t n = __ldg(p.stop_nodes + j);
@@ -565,6 +661,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       const EdgeMeta em = load_em(p, e);
       const int C = (int)cells_of(em.cnl);
       const int need = min(C, L + p.s0c[class_of(em.cnl)]);
+      if (closable(em) && lane_closed(p, __ldg(p.lane_base + e), k)) continue;
       if (first_up(cur + em.row0, 0, need - 1) >= 0) continue;
       const uint32_t j = __ldg(p.q_trip + __ldg(p.q_off + e) + __ldcg(p.q_pos + e));
       p.dep_key[e] = ((unsigned long long)tag << 32) | j;
@@ -572,19 +669,24 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
     // vehicles
     const int64_t wk = k - p.t0;
     const int win = (wk >= 0 && wk / p.win_steps < p.n_win) ? (int)(wk / p.win_steps) : -1;
-    // two-stage prefetch: slot of the vehicle after next, record of the next one
-    uint32_t s_nx = gtid + gsz < nact ? __ldcg(act + gtid + gsz) : MANTA_NONE;
-    uint32_t s_cu = gtid < nact ? __ldcg(act + gtid) : MANTA_NONE;
-    Veh w_nx;
-    if (s_cu != MANTA_NONE) w_nx = load_veh(p, s_cu);
-    for (uint32_t i = gtid; i < nact; i += gsz) {
-      const uint32_t s = s_cu;
-      Veh w = w_nx;
-      const uint32_t s_nn = i + 2u * gsz < nact ? __ldcg(act + i + 2u * gsz) : MANTA_NONE;
-      if (i + gsz < nact && s_nx != MANTA_NONE) w_nx = load_veh(p, s_nx);
-      s_cu = s_nx;
-      s_nx = s_nn;
+    // warps take batches of 32 list entries from a shared counter (dynamic
+    // balance across warps); the next batch's slots load while this one runs
+    const int wl = threadIdx.x & 31;
+    uint32_t bb = 0;
+    if (wl == 0) bb = atomicAdd(&ctl->next3, 32u);
+    bb = __shfl_sync(0xFFFFFFFFu, bb, 0);
+    uint32_t s_nxt = bb + wl < nact ? __ldcg(act + bb + wl) : MANTA_NONE;
+    uint32_t bn = 0;
+    if (wl == 0) bn = atomicAdd(&ctl->next3, 32u);
+    while (bb < nact) {
+      const uint32_t i = bb + wl;
+      const uint32_t s = s_nxt;
+      bn = __shfl_sync(0xFFFFFFFFu, bn, 0);
+      s_nxt = bn + wl < nact ? __ldcg(act + bn + wl) : MANTA_NONE;
+      bb = bn;
+      if (wl == 0 && bn < nact) bn = atomicAdd(&ctl->next3, 32u);
       if (s == MANTA_NONE) continue;
+      Veh w = load_veh(p, s);
       const float x = w.x, v = w.v;
       const int lane = (int)(w.ld & 0xFFu);
       const uint32_t dwell = (w.ld >> 8) & 0xFFu;
@@ -595,7 +697,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       const int cell = (int)floorf(x);
       const uint32_t gcell = em.row0 + (uint32_t)lane * stride + (uint32_t)cell;
       const Scan sc = leader_scan(p, cur, k, w, cell, c_scan, c_rr);
-      const float a = p.a[cls], b = p.b[cls], T = p.T[cls], s0 = p.s0[cls];
+      const float a = p.a[cls], T = p.T[cls], s0 = p.s0[cls];
       const float v0 = em.lim * p.v0f[cls];
       const float r1 = v / v0, r2 = r1 * r1, r4 = r2 * r2;
       const bool has_next = w.rc + 1u < w.rend;
@@ -610,7 +712,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
           stop_in_place = true;
         } else {
           const float dv = v - sc.vL;
-          const float dyn = (v * dv) / (2.0f * sqrtf(a * b));
+          const float dyn = (v * dv) / s_sab2[cls];
           float ss;
           if (p.textbook) ss = s0 + fmaxf(0.0f, v * T + dyn);
           else ss = (s0 + v * T) + dyn;
@@ -643,7 +745,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
         const int zone = C - 1 - (p.s0c[cls] + 2);
         if ((int)floorf(xn) >= zone && vn < p.stop_eps) dwn = dwell < 255u ? dwell + 1u : 255u;
       }
-      if (has_next && sc.reached_own && __ldg(p.ntype + em.dst) == 1) {
+      if (has_next && sc.reached_own && __ldg(p.ntype + node_of(em)) == 1) {
         const uint32_t g = __ldg(p.lane_base + w.e) + (uint32_t)lane;
         p.slot_id[g] = w.id;
         p.slot_td[g] = ((uint32_t)(tag & 0xFFFFFF) << 8) | dwn;
@@ -686,7 +788,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       if (request) {
         const uint32_t iq = atomicAdd(&ctl->n_req, 1u);
         p.req[iq] = s; p.req_x[iq] = xn; p.req_v[iq] = vn; p.req_dw[iq] = dwn;
-        p.req_g[iq] = rq_g; p.req_t[iq] = rq_t; p.req_e2[iq] = rq_e2; p.req_n[iq] = em.dst;
+        p.req_g[iq] = rq_g; p.req_t[iq] = rq_t; p.req_e2[iq] = rq_e2; p.req_n[iq] = node_of(em);
       }
     }
     if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }

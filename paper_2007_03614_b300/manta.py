@@ -48,7 +48,7 @@ class MantaStats(C.Structure):
 EXPORTS = ("manta_default_config", "manta_create", "manta_load_trips", "manta_step", "manta_stats",
            "manta_edge_counters", "manta_snapshot", "manta_lane_map", "manta_lane_map_bytes",
            "manta_destroy", "manta_last_error", "manta_selftest_barrier_timeout", "manta_run_noalloc",
-           "manta_phase_times")
+           "manta_phase_times", "manta_set_lane_closure")
 
 _lib = None
 
@@ -90,6 +90,8 @@ def load_library():
         lib.manta_run_noalloc.argtypes = ([C.c_int32, C.c_int32] + [P] * 12 + [C.POINTER(MantaConfig), C.c_int64]
                                           + [P] * 3 + [C.c_int64, P, C.POINTER(MantaStats), C.c_int64,
                                                        C.POINTER(C.c_int64)] + [P] * 7)
+        lib.manta_set_lane_closure.restype = C.c_int
+        lib.manta_set_lane_closure.argtypes = [P, C.c_int32, C.c_int32, C.c_int64, C.c_int64]
         lib.manta_phase_times.restype = C.c_int
         lib.manta_phase_times.argtypes = [P, P]
         lib.manta_selftest_barrier_timeout.restype = C.c_int
@@ -173,6 +175,9 @@ class Sim:
         dt = np.ascontiguousarray(depart_time_s, dtype=np.float32)
         _check(self._lib.manta_load_trips(self._h, len(dt), _p(ro), _p(re), _p(dt)))
         self.n_trips = len(dt)
+
+    def set_lane_closure(self, edge, lane, k0, k1):
+        _check(self._lib.manta_set_lane_closure(self._h, int(edge), int(lane), int(k0), int(k1)))
 
     def step(self, n=1):
         _check(self._lib.manta_step(self._h, int(n)))

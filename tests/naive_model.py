@@ -72,6 +72,7 @@ class Naive:
                 j += 1
         self.inlanes = {n: [(e, l) for e in range(self.E) if self.dst[e] == n for l in range(self.nl[e])]
                         for n in range(len(self.ntype))}
+        self.closures = {}                      # (edge, lane) -> (k0, k1)
         self.permit = {n: None for n in range(len(self.ntype))}
         self.rr = {n: 0 for n in range(len(self.ntype))}
         self.routes = [list(map(int, tr.route_edges[tr.route_off[i]:tr.route_off[i + 1]]))
@@ -106,6 +107,10 @@ class Naive:
         m = (k - self.noff[n]) % self.ncyc[n]
         return self.gs[e] <= m < self.gs[e] + self.gl[e]
 
+    def closed(self, e, l, k):
+        w = self.closures.get((e, l))
+        return w is not None and w[0] <= k < w[1]
+
     def next_edge(self, v):
         r = self.routes[v.id]
         return r[v.r + 1] if v.r + 1 < len(r) else None
@@ -121,12 +126,25 @@ class Naive:
         lt = l + d
         if lt < 0 or lt >= self.nl[e]:
             return None
+        if self.closed(e, lt, k):
+            return None
         cell = self.cell(v)
         e2 = self.next_edge(v)
         mask = self.mask[(e, e2)] if e2 is not None else 0xFF
+        if e2 is not None:
+            open_ = 0
+            for q in range(self.nl[e]):
+                if not self.closed(e2, min(q, self.nl[e2] - 1), k):
+                    open_ |= 1 << q
+            if mask & open_:
+                mask &= open_
         ok_l, ok_lt = (mask >> l) & 1, (mask >> lt) & 1
+        obst = self.C[e] // 2
+        closed_here = self.closed(e, l, k) and cell < obst
         mandatory = False
-        if e2 is not None and not ok_l:
+        if closed_here:
+            mandatory = True
+        elif e2 is not None and not ok_l:
             up = [q - l for q in range(l + 1, self.nl[e]) if (mask >> q) & 1]
             dn = [l - q for q in range(0, l) if (mask >> q) & 1]
             dp = min(up) if up else 99
@@ -140,7 +158,7 @@ class Naive:
         hi = min(cell + H, self.C[e] - 1)
         target = self.in_lane(e, lt)
         if mandatory:
-            dist = self.C[e] - 1 - cell
+            dist = (obst - 1 - cell) if closed_here else (self.C[e] - 1 - cell)
             xm = float(dist) * float(c["cell_m"])
             x0, lam = float(F(c["lc_x0_m"])), float(F(c["lc_len_scale_m"]))
             m = 1.0 if xm <= x0 else math.exp(-((xm - x0) / lam) ** 2)
@@ -213,6 +231,12 @@ class Naive:
                         best_p, best_w = p, w
         reads = 0
         out = dict(kind="free", reached_own=False, stop_only=False)
+        e0, l0 = segs[0][0], segs[0][1]
+        obst = self.C[e0] // 2
+        if self.closed(e0, l0, k) and cell < obst and obst <= limit and (best_p is None or best_p >= obst):
+            out.update(kind="virtual", cL=obst + L - 1, vL=F(0.0))
+            self.st["cells_scanned"] += obst - 1 - cell
+            return out
         for si, (e, l, b, r) in enumerate(segs):
             B = b + self.C[e]
             if best_p is not None and best_p < B:
@@ -226,6 +250,8 @@ class Naive:
             n = self.dst[e]
             nxt = route[r + 1]
             blocked = self.ntype[n] == 2 and not self.green(e, k)
+            if self.closed(nxt, min(l, self.nl[nxt] - 1), k):
+                blocked = True
             if si == 0:
                 stop_np = self.ntype[n] == 1 and self.permit[n] != v.id
                 out["reached_own"] = True
@@ -269,6 +295,8 @@ class Naive:
                 continue
             j = min(cand, key=lambda i: (self.dstep[i], i))
             if self.dstep[j] > k:
+                continue
+            if self.closed(e, 0, k):
                 continue
             need = min(self.C[e], L + math.ceil(float(F(c["s0"][self.cls[e]]))))
             if any(self.cell(w) < need for w in self.in_lane(e, 0)):

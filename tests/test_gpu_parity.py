@@ -52,9 +52,12 @@ def _compare_all(o, g, windows=(0,), where=""):
             assert np.array_equal(eo[key], eg[key]), (where, w, key)
 
 
-def _pair(net, tr, **cfg):
+def _pair(net, tr, closures=(), **cfg):
     o = O.OracleSim(net, **cfg)
     g = manta.Sim(net, **cfg)
+    for (e, l, k0, k1) in closures:
+        o.set_lane_closure(e, l, k0, k1)
+        g.set_lane_closure(e, l, k0, k1)
     nets.load(o, tr)
     nets.load(g, tr)
     return o, g
@@ -94,11 +97,11 @@ def test_tiny_all_stop_signs_bit_exact():
 def test_small_mixed_networks_every_step(seed, ci):
     """Random-walk routes on a 3x3 lattice with stop, signal and green nodes:
     every step compared (merges, queues, permits, lane changes)."""
-    from test_oracle_bruteforce import CFGS, _scenario
+    from test_oracle_bruteforce import CFGS, _scenario, closures_for
     net, tr = _scenario(seed, n_trips=40)
     cfg = dict(CFGS[ci])
     cfg["seed"] = 100 + seed
-    o, g = _pair(net, tr, **cfg)
+    o, g = _pair(net, tr, closures=closures_for(net, seed) if ci == 1 else (), **cfg)
     for k in range(600):
         o.step(1)
         g.step(1)
@@ -192,6 +195,26 @@ def test_metro_network_window_bit_exact(metro):
         _compare(o, g, f"metro step {k + 100}")
     _compare_all(o, g, windows=(0,))
     assert g.stats()["on_network"] > 10000
+
+
+def test_metro_incident_closures_bit_exact(metro):
+    """Stress-style incident: lane 0 closed on 200 random freeway edges from
+    07:30 for 5 minutes, on the full metro network with the 07:30-07:35 trips."""
+    net, tr = metro
+    rng = np.random.default_rng(4)
+    fw = np.nonzero(net.edge_class == synth.CLASS_FREEWAY)[0]
+    t0 = int(7.5 * 3600 / 0.5)
+    clo = [(int(e), 0, t0, t0 + 600) for e in rng.choice(fw, 200, replace=False)]
+    sub = _subset(tr, 7.5 * 3600, 7.5 * 3600 + 300)
+    o, g = _pair(net, sub, closures=clo, t0_step=t0, n_stats_windows=4)
+    for k in range(0, 600, 150):
+        o.step(150)
+        g.step(150)
+        _compare(o, g, f"closures step {k + 150}")
+    _compare_all(o, g, windows=(0,))
+    with pytest.raises(manta.MantaError) as ei:
+        g.set_lane_closure(0, 0, 0, 1)
+    assert ei.value.status == manta.E_STATE
 
 
 def test_metro_full_morning_properties(metro):

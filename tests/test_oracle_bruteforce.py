@@ -40,6 +40,18 @@ def _scenario(seed, n_trips=20, nx=3, ny=3):
 CFGS = [dict(), dict(lc_len_scale_m=100.0), dict(idm_textbook=1, lc_len_scale_m=30.0, s0=[1.0, 3.5, 2.0])]
 
 
+def closures_for(net, seed):
+    """Seeded incident closures on a few multi-lane edges: (edge, lane, k0, k1)."""
+    rng = np.random.default_rng(1000 + seed)
+    multi = np.nonzero(net.edge_lanes >= 2)[0]
+    out = []
+    for e in rng.choice(multi, size=min(3, len(multi)), replace=False):
+        lane = int(rng.integers(0, net.edge_lanes[e]))
+        k0 = int(rng.integers(0, 150))
+        out.append((int(e), lane, k0, k0 + int(rng.integers(50, 300))))
+    return out
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])
 @pytest.mark.parametrize("ci", range(len(CFGS)))
 def test_oracle_equals_naive(seed, ci):
@@ -50,6 +62,10 @@ def test_oracle_equals_naive(seed, ci):
     s = O.OracleSim(net, **cfg)
     nets.load(s, tr)
     nv = Naive(net, tr, cfg)
+    if ci == 1:
+        for (e, l, k0, k1) in closures_for(net, seed):
+            s.set_lane_closure(e, l, k0, k1)
+            nv.closures[(e, l)] = (k0, k1)
     for k in range(500):
         s.step(1)
         nv.step()

@@ -426,3 +426,50 @@ def test_wrong_lane_is_a_late_merge_not_a_stop():
             crossed_from = int(prev["lane"][pj[0]])
     assert crossed_from == 1                         # still in the disallowed lane at the node
     assert sn["edge"][byid[0]] == 1 and sn["lane"][byid[0]] == 1
+
+
+# ------------------------------------------------------------ lane closures --
+def test_closed_lane_obstacle_and_mandatory_change():
+    """An incident closure holds a stationary obstacle from mid-edge on: a
+    vehicle behind it in a one-lane road stops short of it; in a two-lane road
+    it changes lanes (mandatory) and passes."""
+    # one lane: stops behind the obstacle at cell C/2 = 100
+    net = nets.line(1, length=200.0, lanes=1, speed=13.889)
+    tr = nets.trips([[0]], [1e7])
+    s = O.OracleSim(net)
+    nets.load(s, tr)
+    s.set_lane_closure(0, 0, 0, 1000)
+    s.place(0, 0, 0, 20.0, 10.0)
+    s.step(200)
+    sn = s.snapshot()
+    assert sn["v"][0] < 0.05 and 100 - 1 - 2 - 1.5 <= sn["x"][0] <= 100 - 1
+    # two lanes: the vehicle leaves the closed lane before the obstacle and arrives
+    net = nets.line(1, length=200.0, lanes=2, speed=13.889)
+    s = O.OracleSim(net, lc_len_scale_m=30.0)
+    nets.load(s, tr)
+    s.set_lane_closure(0, 0, 0, 1000)
+    s.place(0, 0, 0, 20.0, 10.0)
+    for _ in range(60):
+        s.step(1)
+        sn = s.snapshot()
+        if len(sn["id"]) and sn["x"][0] >= 100:
+            assert sn["lane"][0] == 1
+    assert s.stats()["arrived"] == 1 and s.stats()["lane_changes"] == 1
+
+
+def test_closed_lane_blocks_entry_and_departures_until_reopened():
+    net = nets.line(2, length=100.0, lanes=1, speed=13.889)
+    tr = nets.trips([[0, 1], [1]], [0.0, 0.0])
+    s = O.OracleSim(net)
+    nets.load(s, tr)
+    s.set_lane_closure(1, 0, 0, 100)            # lane 0 of edge 1 closed for steps [0, 100)
+    s.step(80)
+    sn = s.snapshot()
+    byid = {int(i): j for j, i in enumerate(sn["id"])}
+    assert 1 not in byid                          # the departure onto edge 1 waits
+    assert sn["edge"][byid[0]] == 0 and sn["v"][byid[0]] < 0.05   # held at the node
+    s.step(60)
+    st = s.stats()
+    assert st["departed"] == 2                    # both moved on after step 100
+    with pytest.raises(O.OracleError):
+        s.set_lane_closure(0, 0, 0, 10)          # only before the first step
