@@ -36,18 +36,47 @@ UNIT = "vehicle-updates/s"
 T0_STEP = 36000                     # 05:00 at dt = 0.5 s
 MORNING_STEPS = 50400               # 05:00-12:00
 
-# Algorithmic bytes of the step kernel ("Roofline"): per vehicle
-# update, per lane-map cell examined by the leader scan, per route boundary
-# crossed by a scan, per gap-acceptance evaluation.
-BYTES_PER_UPDATE = 114
+# Algorithmic bytes of the step kernel: per vehicle update (active-list
+# entries, vehicle record read twice and written once, the map byte written
+# and cleared, the per-edge speed statistic read-modify-write), per lane-map
+# cell examined by a leader scan, per node crossed by a scan (route entry,
+# edge record, signal window, node type), per gap-acceptance evaluation.
+BYTES_PER_UPDATE = 162
 BYTES_PER_CELL = 1
-BYTES_PER_ROUTE_READ = 20
-BYTES_PER_LC_EVAL = 48
+BYTES_PER_ROUTE_READ = 29
+BYTES_PER_LC_EVAL = 64
+KERNEL_SOURCES = ("paper_2007_03614_b300/csrc/step_kernel.cuh", "paper_2007_03614_b300/csrc/sim.cuh")
+TRAFFIC_PROFILE = "profiles/metro_step_kernel_ncu.md"
 
 
 def algorithmic_bytes(d: dict) -> int:
     return (d["vehicle_updates"] * BYTES_PER_UPDATE + d["cells_scanned"] * BYTES_PER_CELL
             + d["route_reads"] * BYTES_PER_ROUTE_READ + d["lc_evals"] * BYTES_PER_LC_EVAL)
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic_per_update():
+    """DRAM bytes per vehicle update from the committed ncu summary, if it was
+    taken on the kernel as it is now (same source hash); else None."""
+    try:
+        vals = {}
+        for line in open(os.path.join(ROOT, TRAFFIC_PROFILE)):
+            if ":" in line and line.strip().startswith(("kernel_sha256", "dram_bytes_per_vehicle_update")):
+                k, v = line.strip().strip("-* `").split(":", 1)
+                vals[k.strip(" `")] = v.strip(" `")
+        if vals.get("kernel_sha256") == kernel_hash():
+            return float(vals["dram_bytes_per_vehicle_update"])
+    except Exception:
+        pass
+    return None
 
 
 def _peaks():
@@ -152,10 +181,13 @@ def run_gpu(args):
         sim = manta.Sim(net, stream=stream, t0_step=int(lo / 0.5), n_stats_windows=8)
         sim.load_trips(off, edges, dep)
         sim.step(1200)
+        u0 = sim.stats()["vehicle_updates"]
         for _ in range(args.steps):
             sim.step(chunk)
         st = sim.stats()
-        print(json.dumps({"profile_case": True, "stats": st, "phase_ms": [float(x) for x in sim.phase_times_ms()]}))
+        print(json.dumps({"profile_case": True, "kernel_sha256": kernel_hash(),
+                          "updates_in_profiled_launches": st["vehicle_updates"] - u0, "stats": st,
+                          "phase_ms": [float(x) for x in sim.phase_times_ms()]}))
         return
     # ---- device-resident run (the headline value) ----
     sim = manta.Sim(net, stream=stream, t0_step=T0_STEP)
@@ -165,6 +197,7 @@ def run_gpu(args):
         for _ in range(args.warmup):
             sim.step(chunk)
     s0 = sim.stats()
+    ph0 = sim.phase_times_ms()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -184,7 +217,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     s1 = sim.stats()
-    phase_ms = [round(float(x), 2) for x in sim.phase_times_ms()]
+    phase_ms = [round(float(a - b), 2) for a, b in zip(sim.phase_times_ms(), ph0)]
     elapsed = sum(times)
     d = {k: s1[k] - s0[k] for k in ("vehicle_updates", "cells_scanned", "route_reads", "lc_evals", "clamps",
                                     "lane_changes", "departed", "arrived")}
@@ -236,6 +269,8 @@ def run_gpu(args):
     bytes_alg = algorithmic_bytes(d)
     per_launch_s = elapsed / max(1, args.steps)
     achieved = bytes_alg / max(1, args.steps) / per_launch_s / 1e9
+    tpu = measured_traffic_per_update()
+    traffic = None if tpu is None else int(tpu * d["vehicle_updates"] / max(1, args.steps))
     out = {
         "metric": METRIC, "value": total_updates / elapsed, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
@@ -250,9 +285,9 @@ def run_gpu(args):
         "gpu_launches": args.steps * ((chunk + 2047) // 2048),
         "morning_wall_s": morning,
         "counters": d,
-        "phase_ms_all_chunks": phase_ms,
+        "phase_ms_timed": phase_ms,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(bytes_alg / max(1, args.steps))},
         "clocks": clk.summary(),
         "e2e": e2e,
