@@ -327,6 +327,73 @@ def cpu_baseline(net, tr, n_steps):
                       f"network at 07:30, {upd} vehicle updates in {dt:.1f} s"}
 
 
+def run_ensemble(args):
+    """64 uneven what-if scenarios, one simulated hour each (07:00-08:00), run
+    (a) batched: one simulation of the disjoint union, one launch per 2048 steps;
+    (b) sequential: one simulation per scenario, one after another.
+    A bench step is one complete ensemble; value = scenarios/s of (a)."""
+    import torch
+
+    from paper_2007_03614_b300 import manta, synth
+    from paper_2007_03614_b300.build import build
+    rank, world = _dist()
+    if rank != 0:
+        return
+    build()
+    manta.load_library()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    sc = synth.ensemble_scenarios(n=args.scenarios)
+    ens = synth.union(sc)
+    t0 = int(7 * 3600 / 0.5)
+    steps = 7200
+
+    def timed(sim):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sim.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / 1000.0
+
+    batched, upd = [], 0
+    for it in range(args.warmup + args.steps):
+        sim = manta.Sim(ens.net, stream=stream, t0_step=t0, n_stats_windows=16)
+        sim.load_trips(ens.trips.route_off, ens.trips.route_edges, ens.trips.depart_time_s)
+        dt = timed(sim)
+        if it >= args.warmup:
+            batched.append(dt)
+            upd = sim.stats()["vehicle_updates"]
+        sim.close()
+    seq = 0.0
+    seq_upd = 0
+    for net, tr in sc:
+        sim = manta.Sim(net, stream=stream, t0_step=t0, n_stats_windows=16)
+        sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+        seq += timed(sim)
+        seq_upd += sim.stats()["vehicle_updates"]
+        sim.close()
+    tb = sum(batched) / len(batched)
+    n = len(sc)
+    print(json.dumps({
+        "metric": f"scenarios/s ({n} uneven what-if scenarios, 1 simulated hour each at dt = 0.5 s)",
+        "value": n / tb, "unit": "scenarios/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * tb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ensemble", "scenarios": n, "edges_total": int(ens.net.n_edges),
+                   "trips_total": int(ens.trips.n_trips),
+                   "edges_per_scenario": [int(x) for x in np.diff(ens.edge_off)],
+                   "trips_per_scenario": [int(x) for x in np.diff(ens.trip_off)],
+                   "sim_steps": steps, "t0_step": t0},
+        "batched": {"seconds": tb, "scenarios_per_s": n / tb, "vehicle_updates": upd,
+                    "vehicle_updates_per_s": upd / tb},
+        "sequential": {"seconds": seq, "scenarios_per_s": n / seq, "vehicle_updates": seq_upd,
+                       "vehicle_updates_per_s": seq_upd / seq},
+        "batched_over_sequential": seq / tb,
+        "gpu_launches": args.steps * ((steps + 2047) // 2048)}))
+
+
 def run_reference(args):
     rank, world = _dist()
     if rank != 0:
@@ -369,6 +436,8 @@ def main():
     ap.add_argument("--ref-chunk", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="metro", choices=["metro", "ensemble"])
+    ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: 07:30-08:00 trips, 1200-step warm-up launch, then --steps launches")
     args = ap.parse_args()
@@ -376,6 +445,8 @@ def main():
         raise SystemExit("need --steps >= 1 and --warmup >= 0")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
     else:
         run_gpu(args)
 

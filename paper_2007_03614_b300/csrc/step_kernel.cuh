@@ -71,7 +71,7 @@ __device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned &target, uint64_t limi
           c = kBarrierAbort;
           break;
         }
-        if (spins > 1024u) __nanosleep(64);
+        if (spins > 32u) __nanosleep(128);
       }
     }
     *s_ok = c < kBarrierAbort;
@@ -296,7 +296,9 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
   const float mprob = __ldg(p.mtab + (C - 1 - cell));
   Batch bt, bo;
   load_batch(trow, lo_t & ~15, hi, bt);
-  const bool own_scan = cell + 1 <= hi;
+  // a stopped vehicle cannot find a slower leader, so only a mandatory change
+  // is possible: skip the own-lane fetch
+  const bool own_scan = cell + 1 <= hi && v > 0.0f;
   if (own_scan) load_batch(orow, (cell + 1) & ~15, hi, bo);
   uint32_t mask = ent >> MANTA_EDGE_BITS;
   int obst = -1;

@@ -187,7 +187,7 @@ def lattice(nx, ny, *, arterial_every=0, freeway_every=0, local_keep=1.0,
     return net
 
 
-def make_trips(net: Network, n_trips, *, od_model="uniform", zones=(20, 25), pool_per_zone=16,
+def make_trips(net: Network, n_trips, *, od_model="uniform", zones=(20, 25), pool_per_zone=None,
                spacing_km=0.15, beta_km=10.0, zone_mass_sigma=1.0,
                depart="uniform", t_lo_s=0.0, t_hi_s=600.0, mean_s=0.0, sd_s=1.0,
                mean2_s=0.0, sd2_s=1.0, w2=0.0, seed=1, n_threads=None) -> Trips:
@@ -213,7 +213,9 @@ def make_trips(net: Network, n_trips, *, od_model="uniform", zones=(20, 25), poo
     tp.n_trips = n_trips
     tp.od_model = {"uniform": 0, "gravity": 1}[od_model]
     tp.zones_x, tp.zones_y = zones
-    tp.pool_per_zone = pool_per_zone
+    # origin pool: per zone for the gravity model (default 16); for uniform OD a
+    # pool over the whole network (default 0 = every node may be an origin)
+    tp.pool_per_zone = (16 if od_model == "gravity" else 0) if pool_per_zone is None else pool_per_zone
     tp.spacing_km, tp.beta_km, tp.zone_mass_sigma = spacing_km, beta_km, zone_mass_sigma
     tp.depart_model = {"uniform": 0, "normal": 1, "bimodal": 2}[depart]
     tp.t_lo_s, tp.t_hi_s, tp.mean_s, tp.sd_s = t_lo_s, t_hi_s, mean_s, sd_s
@@ -247,7 +249,7 @@ def tiny_network(seed=1) -> Network:
 def tiny_trips(net: Network, n_trips=1000, seed=1) -> Trips:
     """Uniform-random OD node pairs, departures uniform over the first 10 min."""
     return make_trips(net, n_trips, od_model="uniform", depart="uniform", t_lo_s=0.0,
-                      t_hi_s=600.0, seed=seed)
+                      t_hi_s=600.0, seed=seed, pool_per_zone=0)
 
 
 METRO_SIDE = 482
@@ -281,3 +283,76 @@ def metro_trips(net: Network, n_trips=3_200_000, seed=2, t_lo_s=5 * 3600.0, t_hi
     return make_trips(net, n_trips, od_model="gravity", zones=(20, 25), pool_per_zone=16,
                       spacing_km=0.15, beta_km=METRO_BETA_KM, depart="normal", t_lo_s=t_lo_s, t_hi_s=t_hi_s,
                       mean_s=8 * 3600.0, sd_s=75 * 60.0, seed=seed, n_threads=n_threads)
+
+
+# ------------------------------------------------------------------ ensemble --
+@dataclass
+class Ensemble:
+    """Independent scenarios merged into one network and one trip table.
+
+    Scenario s owns nodes [node_off[s], node_off[s+1]), edges [edge_off[s],
+    edge_off[s+1]) and trips [trip_off[s], trip_off[s+1]); no edge connects two
+    scenarios, so one simulation of the union advances all of them at once."""
+    net: Network
+    trips: Trips
+    node_off: np.ndarray
+    edge_off: np.ndarray
+    trip_off: np.ndarray
+    scenarios: list
+
+
+def union(parts) -> Ensemble:
+    """Disjoint union of (Network, Trips) pairs (node, edge and trip ids offset)."""
+    nets_, trs = [p[0] for p in parts], [p[1] for p in parts]
+    node_off = np.concatenate([[0], np.cumsum([n.n_nodes for n in nets_])]).astype(np.int64)
+    edge_off = np.concatenate([[0], np.cumsum([n.n_edges for n in nets_])]).astype(np.int64)
+    trip_off = np.concatenate([[0], np.cumsum([t.n_trips for t in trs])]).astype(np.int64)
+    cat = lambda name, dt: np.concatenate([getattr(n, name) for n in nets_]).astype(dt)
+    net = Network(
+        edge_src=np.concatenate([n.edge_src + node_off[i] for i, n in enumerate(nets_)]).astype(np.int32),
+        edge_dst=np.concatenate([n.edge_dst + node_off[i] for i, n in enumerate(nets_)]).astype(np.int32),
+        edge_lanes=cat("edge_lanes", np.uint8), edge_length_m=cat("edge_length_m", np.float32),
+        edge_speed_limit_mps=cat("edge_speed_limit_mps", np.float32), edge_class=cat("edge_class", np.uint8),
+        node_type=cat("node_type", np.uint8), node_cycle_steps=cat("node_cycle_steps", np.int32),
+        node_offset_steps=cat("node_offset_steps", np.int32), edge_green_start=cat("edge_green_start", np.int16),
+        edge_green_len=cat("edge_green_len", np.int16),
+        conn_lane_mask=np.concatenate([n.conn_lane_mask for n in nets_]).astype(np.uint32))
+    route_edges = np.concatenate([t.route_edges + edge_off[i] for i, t in enumerate(trs)]).astype(np.int32)
+    route_off = np.zeros(int(trip_off[-1]) + 1, np.int64)
+    base = 0
+    for i, t in enumerate(trs):
+        route_off[trip_off[i] + 1: trip_off[i + 1] + 1] = t.route_off[1:] + base
+        base += int(t.route_off[-1])
+    trips = Trips(route_off=route_off, route_edges=route_edges,
+                  depart_time_s=np.concatenate([t.depart_time_s for t in trs]).astype(np.float32))
+    return Ensemble(net=net, trips=trips, node_off=node_off, edge_off=edge_off, trip_off=trip_off, scenarios=[])
+
+
+def ensemble_scenarios(n=64, seed=100, edges_range=(5_000, 100_000), trips_range=(10_000, 500_000),
+                       closed_frac=(0.0, 0.05), window_s=3600.0, t0_s=7 * 3600.0):
+    """What-if scenarios of uneven size: lattice networks (plain grids for even
+    scenario indices, the arterial/freeway hierarchy for odd ones) with edge
+    counts log-uniform in `edges_range`, trip counts log-uniform in
+    `trips_range`, a random fraction of local segments closed before routing,
+    departures over one hour from t0 (per-scenario seeds seed + i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        target_e = float(np.exp(rng.uniform(np.log(edges_range[0]), np.log(edges_range[1]))))
+        n_trips = int(np.exp(rng.uniform(np.log(trips_range[0]), np.log(trips_range[1]))))
+        closed = float(rng.uniform(*closed_frac))
+        hier = i % 2 == 1
+        keep = 0.57 * (1.0 - closed) if hier else 0.75 * (1.0 - closed)
+        # directed edges ~ 2 * 2 * side^2 * keep-ish: solve for the side
+        side = max(12, int(np.sqrt(target_e / (4.0 * (keep if not hier else 0.62)))))
+        if hier:
+            net = lattice(side, side, arterial_every=8, freeway_every=32, local_keep=keep, len_median_m=120.0,
+                          len_sigma=0.8, len_min_m=20.0, len_max_m=2000.0, signals_at=1, limited_access=True,
+                          seed=seed + i)
+        else:
+            net = lattice(side, side, arterial_every=4, local_keep=keep, len_median_m=120.0, len_sigma=0.5,
+                          len_min_m=20.0, len_max_m=1000.0, signals_at=1, seed=seed + i)
+        tr = make_trips(net, n_trips, od_model="uniform", depart="uniform", t_lo_s=t0_s, t_hi_s=t0_s + window_s,
+                        seed=seed + i, pool_per_zone=256)
+        out.append((net, tr))
+    return out

@@ -466,11 +466,21 @@ SYNTH_API synth_trips *synth_make_trips(const synth_net *net, const synth_trip_p
   for (int32_t n = 0; n < nn; ++n)
     if (!net->node_trip_ok || net->node_trip_ok[n]) ends[n_ends++] = n;
   if (p->od_model == 0) {
+    /* uniform OD; with pool_per_zone > 0 the origins come from that many
+       uniformly drawn nodes (one shortest-path tree per pool node) */
+    int32_t *opool = NULL;
+    int32_t np_ = 0;
+    if (p->pool_per_zone > 0 && p->pool_per_zone < n_ends) {
+      np_ = p->pool_per_zone;
+      opool = (int32_t *)malloc(sizeof(int32_t) * (size_t)np_);
+      for (int32_t q = 0; q < np_; ++q) opool[q] = ends[rng_below(&r, (uint64_t)n_ends)];
+    }
     for (int64_t k = 0; k < nt; ++k) {
-      int32_t o = ends[rng_below(&r, (uint64_t)n_ends)], d;
+      int32_t o = opool ? opool[rng_below(&r, (uint64_t)np_)] : ends[rng_below(&r, (uint64_t)n_ends)], d;
       do { d = ends[rng_below(&r, (uint64_t)n_ends)]; } while (d == o && n_ends > 1);
       t->origin[k] = o; t->dest[k] = d;
     }
+    free(opool);
   } else {
     /* zones: rectangular blocks of the lattice */
     int32_t maxi = 0, maxj = 0;

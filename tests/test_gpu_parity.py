@@ -241,3 +241,21 @@ def test_metro_full_morning_properties(metro):
     same = row_of[1:] == row_of[:-1]
     assert np.all(np.diff(occ)[same] >= 5)
     assert st["on_network"] > 100000
+
+
+def test_ensemble_union_bit_exact():
+    """Batched what-if scenarios: the disjoint union of uneven scenarios runs as
+    one simulation; it matches the oracle on the same union."""
+    sc = synth.ensemble_scenarios(n=5, seed=7, edges_range=(800, 6000), trips_range=(300, 3000))
+    ens = synth.union(sc)
+    t0 = int(7 * 3600 / 0.5)
+    o, g = _pair(ens.net, ens.trips, t0_step=t0, n_stats_windows=4)
+    for k in range(0, 900, 150):
+        o.step(150)
+        g.step(150)
+        _compare(o, g, f"ensemble step {k + 150}")
+    _compare_all(o, g, windows=(0, 1))
+    # every scenario made progress
+    ec = g.edge_counters(0)
+    for s in range(len(sc)):
+        assert int(ec["entries"][ens.edge_off[s]:ens.edge_off[s + 1]].sum()) > 0

@@ -473,3 +473,19 @@ def test_closed_lane_blocks_entry_and_departures_until_reopened():
     assert st["departed"] == 2                    # both moved on after step 100
     with pytest.raises(O.OracleError):
         s.set_lane_closure(0, 0, 0, 10)          # only before the first step
+
+
+def test_ensemble_union_is_disjoint():
+    """The union of scenarios keeps every route inside its own scenario and the
+    oracle accepts it (contiguous routes, edge and node ids offset)."""
+    from paper_2007_03614_b300 import synth
+    sc = synth.ensemble_scenarios(n=3, seed=3, edges_range=(500, 2000), trips_range=(100, 400))
+    ens = synth.union(sc)
+    for s in range(3):
+        a, b = ens.trip_off[s], ens.trip_off[s + 1]
+        r = ens.trips.route_edges[ens.trips.route_off[a]:ens.trips.route_off[b]]
+        assert r.min() >= ens.edge_off[s] and r.max() < ens.edge_off[s + 1]
+    o = O.OracleSim(ens.net, t0_step=50400)
+    nets.load(o, ens.trips)
+    o.step(100)
+    o.check()
