@@ -627,7 +627,7 @@ manta_status manta_snapshot(manta_sim *S, int64_t cap, int64_t *n_out, float *x,
     if (x) x[i] = w.x;
     if (v) v[i] = w.v;
     if (edge) edge[i] = (int32_t)w.e;
-    if (lane) lane[i] = (uint8_t)(w.ld & 0xFFu);
+    if (lane) lane[i] = (uint8_t)(w.ld & 0xFu);
     if (id) id[i] = w.id;
     if (dwell) dwell[i] = (uint8_t)((w.ld >> 8) & 0xFFu);
     if (route_pos) route_pos[i] = (int32_t)(w.rc - S->route_off_h[w.id]);

@@ -55,7 +55,8 @@ struct __align__(16) Veh {
   uint32_t rc;     // index of the current edge in the route array
   uint32_t rend;   // one past the last route entry of the trip
   uint32_t e;      // current edge
-  uint32_t ld;     // lane | dwell << 8 | lane-change target << 16
+  uint32_t ld;     // lane (bits 0-3) | next edge has a closure (bit 4) | dwell << 8 |
+                   // lane-change target << 16 | lane mask toward the next edge << 24
   uint32_t pcell;  // its cell in the other map buffer (cleared next step), or none
   EdgeMeta em;     // record of edge e
 };

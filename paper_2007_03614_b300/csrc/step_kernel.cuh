@@ -149,6 +149,20 @@ __device__ __forceinline__ void store_veh(const Params &p, uint32_t s, const Veh
   reinterpret_cast<uint4 *>(p.veh + s)[2] = make_uint4(w.em.row0, w.em.cnl, __float_as_uint(w.em.lim), w.em.dst);
 }
 
+// lane word of a vehicle record
+__device__ __forceinline__ int ld_lane(uint32_t ld) { return (int)(ld & 0xFu); }
+__device__ __forceinline__ uint32_t ld_dwell(uint32_t ld) { return (ld >> 8) & 0xFFu; }
+__device__ __forceinline__ uint32_t ld_mask(uint32_t ld) { return ld >> 24; }
+__device__ __forceinline__ bool ld_nxclo(uint32_t ld) { return (ld >> 4) & 1u; }
+// the bits fixed while the vehicle stays on its edge: mask toward the next edge, next-edge closure flag
+constexpr uint32_t kLdEdgeBits = 0xFF000010u;
+// lane word for a vehicle entering route entry r (mask from the route entry, closure flag from the bitset)
+__device__ __forceinline__ uint32_t ld_for_entry(const Params &p, uint32_t r, uint32_t lane) {
+  const uint32_t ent = __ldg(p.route + r);
+  const uint32_t nx = (__ldg(p.nclo + (r >> 5)) >> (r & 31)) & 1u;
+  return (ent & 0xFF000000u) | (nx << 4) | lane;
+}
+
 // ---------------------------------------------------------------- lane map
 // bit 7 of each byte of the result is set iff that byte of w is not 0xFF
 __device__ __forceinline__ uint32_t occupied_bits(uint32_t w) {
@@ -168,27 +182,33 @@ __device__ __forceinline__ void load_batch(const uint8_t *row, int c, int hi, Ba
   b.q[3] = (c + 48 <= hi) ? __ldcg(reinterpret_cast<const uint4 *>(row + c + 48)) : none;
 }
 // First occupied cell in [lo, hi] within the batch starting at cell c, or -1.
-// Branch-free: every word is tested and the lowest hit kept by selects; only
-// the first 16-byte chunk can hold cells below lo (lo lies in it for the first
-// batch of a scan, below it for later batches), and a first hit beyond hi
-// means there is none in range.
+// Cells below lo (only the first 16-byte chunk can hold them: lo lies in it for
+// the first batch of a scan, below it for later batches) are made to look
+// empty; empty chunks are recognised with three-input ANDs, and only the first
+// non-empty chunk is searched byte by byte.  A first hit beyond hi means there
+// is none in range.
 __device__ __forceinline__ int check_batch(const Batch &b, int c, int lo, int hi) {
-  const uint32_t w[16] = {b.q[0].x, b.q[0].y, b.q[0].z, b.q[0].w, b.q[1].x, b.q[1].y, b.q[1].z, b.q[1].w,
-                          b.q[2].x, b.q[2].y, b.q[2].z, b.q[2].w, b.q[3].x, b.q[3].y, b.q[3].z, b.q[3].w};
-  int fk = -1;
-  uint32_t fm = 0u;
+  uint32_t w[16] = {b.q[0].x, b.q[0].y, b.q[0].z, b.q[0].w, b.q[1].x, b.q[1].y, b.q[1].z, b.q[1].w,
+                    b.q[2].x, b.q[2].y, b.q[2].z, b.q[2].w, b.q[3].x, b.q[3].y, b.q[3].z, b.q[3].w};
 #pragma unroll
-  for (int k = 15; k >= 0; --k) {
-    uint32_t m = occupied_bits(w[k]);
-    if (k < 4) {
-      const int d = lo - (c + 4 * k);
-      m = d <= 0 ? m : (d >= 4 ? 0u : (m & (0xFFFFFFFFu << (8 * d))));
-    }
-    fk = m ? k : fk;
-    fm = m ? m : fm;
+  for (int k = 0; k < 4; ++k) {
+    const int d = lo - (c + 4 * k);
+    w[k] |= d <= 0 ? 0u : (d >= 4 ? 0xFFFFFFFFu : ((1u << (8 * d)) - 1u));
   }
-  const int first = c + 4 * fk + ((__ffs(fm) - 1) >> 3);
-  return (fk < 0 || first > hi) ? -1 : first;
+  const bool f0 = (w[0] & w[1] & w[2] & w[3]) != 0xFFFFFFFFu;
+  const bool f1 = (w[4] & w[5] & w[6] & w[7]) != 0xFFFFFFFFu;
+  const bool f2 = (w[8] & w[9] & w[10] & w[11]) != 0xFFFFFFFFu;
+  const bool f3 = (w[12] & w[13] & w[14] & w[15]) != 0xFFFFFFFFu;
+  if (!(f0 || f1 || f2 || f3)) return -1;
+  const int j = f0 ? 0 : (f1 ? 1 : (f2 ? 2 : 3));
+  const uint32_t a0 = f0 ? w[0] : (f1 ? w[4] : (f2 ? w[8] : w[12]));
+  const uint32_t a1 = f0 ? w[1] : (f1 ? w[5] : (f2 ? w[9] : w[13]));
+  const uint32_t a2 = f0 ? w[2] : (f1 ? w[6] : (f2 ? w[10] : w[14]));
+  const uint32_t a3 = f0 ? w[3] : (f1 ? w[7] : (f2 ? w[11] : w[15]));
+  const int t = a0 != 0xFFFFFFFFu ? 0 : (a1 != 0xFFFFFFFFu ? 1 : (a2 != 0xFFFFFFFFu ? 2 : 3));
+  const uint32_t a = t == 0 ? a0 : (t == 1 ? a1 : (t == 2 ? a2 : a3));
+  const int first = c + 16 * j + 4 * t + ((__ffs(occupied_bits(a)) - 1) >> 3);
+  return first > hi ? -1 : first;
 }
 // First occupied cell of row[lo..hi] (inclusive), continuing from a batch
 // already loaded at lo & ~15; -1 if none.  Rows are 16-byte aligned and padded.
@@ -278,7 +298,7 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t *counter, bool pred) {
 __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const Veh &w, uint32_t &c_lce) {
   const EdgeMeta &em = w.em;
   const int nl = lanes_of(em.cnl);
-  const int lane = (int)(w.ld & 0xFFu);
+  const int lane = ld_lane(w.ld);
   const int dir = (k & 1) ? -1 : 1;
   const int lt = lane + dir;
   if (lt < 0 || lt >= nl) return -1;
@@ -291,8 +311,7 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
   const uint8_t *orow = cur + em.row0 + (uint32_t)lane * stride;
   const int hi = min(cell + H, C - 1);
   const int lo_t = max(0, cell - L + 1);     // target-lane cells from the lateral-overlap window on
-  const uint32_t ent = has_next ? __ldg(p.route + w.rc) : 0xFFFFFFFFu;
-  const bool next_clo = has_next && ((__ldg(p.nclo + (w.rc >> 5)) >> (w.rc & 31)) & 1u);
+  const bool next_clo = has_next && ld_nxclo(w.ld);
   const float mprob = __ldg(p.mtab + (C - 1 - cell));
   Batch bt, bo;
   load_batch(trow, lo_t & ~15, hi, bt);
@@ -300,7 +319,7 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
   // is possible: skip the own-lane fetch
   const bool own_scan = cell + 1 <= hi && v > 0.0f;
   if (own_scan) load_batch(orow, (cell + 1) & ~15, hi, bo);
-  uint32_t mask = ent >> MANTA_EDGE_BITS;
+  uint32_t mask = has_next ? ld_mask(w.ld) : 0xFFu;
   int obst = -1;
   bool closed_here = false;
   if (closable(em)) {
@@ -424,7 +443,7 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, cons
   Scan s;
   s.kind = SC_FREE; s.cL = 0; s.vL = 0.0f; s.reached_own = false; s.stop_only = false; s.e2 = MANTA_NONE;
   const int limit = cell + p.H;
-  int base = 0, pos = cell + 1, sl = (int)(w.ld & 0xFFu);
+  int base = 0, pos = cell + 1, sl = ld_lane(w.ld);
   uint32_t r = w.rc, se = w.e;
   EdgeMeta sm = w.em;
   bool own = true;
@@ -583,7 +602,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
         if (s != MANTA_NONE) {
           w = load_veh(p, s);
           if (w.pcell != MANTA_NONE) nxt[w.pcell] = (uint8_t)MANTA_EMPTY;
-          cand = lanes_of(w.em.cnl) >= 2;
+          // only vehicles that can change lanes this step join the queue: the
+          // step's direction must point at a lane, and either the vehicle moves
+          // (a discretionary change needs a slower leader) or a mandatory
+          // change is possible (lane not allowed, closures here or next)
+          const int nl = lanes_of(w.em.cnl), ln = ld_lane(w.ld);
+          const int lt = ln + ((k & 1) ? -1 : 1);
+          cand = nl >= 2 && lt >= 0 && lt < nl &&
+                 (w.v > 0.0f || !((ld_mask(w.ld) >> ln) & 1u) || closable(w.em) || ld_nxclo(w.ld));
           if (cand) w.pcell = s;          // the queue entry carries the slot in pcell
         }
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
@@ -639,11 +665,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
         const EdgeMeta &em = w.em;
         const uint32_t stride = stride_of(cells_of(em.cnl));
         const uint32_t cell = (uint32_t)(int)floorf(w.x);
-        const uint32_t lo = w.ld & 0xFFu, ln = (w.ld >> 16) & 0xFFu;
+        const uint32_t lo = (uint32_t)ld_lane(w.ld), ln = (w.ld >> 16) & 0xFFu;
         const uint32_t a = em.row0 + lo * stride + cell, b = em.row0 + ln * stride + cell;
         cur[b] = cur[a];
         cur[a] = (uint8_t)MANTA_EMPTY;
-        p.veh[s].ld = (w.ld & 0x0000FF00u) | ln;
+        p.veh[s].ld = (w.ld & (kLdEdgeBits | 0x0000FF00u)) | ln;
         c_lc++;
       }
       if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
@@ -690,8 +716,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       if (s == MANTA_NONE) continue;
       Veh w = load_veh(p, s);
       const float x = w.x, v = w.v;
-      const int lane = (int)(w.ld & 0xFFu);
-      const uint32_t dwell = (w.ld >> 8) & 0xFFu;
+      const int lane = ld_lane(w.ld);
+      const uint32_t dwell = ld_dwell(w.ld);
       const EdgeMeta em = w.em;
       const int C = (int)cells_of(em.cnl);
       const int cls = class_of(em.cnl);
@@ -770,7 +796,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
         p.req_key[rq_g] = ((unsigned long long)tag << 32) | w.id;
       } else if (!arrive) {
         w.x = xn; w.v = vn;
-        w.ld = (uint32_t)lane | (dwn << 8);
+        w.ld = (w.ld & kLdEdgeBits) | (uint32_t)lane | (dwn << 8);
         w.pcell = gcell;
         store_veh_state(p, s, w);
         nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xn)] = speed_code(vn);
@@ -807,7 +833,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       const unsigned long long dk = __ldcg(p.dep_key + e2);
       const EdgeMeta em2 = load_em(p, e2);
       Veh w = load_veh(p, s);
-      const int lane = (int)(w.ld & 0xFFu);
+      const int lane = ld_lane(w.ld);
       const EdgeMeta em = w.em;
       const uint32_t stride = stride_of(cells_of(em.cnl));
       bool win_it = min_competitor(p, o0, o1, gown, tgt, tag) > w.id;
@@ -825,7 +851,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
         vf = __ldcg(p.req_v + i);
         const uint32_t l2 = tgt - lb2;
         w.e = e2; w.rc = w.rc + 1u;
-        w.ld = l2;
+        w.ld = ld_for_entry(p, w.rc, l2);
         w.em = em2;
         nxt[em2.row0 + l2 * stride_of(cells_of(em2.cnl)) + (uint32_t)(int)floorf(xf)] = speed_code(vf);
         ef = e2;
@@ -833,7 +859,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
         const int C = (int)cells_of(em.cnl);
         xf = fmaxf(w.x, __int2float_rn(C - 1));
         vf = 0.0f;
-        w.ld = (uint32_t)lane | (__ldcg(p.req_dw + i) << 8);
+        w.ld = (w.ld & kLdEdgeBits) | (uint32_t)lane | (__ldcg(p.req_dw + i) << 8);
         nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xf)] = speed_code(vf);
         ef = w.e;
       }
@@ -865,7 +891,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
         const EdgeMeta em = load_em(p, e);
         Veh w;
         w.x = 0.0f; w.v = 0.0f; w.id = j; w.rc = __ldg(p.route_off + j); w.rend = __ldg(p.route_off + j + 1u);
-        w.e = e; w.ld = 0u; w.pcell = MANTA_NONE; w.em = em;
+        w.e = e; w.ld = ld_for_entry(p, w.rc, 0u); w.pcell = MANTA_NONE; w.em = em;
         store_veh(p, s, w);
         nxt[em.row0] = speed_code(0.0f);
         atomicAdd(p.entry + e, 1u);
