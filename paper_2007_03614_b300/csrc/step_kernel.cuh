@@ -187,7 +187,7 @@ __device__ __forceinline__ void load_batch(const uint8_t *row, int c, int hi, Ba
 // empty; empty chunks are recognised with three-input ANDs, and only the first
 // non-empty chunk is searched byte by byte.  A first hit beyond hi means there
 // is none in range.
-__device__ __forceinline__ int check_batch(const Batch &b, int c, int lo, int hi) {
+__device__ __forceinline__ int check_batch(const Batch &b, int c, int lo, int hi, uint32_t &byte) {
   uint32_t w[16] = {b.q[0].x, b.q[0].y, b.q[0].z, b.q[0].w, b.q[1].x, b.q[1].y, b.q[1].z, b.q[1].w,
                     b.q[2].x, b.q[2].y, b.q[2].z, b.q[2].w, b.q[3].x, b.q[3].y, b.q[3].z, b.q[3].w};
 #pragma unroll
@@ -207,31 +207,33 @@ __device__ __forceinline__ int check_batch(const Batch &b, int c, int lo, int hi
   const uint32_t a3 = f0 ? w[3] : (f1 ? w[7] : (f2 ? w[11] : w[15]));
   const int t = a0 != 0xFFFFFFFFu ? 0 : (a1 != 0xFFFFFFFFu ? 1 : (a2 != 0xFFFFFFFFu ? 2 : 3));
   const uint32_t a = t == 0 ? a0 : (t == 1 ? a1 : (t == 2 ? a2 : a3));
-  const int first = c + 16 * j + 4 * t + ((__ffs(occupied_bits(a)) - 1) >> 3);
+  const int bpos = (__ffs(occupied_bits(a)) - 1) >> 3;
+  const int first = c + 16 * j + 4 * t + bpos;
+  byte = (a >> (8 * bpos)) & 0xFFu;          // the speed code, already in registers
   return first > hi ? -1 : first;
 }
 // First occupied cell of row[lo..hi] (inclusive), continuing from a batch
 // already loaded at lo & ~15; -1 if none.  Rows are 16-byte aligned and padded.
-__device__ __forceinline__ int scan_from(const uint8_t *row, int lo, int hi, Batch &b) {
+__device__ __forceinline__ int scan_from(const uint8_t *row, int lo, int hi, Batch &b, uint32_t &byte) {
   int c = lo & ~15;
   for (;;) {
-    const int r = check_batch(b, c, lo, hi);
+    const int r = check_batch(b, c, lo, hi, byte);
     if (r >= 0) return r;
     c += 64;
     if (c > hi) return -1;
     load_batch(row, c, hi, b);
   }
 }
-__device__ __forceinline__ int first_up(const uint8_t *row, int lo, int hi) {
+__device__ __forceinline__ int first_up(const uint8_t *row, int lo, int hi, uint32_t &byte) {
   if (lo > hi) return -1;
   Batch b;
   load_batch(row, lo & ~15, hi, b);
-  return scan_from(row, lo, hi, b);
+  return scan_from(row, lo, hi, b, byte);
 }
 
 // Last occupied cell in row[lo..hi] (scanning downward from hi) or -1;
 // four 16-byte chunks per round trip, each block tested branch-free.
-__device__ __forceinline__ int first_down(const uint8_t *row, int hi, int lo) {
+__device__ __forceinline__ int first_down(const uint8_t *row, int hi, int lo, uint32_t &byte) {
   if (lo > hi) return -1;
   const uint4 none = make_uint4(~0u, ~0u, ~0u, ~0u);
   for (int c = hi & ~15; c + 15 >= lo; c -= 64) {
@@ -252,7 +254,9 @@ __device__ __forceinline__ int first_down(const uint8_t *row, int hi, int lo) {
         const int dl = lo - base, dh = base + 3 - hi;
         m = dl <= 0 ? m : (dl >= 4 ? 0u : (m & (0xFFFFFFFFu << (8 * dl))));
         m = dh <= 0 ? m : (dh >= 4 ? 0u : (m & (0xFFFFFFFFu >> (8 * dh))));
-        const int hit = base + ((31 - __clz(m)) >> 3);
+        const int bp = (31 - __clz(m)) >> 3;
+        const int hit = base + bp;
+        byte = (m && hit > best) ? ((w[t] >> (8 * bp)) & 0xFFu) : byte;
         best = m ? hit : best;
       }
     }
@@ -262,7 +266,6 @@ __device__ __forceinline__ int first_down(const uint8_t *row, int hi, int lo) {
   return -1;
 }
 
-__device__ __forceinline__ uint8_t cell_byte(const uint8_t *row, int c) { return __ldcg(row + c); }
 
 __device__ __forceinline__ EdgeSig load_sig(const Params &p, uint32_t e) {
   const int2 w = __ldg(reinterpret_cast<const int2 *>(p.es) + e);
@@ -355,30 +358,34 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
     return -1;
   }
   int c1, ca;
+  uint32_t bc1 = 0, bca = 0, bcb = 0;
   if (mandatory) {
     const float u1 = uni(p.seed, w.id, k, 0);
     // Eq. 2 at the distance to the end of the edge, or to the obstacle of a closed lane
     const float mp = closed_here ? __ldg(p.mtab + (obst - 1 - cell)) : mprob;
     if (!(u1 < mp)) return -1;
-    c1 = scan_from(trow, lo_t, hi, bt);
+    c1 = scan_from(trow, lo_t, hi, bt, bc1);
     ca = c1;
+    bca = bc1;
   } else {
     if (!own_scan) return -1;
-    const int co = scan_from(orow, cell + 1, hi, bo);
+    uint32_t bco;
+    const int co = scan_from(orow, cell + 1, hi, bo, bco);
     if (co < 0) return -1;
-    if (!(speed_decode(cell_byte(orow, co)) < v)) return -1;
+    if (!(speed_decode(bco) < v)) return -1;
     const int own_gap = co - L - cell;
-    c1 = scan_from(trow, lo_t, hi, bt);
-    ca = (c1 >= 0 && c1 <= cell + L - 1) ? first_up(trow, cell + L, hi) : c1;
+    c1 = scan_from(trow, lo_t, hi, bt, bc1);
+    if (c1 >= 0 && c1 <= cell + L - 1) ca = first_up(trow, cell + L, hi, bca);
+    else { ca = c1; bca = bc1; }
     if (ca >= 0 && !(ca - L - cell > own_gap)) return -1;
   }
   c_lce++;
   if (c1 >= 0 && c1 <= cell + L - 1) return -1;     // lateral overlap
-  const int cb = first_down(trow, cell - L, max(0, cell - H));
+  const int cb = first_down(trow, cell - L, max(0, cell - H), bcb);
   const float g = v < p.g_split ? p.g_low : p.g_high;
   const float alpha = p.alpha_lo + (p.alpha_hi - p.alpha_lo) * uni(p.seed, w.id, 0, 3);
   if (ca >= 0) {
-    const float va = speed_decode(cell_byte(trow, ca));
+    const float va = speed_decode(bca);
     const float eps_a = irwin_hall(p.seed, w.id, k, 1);
     float t = g + alpha * v;          // Eq. 3, alpha_a = alpha_i
     t = t + alpha * (v - va);
@@ -386,7 +393,7 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
     if (!(__int2float_rn(ca - L - cell) >= glead)) return -1;
   }
   if (cb >= 0) {
-    const float vb = speed_decode(cell_byte(trow, cb));
+    const float vb = speed_decode(bcb);
     const float eps_b = irwin_hall(p.seed, w.id, k, 2);
     float t = g + alpha * v;          // Eq. 4, alpha_b = alpha_i
     t = t + alpha * (v - vb);
@@ -456,9 +463,10 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, cons
   if (obst >= 0 && obst <= limit) {
     // only the cells before the obstacle can hold the leader
     const uint8_t *row = cur + sm.row0 + (uint32_t)sl * stride_of(cells_of(sm.cnl));
-    const int c = first_up(row, cell + 1, obst - 1);
+    uint32_t byte = 0;
+    const int c = first_up(row, cell + 1, obst - 1, byte);
     if (c >= 0) {
-      s.kind = SC_LEADER; s.cL = c; s.vL = speed_decode(cell_byte(row, c));
+      s.kind = SC_LEADER; s.cL = c; s.vL = speed_decode(byte);
       c_scan += (uint32_t)(c - cell);
     } else {
       s.kind = SC_VIRTUAL; s.cL = obst + p.L - 1; s.vL = 0.0f;
@@ -488,9 +496,10 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, cons
       sm2 = load_em(p, nent & MANTA_EDGE_MASK);
     }
     if (scan) {
-      const int c = scan_from(row, pos - base, hi_pos - base, b);
+      uint32_t byte = 0;
+      const int c = scan_from(row, pos - base, hi_pos - base, b, byte);
       if (c >= 0) {
-        s.kind = SC_LEADER; s.cL = base + c; s.vL = speed_decode(cell_byte(row, c));
+        s.kind = SC_LEADER; s.cL = base + c; s.vL = speed_decode(byte);
         c_scan += (uint32_t)(s.cL - cell);
         return s;
       }
@@ -690,7 +699,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       const int C = (int)cells_of(em.cnl);
       const int need = min(C, L + p.s0c[class_of(em.cnl)]);
       if (closable(em) && lane_closed(p, __ldg(p.lane_base + e), k)) continue;
-      if (first_up(cur + em.row0, 0, need - 1) >= 0) continue;
+      uint32_t byte;
+      if (first_up(cur + em.row0, 0, need - 1, byte) >= 0) continue;
       const uint32_t j = __ldg(p.q_trip + __ldg(p.q_off + e) + __ldcg(p.q_pos + e));
       p.dep_key[e] = ((unsigned long long)tag << 32) | j;
     }
