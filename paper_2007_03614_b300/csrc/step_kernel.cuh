@@ -474,13 +474,17 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, cons
     }
     return s;
   }
+  // route entry r + 1, fetched one segment ahead so that crossing a node
+  // costs one round trip (the next row) rather than two (entry, then record)
+  uint32_t nent = 0;
+  if ((int)cells_of(sm.cnl) <= limit && r + 1u < w.rend) nent = __ldg(p.route + r + 1u);
   for (;;) {
     const int segC = (int)cells_of(sm.cnl);
     const int hi_pos = min(limit, base + segC - 1);
     const int B = base + segC;
     const bool reach = (B <= limit) && (r + 1u < w.rend);
-    uint32_t nent = 0;
-    if (reach) nent = __ldg(p.route + r + 1u);
+    uint32_t nent2 = 0;
+    if (reach && r + 2u < w.rend) nent2 = __ldg(p.route + r + 2u);
     const uint8_t *row = cur + sm.row0 + (uint32_t)sl * stride_of((uint32_t)segC);
     Batch b;
     const bool scan = pos <= hi_pos;
@@ -531,6 +535,7 @@ __device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, cons
     sm = sm2;
     sl = min(sl, lanes_of(sm.cnl) - 1);
     own = false;
+    nent = nent2;
   }
 }
 
