@@ -94,6 +94,21 @@ def _dist():
     return rank, world
 
 
+def aggregate_ranks(elapsed_s: float, updates: int, device="cpu"):
+    """Whole-job figures over the ranks of a replica run: the slowest rank's
+    time and the sum of every rank's vehicle updates (each rank simulates its
+    own replica; nothing else is exchanged).  Single process: unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(elapsed_s), float(updates)
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def workload(seed=2):
     from paper_2007_03614_b300 import synth
     net = synth.metro_network(seed=seed)
@@ -221,15 +236,7 @@ def run_gpu(args):
     elapsed = sum(times)
     d = {k: s1[k] - s0[k] for k in ("vehicle_updates", "cells_scanned", "route_reads", "lc_evals", "clamps",
                                     "lane_changes", "departed", "arrived")}
-    if world > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        u = torch.tensor([d["vehicle_updates"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_updates = float(u.item())
-    else:
-        total_updates = float(d["vehicle_updates"])
+    elapsed, total_updates = aggregate_ranks(elapsed, d["vehicle_updates"], device="cuda")
     morning = None
     if T0_STEP + (args.warmup + args.steps) * chunk >= T0_STEP + MORNING_STEPS:
         morning = None  # filled by the e2e run below, which always simulates the whole morning
