@@ -204,6 +204,25 @@ def run_gpu(args):
                           "updates_in_profiled_launches": st["vehicle_updates"] - u0, "stats": st,
                           "phase_ms": [float(x) for x in sim.phase_times_ms()]}))
         return
+    if args.profile_peak:
+        # the headline workload from 05:00 to 07:45 in untimed launches of 1800
+        # steps (eleven), then `--steps` launches of `--chunk` steps in the
+        # congested peak: the case for counter captures of the peak state
+        sim = manta.Sim(net, stream=stream, t0_step=T0_STEP)
+        sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+        n = int(7.75 * 3600 / 0.5) - T0_STEP
+        while n > 0:
+            sim.step(min(1800, n))
+            n -= 1800
+        u0 = sim.stats()["vehicle_updates"]
+        ph0 = sim.phase_times_ms()
+        for _ in range(args.steps):
+            sim.step(chunk)
+        st = sim.stats()
+        print(json.dumps({"profile_peak": True, "kernel_sha256": kernel_hash(),
+                          "updates_in_profiled_launches": st["vehicle_updates"] - u0, "stats": st,
+                          "phase_ms": [float(x) - float(y) for x, y in zip(sim.phase_times_ms(), ph0)]}))
+        return
     # ---- device-resident run (the headline value) ----
     sim = manta.Sim(net, stream=stream, t0_step=T0_STEP)
     sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
@@ -447,6 +466,9 @@ def main():
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: 07:30-08:00 trips, 1200-step warm-up launch, then --steps launches")
+    ap.add_argument("--profile-peak", action="store_true",
+                    help="counter-capture case: the headline workload run to 07:45, then --steps launches "
+                         "of --chunk steps")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("need --steps >= 1 and --warmup >= 0")

@@ -25,9 +25,12 @@
 #include "sim.cuh"
 
 #ifndef MANTA_MIN_BLOCKS_PER_SM
-#define MANTA_MIN_BLOCKS_PER_SM 2
+#define MANTA_MIN_BLOCKS_PER_SM 1
 #endif
-constexpr int kBlock = 256;
+#ifndef MANTA_BLOCK
+#define MANTA_BLOCK 384
+#endif
+constexpr int kBlock = MANTA_BLOCK;
 constexpr int kMinBlocksPerSM = MANTA_MIN_BLOCKS_PER_SM;
 
 __device__ __forceinline__ uint64_t globaltimer() {
@@ -403,9 +406,12 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
   return lt;
 }
 
-// Lowest id among the other crossing requests for target lane `tgt` posted
-// this step (tag) by the in-lanes [o0, o1) of a node, excluding lane `skip`;
-// MANTA_NONE if there is none.  Eight in-lanes per round trip.
+// Key of lane l of edge e as a request target.
+__device__ __forceinline__ uint32_t target_key(uint32_t e, uint32_t l) { return (e << 4) | l; }
+
+// Lowest id among the other crossing requests for target lane key `tgt`
+// posted this step (tag) by the in-lanes [o0, o1) of a node, excluding lane
+// `skip`; MANTA_NONE if there is none.  Eight in-lanes per round trip.
 __device__ __forceinline__ uint32_t min_competitor(const Params &p, uint32_t o0, uint32_t o1, uint32_t skip,
                                                    uint32_t tgt, uint32_t tag) {
   uint32_t best = MANTA_NONE;
@@ -436,107 +442,164 @@ struct Scan {
   float vL;
   bool reached_own;  // the scan examined the vehicle's own head node
   bool stop_only;    // ... and only a stop sign (no permit) held it there
-  uint32_t e2;       // next route edge, when read
+  uint32_t nt_own;   // type of the own head node, when reached
+  uint32_t e2;       // next route edge, when reached
+  uint32_t e2cnl;    // its cells | lanes | class word, when reached
 };
 
-// Walk the lane map along the route from the cell ahead, at most H cells,
-// stopping at the first occupied byte or at a node that holds the vehicle
-// (red signal; stop sign without the permit, or any stop sign beyond the own
-// node).  A lane not allowed for the next edge does not hold the vehicle.
-// The next segment's route entry and edge record are fetched while the
-// current row is scanned.
-__device__ Scan leader_scan(const Params &p, const uint8_t *cur, int64_t k, const Veh &w, int cell,
-                            uint32_t &c_scan, uint32_t &c_rr) {
-  Scan s;
-  s.kind = SC_FREE; s.cL = 0; s.vL = 0.0f; s.reached_own = false; s.stop_only = false; s.e2 = MANTA_NONE;
-  const int limit = cell + p.H;
-  int base = 0, pos = cell + 1, sl = ld_lane(w.ld);
-  uint32_t r = w.rc, se = w.e;
-  EdgeMeta sm = w.em;
-  bool own = true;
-  // a closed own lane holds a stationary obstacle from mid-edge on (cell C / 2)
-  int obst = -1;
-  if (closable(sm)) {
-    const int half = (int)cells_of(sm.cnl) / 2;
-    if (cell < half && lane_closed(p, __ldg(p.lane_base + w.e) + (uint32_t)sl, k)) obst = half;
-  }
-  if (obst >= 0 && obst <= limit) {
-    // only the cells before the obstacle can hold the leader
-    const uint8_t *row = cur + sm.row0 + (uint32_t)sl * stride_of(cells_of(sm.cnl));
-    uint32_t byte = 0;
-    const int c = first_up(row, cell + 1, obst - 1, byte);
-    if (c >= 0) {
-      s.kind = SC_LEADER; s.cL = c; s.vL = speed_decode(byte);
-      c_scan += (uint32_t)(c - cell);
-    } else {
-      s.kind = SC_VIRTUAL; s.cL = obst + p.L - 1; s.vL = 0.0f;
-      c_scan += (uint32_t)(obst - 1 - cell);
-    }
-    return s;
-  }
-  // route entry r + 1, fetched one segment ahead so that crossing a node
-  // costs one round trip (the next row) rather than two (entry, then record)
-  uint32_t nent = 0;
-  if ((int)cells_of(sm.cnl) <= limit && r + 1u < w.rend) nent = __ldg(p.route + r + 1u);
-  for (;;) {
-    const int segC = (int)cells_of(sm.cnl);
-    const int hi_pos = min(limit, base + segC - 1);
-    const int B = base + segC;
-    const bool reach = (B <= limit) && (r + 1u < w.rend);
-    uint32_t nent2 = 0;
-    if (reach && r + 2u < w.rend) nent2 = __ldg(p.route + r + 2u);
-    const uint8_t *row = cur + sm.row0 + (uint32_t)sl * stride_of((uint32_t)segC);
-    Batch b;
-    const bool scan = pos <= hi_pos;
-    if (scan) load_batch(row, (pos - base) & ~15, hi_pos - base, b);
-    uint8_t nt = 0;
-    EdgeSig sig;
-    sig.cyc = 0; sig.off = 0; sig.gs = 0; sig.gl = 0;
-    EdgeMeta sm2;
-    sm2.row0 = 0; sm2.cnl = 0; sm2.lim = 0.0f; sm2.dst = 0;
-    if (reach) {
-      nt = __ldg(p.ntype + node_of(sm));
-      sig = load_sig(p, se);
-      sm2 = load_em(p, nent & MANTA_EDGE_MASK);
-    }
-    if (scan) {
+// A leader scan in progress.  The walk goes along the route from the cell
+// ahead, at most H cells, and stops at the first occupied byte or at a node
+// that holds the vehicle (red signal; stop sign without the permit, or any
+// stop sign beyond the own node).  A lane not allowed for the next edge does
+// not hold the vehicle.  Each round trip fetches one batch of the current
+// row; the batch that ends a segment also fetches the head node's type, the
+// segment's signal window, the next edge's record and the route entry after
+// it, so crossing a node costs no extra round trip.
+struct Walk {
+  int limit;         // last route-relative cell within the horizon
+  int base;          // route-relative cell of the segment's first cell
+  int pos;           // next route-relative cell to examine
+  int sl;            // lane on the segment
+  uint32_t r;        // route entry of the segment
+  uint32_t se;       // its edge
+  uint32_t nent;     // route entry r + 1 (fetched one segment ahead)
+  EdgeMeta sm;       // record of the segment's edge
+  bool own;          // the segment is the vehicle's own edge
+};
+// What one round trip brings: a vehicle record (b.q[0..2]) or a row batch,
+// plus the node data when the batch ends a segment.
+struct Fetch {
+  Batch b;
+  uint32_t nt;
+  EdgeSig sig;
+  EdgeMeta sm2;
+  uint32_t nent2;
+};
+
+__device__ __forceinline__ Veh unpack_veh(const Batch &b) {
+  Veh w;
+  w.x = __uint_as_float(b.q[0].x); w.v = __uint_as_float(b.q[0].y); w.id = b.q[0].z; w.rc = b.q[0].w;
+  w.rend = b.q[1].x; w.e = b.q[1].y; w.ld = b.q[1].z; w.pcell = b.q[1].w;
+  w.em.row0 = b.q[2].x; w.em.cnl = b.q[2].y; w.em.lim = __uint_as_float(b.q[2].z); w.em.dst = b.q[2].w;
+  return w;
+}
+
+// Sets up the walk of vehicle w from `cell`.  A closed own lane holds a
+// stationary obstacle from mid-edge on (cell C / 2); when it lies within the
+// horizon only the cells before it can hold the leader, and the scan is
+// completed here (returns true).
+__device__ __forceinline__ bool walk_start(const Params &p, const uint8_t *cur, int64_t k, const Veh &w, int cell,
+                                           Walk &wk, Scan &s, uint32_t &c_scan) {
+  s.kind = SC_FREE; s.cL = 0; s.vL = 0.0f; s.reached_own = false; s.stop_only = false;
+  s.nt_own = 0u; s.e2 = MANTA_NONE; s.e2cnl = 0u;
+  wk.limit = cell + p.H; wk.base = 0; wk.pos = cell + 1; wk.sl = ld_lane(w.ld);
+  wk.r = w.rc; wk.se = w.e; wk.sm = w.em; wk.own = true; wk.nent = 0u;
+  const int C = (int)cells_of(w.em.cnl);
+  if (closable(w.em)) {
+    const int half = C / 2;
+    if (cell < half && half <= wk.limit && lane_closed(p, __ldg(p.lane_base + w.e) + (uint32_t)wk.sl, k)) {
+      const uint8_t *row = cur + w.em.row0 + (uint32_t)wk.sl * stride_of((uint32_t)C);
       uint32_t byte = 0;
-      const int c = scan_from(row, pos - base, hi_pos - base, b, byte);
+      const int c = first_up(row, cell + 1, half - 1, byte);
       if (c >= 0) {
-        s.kind = SC_LEADER; s.cL = base + c; s.vL = speed_decode(byte);
-        c_scan += (uint32_t)(s.cL - cell);
-        return s;
+        s.kind = SC_LEADER; s.cL = c; s.vL = speed_decode(byte);
+        c_scan += (uint32_t)(c - cell);
+      } else {
+        s.kind = SC_VIRTUAL; s.cL = half + p.L - 1; s.vL = 0.0f;
+        c_scan += (uint32_t)(half - 1 - cell);
       }
+      return true;
     }
-    if (B > limit) { c_scan += (uint32_t)p.H; return s; }
-    if (r + 1u >= w.rend) { c_scan += (uint32_t)(B - 1 - cell); return s; }
-    c_rr++;
-    const uint32_t n = node_of(sm);
-    const uint32_t e2 = nent & MANTA_EDGE_MASK;
-    bool blocked = false;
-    if (nt == 2 && !is_green(sig, k)) blocked = true;
-    if (closable(sm2) && lane_closed(p, __ldg(p.lane_base + e2) + (uint32_t)min(sl, lanes_of(sm2.cnl) - 1), k))
-      blocked = true;                    // no entry into a closed lane
-    if (own) {
-      const bool stop_np = (nt == 1) && (ldv(p.permit + n) != w.id);
-      s.reached_own = true;
-      s.stop_only = stop_np;
-      s.e2 = e2;
-      if (stop_np) blocked = true;
-    } else if (nt == 1) {
-      blocked = true;
-    }
-    if (blocked) {
-      s.kind = SC_VIRTUAL; s.cL = B + p.L - 1; s.vL = 0.0f;
-      c_scan += (uint32_t)(B - 1 - cell);
-      return s;
-    }
-    ++r; base = B; pos = B; se = e2;
-    sm = sm2;
-    sl = min(sl, lanes_of(sm.cnl) - 1);
-    own = false;
-    nent = nent2;
   }
+  if (C <= wk.limit && w.rc + 1u < w.rend) wk.nent = __ldg(p.route + w.rc + 1u);
+  return false;
+}
+
+// Issues the loads of the walk's next round trip.
+__device__ __forceinline__ void walk_issue(const Params &p, const uint8_t *cur, const Veh &w, const Walk &wk,
+                                           Fetch &f) {
+  const int segC = (int)cells_of(wk.sm.cnl);
+  const int hi = min(wk.limit, wk.base + segC - 1) - wk.base;   // row-relative
+  const int lo = wk.pos - wk.base;
+  const int c0 = lo & ~15;
+  if (lo <= hi) load_batch(cur + wk.sm.row0 + (uint32_t)wk.sl * stride_of((uint32_t)segC), c0, hi, f.b);
+  const bool last = lo > hi || c0 + 64 > hi;
+  if (last && wk.base + segC <= wk.limit && wk.r + 1u < w.rend) {
+    f.nt = __ldg(p.ntype + node_of(wk.sm));
+    f.sig = load_sig(p, wk.se);
+    f.sm2 = load_em(p, wk.nent & MANTA_EDGE_MASK);
+    f.nent2 = wk.r + 2u < w.rend ? __ldg(p.route + wk.r + 2u) : 0u;
+  }
+}
+
+// Consumes the round trip issued by walk_issue: returns true when the scan
+// is complete (result in s), otherwise advances the walk.
+__device__ __forceinline__ bool walk_process(const Params &p, int64_t k, const Veh &w, int cell, Walk &wk,
+                                             const Fetch &f, Scan &s, uint32_t &c_scan, uint32_t &c_rr) {
+  const int segC = (int)cells_of(wk.sm.cnl);
+  const int hi = min(wk.limit, wk.base + segC - 1) - wk.base;
+  const int lo = wk.pos - wk.base;
+  const int c0 = lo & ~15;
+  const bool last = lo > hi || c0 + 64 > hi;
+  if (lo <= hi) {
+    uint32_t byte = 0;
+    const int c = check_batch(f.b, c0, lo, hi, byte);
+    if (c >= 0) {
+      s.kind = SC_LEADER; s.cL = wk.base + c; s.vL = speed_decode(byte);
+      c_scan += (uint32_t)(s.cL - cell);
+      return true;
+    }
+    if (!last) { wk.pos = wk.base + c0 + 64; return false; }
+  }
+  const int B = wk.base + segC;
+  if (B > wk.limit) { c_scan += (uint32_t)p.H; return true; }
+  if (wk.r + 1u >= w.rend) { c_scan += (uint32_t)(B - 1 - cell); return true; }
+  c_rr++;
+  const uint32_t n = node_of(wk.sm);
+  const uint32_t e2 = wk.nent & MANTA_EDGE_MASK;
+  bool blocked = false;
+  if (f.nt == 2u && !is_green(f.sig, k)) blocked = true;
+  if (closable(f.sm2) &&
+      lane_closed(p, __ldg(p.lane_base + e2) + (uint32_t)min(wk.sl, lanes_of(f.sm2.cnl) - 1), k))
+    blocked = true;                      // no entry into a closed lane
+  if (wk.own) {
+    const bool stop_np = (f.nt == 1u) && (ldv(p.permit + n) != w.id);
+    s.reached_own = true;
+    s.stop_only = stop_np;
+    s.nt_own = f.nt;
+    s.e2 = e2;
+    s.e2cnl = f.sm2.cnl;
+    if (stop_np) blocked = true;
+  } else if (f.nt == 1u) {
+    blocked = true;
+  }
+  if (blocked) {
+    s.kind = SC_VIRTUAL; s.cL = B + p.L - 1; s.vL = 0.0f;
+    c_scan += (uint32_t)(B - 1 - cell);
+    return true;
+  }
+  wk.r = wk.r + 1u; wk.base = B; wk.pos = B; wk.se = e2;
+  wk.sm = f.sm2;
+  wk.sl = min(wk.sl, lanes_of(f.sm2.cnl) - 1);
+  wk.own = false;
+  wk.nent = f.nent2;
+  return false;
+}
+
+// Appends the n crossing requests staged in buffer q (field-major, 32 per
+// field) to the request list.  Called by the lanes in `am` (rank rk of cnt).
+__device__ __forceinline__ void flush_requests(const Params &p, const uint32_t *q, int n, unsigned am, int rk,
+                                               int cnt) {
+  uint32_t g0 = 0;
+  if (rk == 0) g0 = atomicAdd(&p.ctl->n_req, (uint32_t)n);
+  g0 = __shfl_sync(am, g0, __ffs(am) - 1);
+  for (int j = rk; j < n; j += cnt) {
+    const uint32_t o = g0 + (uint32_t)j;
+    p.req[o] = q[0 * 32 + j]; p.req_x[o] = __uint_as_float(q[1 * 32 + j]); p.req_v[o] = __uint_as_float(q[2 * 32 + j]);
+    p.req_dw[o] = q[3 * 32 + j]; p.req_g[o] = q[4 * 32 + j]; p.req_t[o] = q[5 * 32 + j]; p.req_e2[o] = q[6 * 32 + j];
+    p.req_n[o] = q[7 * 32 + j];
+  }
+  __syncwarp(am);
 }
 
 // ------------------------------------------------------------ the kernel
@@ -544,7 +607,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
   __shared__ int s_ok;
   __shared__ unsigned long long s_cnt[CNT_N];
   __shared__ float s_sab2[8];                       // 2 sqrt(a b) per road class (Eq. 1)
-  __shared__ Veh s_lcq[kBlock / 32][64];            // per-warp queue of lane-change candidates
+  // per-warp scratch, 3 KB: in P1 a queue of 64 lane-change candidates
+  // (vehicle records); in P3 the work pool (32 slots, 32 list indices) and
+  // 32 staged crossing requests (8 fields, field-major)
+  __shared__ __align__(16) uint32_t s_wbuf[kBlock / 32][64 * sizeof(Veh) / 4];
+  __shared__ int s_rqn[kBlock / 32];
   Ctl *ctl = p.ctl;
   if (threadIdx.x < CNT_N) s_cnt[threadIdx.x] = 0ull;
   if (threadIdx.x < 8) s_sab2[threadIdx.x] = 2.0f * sqrtf(p.a[threadIdx.x] * p.b[threadIdx.x]);
@@ -602,7 +669,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
     }
     {
       const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-      Veh *q = s_lcq[wid];
+      Veh *q = reinterpret_cast<Veh *>(s_wbuf[wid]);
       int qn = 0;   // warp-uniform queue length
       for (uint32_t base = gtid - (uint32_t)lane; base < nact; base += gsz) {
         const uint32_t i = base + (uint32_t)lane;
@@ -710,129 +777,216 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       p.dep_key[e] = ((unsigned long long)tag << 32) | j;
     }
     // vehicles
-    const int64_t wk = k - p.t0;
-    const int win = (wk >= 0 && wk / p.win_steps < p.n_win) ? (int)(wk / p.win_steps) : -1;
-    // warps take batches of 32 list entries from a shared counter (dynamic
-    // balance across warps); the next batch's slots load while this one runs
-    const int wl = threadIdx.x & 31;
-    uint32_t bb = 0;
-    if (wl == 0) bb = atomicAdd(&ctl->next3, 32u);
-    bb = __shfl_sync(0xFFFFFFFFu, bb, 0);
-    uint32_t s_nxt = bb + wl < nact ? __ldcg(act + bb + wl) : MANTA_NONE;
-    uint32_t bn = 0;
-    if (wl == 0) bn = atomicAdd(&ctl->next3, 32u);
-    while (bb < nact) {
-      const uint32_t i = bb + wl;
-      const uint32_t s = s_nxt;
-      bn = __shfl_sync(0xFFFFFFFFu, bn, 0);
-      s_nxt = bn + wl < nact ? __ldcg(act + bn + wl) : MANTA_NONE;
-      bb = bn;
-      if (wl == 0 && bn < nact) bn = atomicAdd(&ctl->next3, 32u);
-      if (s == MANTA_NONE) continue;
-      Veh w = load_veh(p, s);
-      const float x = w.x, v = w.v;
-      const int lane = ld_lane(w.ld);
-      const uint32_t dwell = ld_dwell(w.ld);
-      const EdgeMeta em = w.em;
-      const int C = (int)cells_of(em.cnl);
-      const int cls = class_of(em.cnl);
-      const uint32_t stride = stride_of((uint32_t)C);
-      const int cell = (int)floorf(x);
-      const uint32_t gcell = em.row0 + (uint32_t)lane * stride + (uint32_t)cell;
-      const Scan sc = leader_scan(p, cur, k, w, cell, c_scan, c_rr);
-      const float a = p.a[cls], T = p.T[cls], s0 = p.s0[cls];
-      const float v0 = em.lim * p.v0f[cls];
-      const float r1 = v / v0, r2 = r1 * r1, r4 = r2 * r2;
-      const bool has_next = w.rc + 1u < w.rend;
-      float xn, vn;
-      bool stop_in_place = false;
-      float acc = 0.0f;
-      if (sc.kind == SC_FREE) {
-        acc = a * (1.0f - r4);
-      } else {
-        const float sg = __int2float_rn(sc.cL - cell - L);
-        if (sg <= 0.0f) {
-          stop_in_place = true;
+    const int64_t kr = k - p.t0;
+    const int win = (kr >= 0 && kr / p.win_steps < p.n_win) ? (int)(kr / p.win_steps) : -1;
+    // Each lane carries one vehicle through its record fetch and a leader
+    // walk of one lane-map batch per round trip; every iteration first issues
+    // the loads of all lanes and then consumes them, and a lane whose vehicle
+    // is done takes the next one from the warp's pool at once, so lanes do
+    // not wait for the longest walk of their warp.  The pool takes chunks of
+    // list entries from a shared counter (holes dropped), the next chunk's
+    // slots loading while the pool drains.  Chunks hold 32 entries while the
+    // list is long and shrink as it runs out (guided self-scheduling), so
+    // warps finish the phase close together.
+    {
+      const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      const unsigned lt_mask = (1u << wl) - 1u;
+      const uint32_t nwarps = gridDim.x * (kBlock / 32);
+      uint32_t *ps = s_wbuf[wid], *pi = s_wbuf[wid] + 32;
+      uint32_t ch = 0, csz = 32u;
+      if (wl == 0) ch = atomicAdd(&ctl->next3, 32u);
+      ch = __shfl_sync(0xFFFFFFFFu, ch, 0);
+      uint32_t cslot = ch + wl < nact ? __ldcg(act + ch + wl) : MANTA_NONE;
+      // the chunk after it: its counter value is taken one chunk ahead, so
+      // installing a chunk never waits for the atomic (lane 0 holds it)
+      uint32_t chn = 0, cszn = 32u;
+      if (wl == 0) chn = atomicAdd(&ctl->next3, 32u);
+      uint32_t *rqb = s_wbuf[wid] + 64;
+      if (wl == 0) s_rqn[wid] = 0;
+      int pn = 0, pu = 0;         // pool size and entries taken (warp-uniform)
+      int st = 0;                 // 0 idle, 1 record requested, 2 walking
+      uint32_t s = 0, i = 0, lb = 0;
+      int cell = 0;
+      Veh w;
+      Walk wk;
+      Scan sc;
+      for (;;) {
+        __syncwarp();
+        unsigned need = __ballot_sync(0xFFFFFFFFu, st == 0);
+        while (need != 0u) {
+          if (pu == pn) {
+            if (ch >= nact) break;
+            // install the prefetched chunk, then prefetch the next one
+            const bool valid = (uint32_t)wl < csz && cslot != MANTA_NONE;
+            const unsigned vb = __ballot_sync(0xFFFFFFFFu, valid);
+            __syncwarp();
+            if (valid) {
+              const int q = __popc(vb & lt_mask);
+              ps[q] = cslot;
+              pi[q] = ch + (uint32_t)wl;
+            }
+            pn = __popc(vb);
+            pu = 0;
+            ch = __shfl_sync(0xFFFFFFFFu, chn, 0);
+            csz = __shfl_sync(0xFFFFFFFFu, cszn, 0);
+            cslot = (uint32_t)wl < csz && ch + wl < nact ? __ldcg(act + ch + wl) : MANTA_NONE;
+            if (wl == 0) {
+              const uint32_t rem = ch < nact ? nact - ch : 0u;
+              cszn = min(32u, max(4u, rem / (2u * nwarps)));
+              chn = atomicAdd(&ctl->next3, cszn);
+            }
+            __syncwarp();
+            continue;
+          }
+          const int take = min(__popc(need), pn - pu);
+          const int rank = __popc(need & lt_mask);
+          if (st == 0 && rank < take) {
+            s = ps[pu + rank];
+            i = pi[pu + rank];
+            st = 1;
+          }
+          pu += take;
+          need = __ballot_sync(0xFFFFFFFFu, st == 0);
+        }
+        if (__ballot_sync(0xFFFFFFFFu, st != 0) == 0u) break;
+        Fetch f;
+        if (st == 1) {
+          const uint4 *va = reinterpret_cast<const uint4 *>(p.veh + s);
+          f.b.q[0] = __ldcg(va); f.b.q[1] = __ldcg(va + 1); f.b.q[2] = __ldcg(va + 2);
+        } else if (st == 2) {
+          walk_issue(p, cur, w, wk, f);
+        }
+        bool fin = false;
+        if (st == 1) {
+          w = unpack_veh(f.b);
+          lb = __ldg(p.lane_base + w.e);      // needed when the vehicle is done
+          cell = (int)floorf(w.x);
+          fin = walk_start(p, cur, k, w, cell, wk, sc, c_scan);
+          st = 2;
+        } else if (st == 2) {
+          fin = walk_process(p, k, w, cell, wk, f, sc, c_scan, c_rr);
+        }
+        if (!fin) continue;
+        st = 0;
+        const float x = w.x, v = w.v;
+        const int lane = ld_lane(w.ld);
+        const uint32_t dwell = ld_dwell(w.ld);
+        const EdgeMeta em = w.em;
+        const int C = (int)cells_of(em.cnl);
+        const int cls = class_of(em.cnl);
+        const uint32_t stride = stride_of((uint32_t)C);
+        const uint32_t gcell = em.row0 + (uint32_t)lane * stride + (uint32_t)cell;
+        const float a = p.a[cls], T = p.T[cls], s0 = p.s0[cls];
+        const float v0 = em.lim * p.v0f[cls];
+        const float r1 = v / v0, r2 = r1 * r1, r4 = r2 * r2;
+        const bool has_next = w.rc + 1u < w.rend;
+        float xn, vn;
+        bool stop_in_place = false;
+        float acc = 0.0f;
+        if (sc.kind == SC_FREE) {
+          acc = a * (1.0f - r4);
         } else {
-          const float dv = v - sc.vL;
-          const float dyn = (v * dv) / s_sab2[cls];
-          float ss;
-          if (p.textbook) ss = s0 + fmaxf(0.0f, v * T + dyn);
-          else ss = (s0 + v * T) + dyn;
-          const float q = ss / sg;
-          acc = a * ((1.0f - r4) - q * q);
+          const float sg = __int2float_rn(sc.cL - cell - L);
+          if (sg <= 0.0f) {
+            stop_in_place = true;
+          } else {
+            const float dv = v - sc.vL;
+            const float dyn = (v * dv) / s_sab2[cls];
+            float ss;
+            if (p.textbook) ss = s0 + fmaxf(0.0f, v * T + dyn);
+            else ss = (s0 + v * T) + dyn;
+            const float q = ss / sg;
+            acc = a * ((1.0f - r4) - q * q);
+          }
+        }
+        if (stop_in_place) {
+          xn = x; vn = 0.0f;
+        } else {
+          const float dt = p.dt;
+          const float vt = v + acc * dt;
+          float xt, vv;
+          if (vt >= 0.0f) { xt = x + (v * dt + (0.5f * acc) * (dt * dt)); vv = vt; }
+          else { xt = x - (v * v) / (2.0f * acc); vv = 0.0f; }
+          bool has_bound = sc.kind != SC_FREE;
+          int bnd = sc.cL - L;
+          if (has_next && xt >= __int2float_rn(C)) {
+            // at most one node per step: stay within the next edge
+            const uint32_t cnl2 = sc.e2 != MANTA_NONE
+                                      ? sc.e2cnl
+                                      : load_em(p, __ldg(p.route + w.rc + 1u) & MANTA_EDGE_MASK).cnl;
+            const int cap = C + (int)cells_of(cnl2) - 1;
+            if (!has_bound || cap < bnd) { has_bound = true; bnd = cap; }
+          }
+          if (has_bound && xt > __int2float_rn(bnd)) { xn = fmaxf(x, __int2float_rn(bnd)); vn = 0.0f; c_clamp++; }
+          else { xn = xt; vn = vv; }
+        }
+        uint32_t dwn = 0;
+        if (has_next && sc.reached_own && sc.stop_only) {
+          const int zone = C - 1 - (p.s0c[cls] + 2);
+          if ((int)floorf(xn) >= zone && vn < p.stop_eps) dwn = dwell < 255u ? dwell + 1u : 255u;
+        }
+        if (has_next && sc.reached_own && sc.nt_own == 1u) {
+          const uint32_t g = lb + (uint32_t)lane;
+          p.slot_id[g] = w.id;
+          p.slot_td[g] = ((uint32_t)(tag & 0xFFFFFF) << 8) | dwn;
+        }
+        c_upd++;
+        const bool crossing = xn >= __int2float_rn(C);
+        const bool arrive = crossing && !has_next;
+        const bool request = crossing && has_next;
+        if (arrive) {
+          atomicAdd(p.exitc + w.e, 1u);
+          c_arr++;
+        }
+        uint32_t rq_g = 0, rq_t = 0, rq_e2 = 0;
+        if (request) {
+          rq_e2 = sc.e2 != MANTA_NONE ? sc.e2 : (__ldg(p.route + w.rc + 1u) & MANTA_EDGE_MASK);
+          const uint32_t cnl2 = sc.e2 != MANTA_NONE ? sc.e2cnl : load_em(p, rq_e2).cnl;
+          const int l2 = min(lane, lanes_of(cnl2) - 1);
+          rq_g = lb + (uint32_t)lane;
+          rq_t = target_key(rq_e2, (uint32_t)l2);
+          p.req_tgt[rq_g] = rq_t;
+          p.req_key[rq_g] = ((unsigned long long)tag << 32) | w.id;
+        } else if (!arrive) {
+          w.x = xn; w.v = vn;
+          w.ld = (w.ld & kLdEdgeBits) | (uint32_t)lane | (dwn << 8);
+          w.pcell = gcell;
+          store_veh_state(p, s, w);
+          nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xn)] = speed_code(vn);
+          if (win >= 0) {
+            const size_t o = (size_t)win * p.E + w.e;
+            atomicAdd(p.ssum + o, (unsigned long long)(vn * 1048576.0f));
+            atomicAdd(p.scnt + o, 1u);
+          }
+        }
+        if (arrive) {
+          act[i] = MANTA_NONE;
+          const uint32_t ia = atomicAdd(&ctl->n_arr, 1u);
+          p.arr[ia] = gcell;
+          p.freel[atomicAdd(&ctl->free_count, 1u)] = s;
+          atomicAdd(&ctl->n_holes[cb ^ 1], 1u);
+        }
+        if (request) {
+          // staged in the warp's buffer; written out 32 at a time
+          const unsigned am = __activemask();
+          const int rk = __popc(am & lt_mask), cnt = __popc(am);
+          int nb = s_rqn[wid];
+          if (nb + cnt > 32) {
+            flush_requests(p, rqb, nb, am, rk, cnt);
+            nb = 0;
+          }
+          const int at = nb + rk;
+          rqb[0 * 32 + at] = s; rqb[1 * 32 + at] = __float_as_uint(xn); rqb[2 * 32 + at] = __float_as_uint(vn);
+          rqb[3 * 32 + at] = dwn; rqb[4 * 32 + at] = rq_g; rqb[5 * 32 + at] = rq_t; rqb[6 * 32 + at] = rq_e2;
+          rqb[7 * 32 + at] = node_of(em);
+          __syncwarp(am);
+          if (rk == 0) s_rqn[wid] = nb + cnt;
+          __syncwarp(am);
         }
       }
-      if (stop_in_place) {
-        xn = x; vn = 0.0f;
-      } else {
-        const float dt = p.dt;
-        const float vt = v + acc * dt;
-        float xt, vv;
-        if (vt >= 0.0f) { xt = x + (v * dt + (0.5f * acc) * (dt * dt)); vv = vt; }
-        else { xt = x - (v * v) / (2.0f * acc); vv = 0.0f; }
-        bool has_bound = sc.kind != SC_FREE;
-        int bnd = sc.cL - L;
-        if (has_next && xt >= __int2float_rn(C)) {
-          // at most one node per step: stay within the next edge
-          uint32_t e2 = sc.e2;
-          if (e2 == MANTA_NONE) e2 = __ldg(p.route + w.rc + 1u) & MANTA_EDGE_MASK;
-          const int cap = C + (int)cells_of(load_em(p, e2).cnl) - 1;
-          if (!has_bound || cap < bnd) { has_bound = true; bnd = cap; }
-        }
-        if (has_bound && xt > __int2float_rn(bnd)) { xn = fmaxf(x, __int2float_rn(bnd)); vn = 0.0f; c_clamp++; }
-        else { xn = xt; vn = vv; }
-      }
-      uint32_t dwn = 0;
-      if (has_next && sc.reached_own && sc.stop_only) {
-        const int zone = C - 1 - (p.s0c[cls] + 2);
-        if ((int)floorf(xn) >= zone && vn < p.stop_eps) dwn = dwell < 255u ? dwell + 1u : 255u;
-      }
-      if (has_next && sc.reached_own && __ldg(p.ntype + node_of(em)) == 1) {
-        const uint32_t g = __ldg(p.lane_base + w.e) + (uint32_t)lane;
-        p.slot_id[g] = w.id;
-        p.slot_td[g] = ((uint32_t)(tag & 0xFFFFFF) << 8) | dwn;
-      }
-      c_upd++;
-      const bool crossing = xn >= __int2float_rn(C);
-      const bool arrive = crossing && !has_next;
-      const bool request = crossing && has_next;
-      if (arrive) {
-        atomicAdd(p.exitc + w.e, 1u);
-        c_arr++;
-      }
-      uint32_t rq_g = 0, rq_t = 0, rq_e2 = 0;
-      if (request) {
-        rq_e2 = sc.e2 != MANTA_NONE ? sc.e2 : (__ldg(p.route + w.rc + 1u) & MANTA_EDGE_MASK);
-        const int l2 = min(lane, lanes_of(load_em(p, rq_e2).cnl) - 1);
-        rq_g = __ldg(p.lane_base + w.e) + (uint32_t)lane;
-        rq_t = __ldg(p.lane_base + rq_e2) + (uint32_t)l2;
-        p.req_tgt[rq_g] = rq_t;
-        p.req_key[rq_g] = ((unsigned long long)tag << 32) | w.id;
-      } else if (!arrive) {
-        w.x = xn; w.v = vn;
-        w.ld = (w.ld & kLdEdgeBits) | (uint32_t)lane | (dwn << 8);
-        w.pcell = gcell;
-        store_veh_state(p, s, w);
-        nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xn)] = speed_code(vn);
-        if (win >= 0) {
-          const size_t o = (size_t)win * p.E + w.e;
-          atomicAdd(p.ssum + o, (unsigned long long)(vn * 1048576.0f));
-          atomicAdd(p.scnt + o, 1u);
-        }
-      }
-      if (arrive) {
-        act[i] = MANTA_NONE;
-        const uint32_t ia = atomicAdd(&ctl->n_arr, 1u);
-        p.arr[ia] = gcell;
-        p.freel[atomicAdd(&ctl->free_count, 1u)] = s;
-        atomicAdd(&ctl->n_holes[cb ^ 1], 1u);
-      }
-      if (request) {
-        const uint32_t iq = atomicAdd(&ctl->n_req, 1u);
-        p.req[iq] = s; p.req_x[iq] = xn; p.req_v[iq] = vn; p.req_dw[iq] = dwn;
-        p.req_g[iq] = rq_g; p.req_t[iq] = rq_t; p.req_e2[iq] = rq_e2; p.req_n[iq] = node_of(em);
-      }
+      __syncwarp();
+      const int nb = s_rqn[wid];
+      if (nb > 0) flush_requests(p, rqb, nb, 0xFFFFFFFFu, wl, 32);
     }
     if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
     if (timer) { const uint64_t t = globaltimer(); ph[2] += t - tp; tp = t; }
@@ -844,7 +998,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       const uint32_t gown = __ldcg(p.req_g + i), tgt = __ldcg(p.req_t + i);
       const uint32_t e2 = __ldcg(p.req_e2 + i), n = __ldcg(p.req_n + i);
       const uint32_t o0 = __ldg(p.nin_off + n), o1 = __ldg(p.nin_off + n + 1);
-      const uint32_t lb2 = __ldg(p.lane_base + e2);
       const unsigned long long dk = __ldcg(p.dep_key + e2);
       const EdgeMeta em2 = load_em(p, e2);
       Veh w = load_veh(p, s);
@@ -852,7 +1005,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       const EdgeMeta em = w.em;
       const uint32_t stride = stride_of(cells_of(em.cnl));
       bool win_it = min_competitor(p, o0, o1, gown, tgt, tag) > w.id;
-      if (win_it && tgt == lb2 && (uint32_t)(dk >> 32) == tag && (uint32_t)dk < w.id) win_it = false;
+      if (win_it && tgt == target_key(e2, 0u) && (uint32_t)(dk >> 32) == tag && (uint32_t)dk < w.id) win_it = false;
       const uint32_t cell = (uint32_t)(int)floorf(w.x);
       w.pcell = em.row0 + (uint32_t)lane * stride + cell;
       float xf, vf;
@@ -864,7 +1017,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
         atomicAdd(p.entry + e2, 1u);
         xf = __ldcg(p.req_x + i) - __int2float_rn(C);
         vf = __ldcg(p.req_v + i);
-        const uint32_t l2 = tgt - lb2;
+        const uint32_t l2 = tgt & 15u;
         w.e = e2; w.rc = w.rc + 1u;
         w.ld = ld_for_entry(p, w.rc, l2);
         w.em = em2;
@@ -894,7 +1047,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       bool won = (uint32_t)(dk >> 32) == tag;
       if (won) {
         const uint32_t n = __ldg(p.esrc + e);
-        won = min_competitor(p, __ldg(p.nin_off + n), __ldg(p.nin_off + n + 1), MANTA_NONE, __ldg(p.lane_base + e),
+        won = min_competitor(p, __ldg(p.nin_off + n), __ldg(p.nin_off + n + 1), MANTA_NONE, target_key(e, 0u),
                              tag) > j;
       }
       uint32_t s = MANTA_NONE;
