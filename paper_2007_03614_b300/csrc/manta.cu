@@ -28,6 +28,7 @@ manta_status fail(manta_status s, const std::string &msg) {
 
 constexpr int32_t kStepsPerLaunch = 2048;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per grid barrier wait
+constexpr uint64_t kMapPad = 64;                    // lane-map padding after the last row
 
 __global__ void prime_kernel(Params p, uint32_t hi, int cb) {
   uint32_t *dep = cb ? p.dep1 : p.dep0;
@@ -309,8 +310,9 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   uint32_t *d_nin = dalloc<uint32_t>(S, lanes_total, &ok);
   uint32_t *d_stops = dalloc<uint32_t>(S, stops.size(), &ok);
   float *d_mtab = dalloc<float>(S, mtab.size(), &ok);
-  P.atlas0 = dalloc<uint8_t>(S, bytes, &ok);
-  P.atlas1 = dalloc<uint8_t>(S, bytes, &ok);
+  // 64 padding bytes: a scan batch may be fetched whole past the last row
+  P.atlas0 = dalloc<uint8_t>(S, bytes + kMapPad, &ok);
+  P.atlas1 = dalloc<uint8_t>(S, bytes + kMapPad, &ok);
   P.permit = dalloc<uint32_t>(S, N, &ok);
   P.rr = dalloc<uint32_t>(S, N, &ok);
   P.req_key = dalloc<unsigned long long>(S, lanes_total, &ok);
@@ -331,8 +333,8 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   bool cp = upload(S, d_em, em) && upload(S, d_es, es) && upload(S, d_nt, ntype) && upload(S, d_esrc, esrc_u) &&
             upload(S, d_lb, lane_base_e) && upload(S, d_nin_off, nin_off) && upload(S, d_nin, nin) &&
             upload(S, d_stops, stops) && upload(S, d_mtab, mtab);
-  cp = cp && cudaMemsetAsync(P.atlas0, 0xFF, bytes, S->stream) == cudaSuccess &&
-       cudaMemsetAsync(P.atlas1, 0xFF, bytes, S->stream) == cudaSuccess &&
+  cp = cp && cudaMemsetAsync(P.atlas0, 0xFF, bytes + kMapPad, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.atlas1, 0xFF, bytes + kMapPad, S->stream) == cudaSuccess &&
        cudaMemsetAsync(P.permit, 0xFF, sizeof(uint32_t) * N, S->stream) == cudaSuccess &&
        cudaMemsetAsync(P.rr, 0, sizeof(uint32_t) * N, S->stream) == cudaSuccess &&
        cudaMemsetAsync(P.req_key, 0, sizeof(unsigned long long) * std::max<uint32_t>(lanes_total, 1), S->stream) == cudaSuccess &&
@@ -467,6 +469,7 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   P.veh = dalloc<Veh>(S, NT, &ok);
   P.act0 = dalloc<uint32_t>(S, NT, &ok); P.act1 = dalloc<uint32_t>(S, NT, &ok);
   P.freel = dalloc<uint32_t>(S, NT, &ok); P.chg = dalloc<uint32_t>(S, NT, &ok);
+  P.p3a = dalloc<uint32_t>(S, NT, &ok); P.chg_pos = dalloc<uint32_t>(S, NT, &ok);
   P.req = dalloc<uint32_t>(S, NT, &ok); P.arr = dalloc<uint32_t>(S, NT, &ok);
   P.req_x = dalloc<float>(S, NT, &ok); P.req_v = dalloc<float>(S, NT, &ok); P.req_dw = dalloc<uint32_t>(S, NT, &ok);
   P.req_g = dalloc<uint32_t>(S, NT, &ok); P.req_t = dalloc<uint32_t>(S, NT, &ok);

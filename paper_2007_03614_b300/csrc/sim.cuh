@@ -107,6 +107,8 @@ struct Params {
   Veh *veh;
   // lists
   uint32_t *act0, *act1, *freel, *chg, *req, *arr, *dep0, *dep1;
+  uint32_t *p3a;               // by active-list position: first lane-map batch of the leader scan
+  uint32_t *chg_pos;           // active-list position of each lane changer
   float *req_x, *req_v;
   uint32_t *req_dw, *req_g, *req_t, *req_e2, *req_n;
   // departure queues

@@ -31,6 +31,7 @@
 #define MANTA_BLOCK 384
 #endif
 constexpr int kBlock = MANTA_BLOCK;
+constexpr int kQueueWords = 64 * (int)sizeof(Veh) / 4;   // per-warp lane-change queue (64 records)
 constexpr int kMinBlocksPerSM = MANTA_MIN_BLOCKS_PER_SM;
 
 __device__ __forceinline__ uint64_t globaltimer() {
@@ -476,12 +477,13 @@ struct Fetch {
   uint32_t nent2;
 };
 
-__device__ __forceinline__ Veh unpack_veh(const Batch &b) {
-  Veh w;
-  w.x = __uint_as_float(b.q[0].x); w.v = __uint_as_float(b.q[0].y); w.id = b.q[0].z; w.rc = b.q[0].w;
-  w.rend = b.q[1].x; w.e = b.q[1].y; w.ld = b.q[1].z; w.pcell = b.q[1].w;
-  w.em.row0 = b.q[2].x; w.em.cnl = b.q[2].y; w.em.lim = __uint_as_float(b.q[2].z); w.em.dst = b.q[2].w;
-  return w;
+// Byte offset in a lane-map buffer of the first 64-byte batch a leader scan
+// from `cell` reads on lane `lane` of edge record em (the batch holding cell
+// + 1), or MANTA_NONE when the vehicle is at the last cell of its edge.  The
+// buffers carry 64 padding bytes so the batch may run past the row end.
+__device__ __forceinline__ uint32_t first_batch(const EdgeMeta &em, int lane, int cell) {
+  const uint32_t C = cells_of(em.cnl);
+  return (uint32_t)cell + 1u < C ? em.row0 + (uint32_t)lane * stride_of(C) + (((uint32_t)cell + 1u) & ~15u) : MANTA_NONE;
 }
 
 // Sets up the walk of vehicle w from `cell`.  A closed own lane holds a
@@ -512,6 +514,30 @@ __device__ __forceinline__ bool walk_start(const Params &p, const uint8_t *cur, 
     }
   }
   if (C <= wk.limit && w.rc + 1u < w.rend) wk.nent = __ldg(p.route + w.rc + 1u);
+  return false;
+}
+
+// Consumes the first batch of the own row, fetched with the vehicle record:
+// returns true when the scan is complete; otherwise the next round trip
+// continues along the row or, when the batch reached the end of the scanned
+// range, fetches the node data only.
+__device__ __forceinline__ bool walk_first(const Params &p, const Veh &w, Walk &wk, const Batch &b, int cell, Scan &s,
+                                           uint32_t &c_scan) {
+  const int segC = (int)cells_of(wk.sm.cnl);
+  const int hi = min(wk.limit, segC - 1);
+  const int lo = wk.pos;
+  const int c0 = lo & ~15;
+  uint32_t byte = 0;
+  const int c = check_batch(b, c0, lo, hi, byte);
+  if (c >= 0) {
+    s.kind = SC_LEADER; s.cL = c; s.vL = speed_decode(byte);
+    c_scan += (uint32_t)(c - cell);
+    return true;
+  }
+  if (c0 + 64 <= hi) { wk.pos = c0 + 64; return false; }
+  if (segC > wk.limit) { c_scan += (uint32_t)p.H; return true; }
+  if (wk.r + 1u >= w.rend) { c_scan += (uint32_t)(segC - 1 - cell); return true; }
+  wk.pos = hi + 1;
   return false;
 }
 
@@ -607,10 +633,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
   __shared__ int s_ok;
   __shared__ unsigned long long s_cnt[CNT_N];
   __shared__ float s_sab2[8];                       // 2 sqrt(a b) per road class (Eq. 1)
-  // per-warp scratch, 3 KB: in P1 a queue of 64 lane-change candidates
-  // (vehicle records); in P3 the work pool (32 slots, 32 list indices) and
-  // 32 staged crossing requests (8 fields, field-major)
-  __shared__ __align__(16) uint32_t s_wbuf[kBlock / 32][64 * sizeof(Veh) / 4];
+  // per-warp scratch, 3.25 KB: in P1 a queue of 64 lane-change candidates
+  // (vehicle records, then their list positions); in P3 the work pool (32
+  // slots, list indices, first-batch offsets) and 32 staged crossing requests
+  // (8 fields, field-major)
+  __shared__ __align__(16) uint32_t s_wbuf[kBlock / 32][kQueueWords + 64];
   __shared__ int s_rqn[kBlock / 32];
   Ctl *ctl = p.ctl;
   if (threadIdx.x < CNT_N) s_cnt[threadIdx.x] = 0ull;
@@ -670,19 +697,27 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
     {
       const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
       Veh *q = reinterpret_cast<Veh *>(s_wbuf[wid]);
+      uint32_t *qpos = s_wbuf[wid] + kQueueWords;   // list position of each queued vehicle
       int qn = 0;   // warp-uniform queue length
-      for (uint32_t base = gtid - (uint32_t)lane; base < nact; base += gsz) {
+      uint32_t base = gtid - (uint32_t)lane;
+      uint32_t s_nx = base + lane < nact ? __ldcg(act_in + base + lane) : MANTA_NONE;
+      for (; base < nact; base += gsz) {
         const uint32_t i = base + (uint32_t)lane;
-        const uint32_t s = i < nact ? __ldcg(act_in + i) : MANTA_NONE;
+        const uint32_t s = s_nx;
+        // the next block's slots load while this block runs
+        s_nx = base + gsz + lane < nact ? __ldcg(act_in + base + gsz + lane) : MANTA_NONE;
+        uint32_t pos = i;
         if (compact) {
           const uint32_t at = warp_append(&ctl->n_compact, s != MANTA_NONE);
           if (s != MANTA_NONE) act[at] = s;
+          pos = at;
         }
         Veh w;
         bool cand = false;
         if (s != MANTA_NONE) {
           w = load_veh(p, s);
           if (w.pcell != MANTA_NONE) nxt[w.pcell] = (uint8_t)MANTA_EMPTY;
+          p.p3a[pos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
           // only vehicles that can change lanes this step join the queue: the
           // step's direction must point at a lane, and either the vehicle moves
           // (a discretionary change needs a slower leader) or a mandatory
@@ -694,28 +729,34 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
           if (cand) w.pcell = s;          // the queue entry carries the slot in pcell
         }
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
-        if (cand) q[qn + __popc(bal & ((1u << lane) - 1u))] = w;
+        if (cand) {
+          const int at = qn + __popc(bal & ((1u << lane) - 1u));
+          q[at] = w;
+          qpos[at] = pos;
+        }
         qn += __popc(bal);
         __syncwarp();
         if (qn >= 32) {
           // a full warp of lane-change decisions
           const Veh c = q[lane];
+          const uint32_t cpos = qpos[lane];
           const int tgt = lc_decide(p, cur, k, c, c_lce);
           if (tgt >= 0) p.veh[c.pcell].ld = (c.ld & 0xFF00FFFFu) | ((uint32_t)tgt << 16);
           const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
-          if (tgt >= 0) p.chg[at] = c.pcell;
+          if (tgt >= 0) { p.chg[at] = c.pcell; p.chg_pos[at] = cpos; }
           __syncwarp();
-          if (lane < qn - 32) q[lane] = q[32 + lane];
+          if (lane < qn - 32) { q[lane] = q[32 + lane]; qpos[lane] = qpos[32 + lane]; }
           qn -= 32;
           __syncwarp();
         }
       }
       if (lane < qn) {
         const Veh c = q[lane];
+        const uint32_t cpos = qpos[lane];
         const int tgt = lc_decide(p, cur, k, c, c_lce);
         if (tgt >= 0) p.veh[c.pcell].ld = (c.ld & 0xFF00FFFFu) | ((uint32_t)tgt << 16);
         const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
-        if (tgt >= 0) p.chg[at] = c.pcell;
+        if (tgt >= 0) { p.chg[at] = c.pcell; p.chg_pos[at] = cpos; }
       }
       __syncwarp();
     }
@@ -742,6 +783,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
     if (nchg) {
       for (uint32_t i = gtid; i < nchg; i += gsz) {
         const uint32_t s = __ldcg(p.chg + i);
+        const uint32_t pos = __ldcg(p.chg_pos + i);
         const Veh w = load_veh(p, s);
         const EdgeMeta &em = w.em;
         const uint32_t stride = stride_of(cells_of(em.cnl));
@@ -751,6 +793,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
         cur[b] = cur[a];
         cur[a] = (uint8_t)MANTA_EMPTY;
         p.veh[s].ld = (w.ld & (kLdEdgeBits | 0x0000FF00u)) | ln;
+        p.p3a[pos] = first_batch(em, (int)ln, (int)cell);
         c_lc++;
       }
       if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
@@ -792,20 +835,21 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
       const unsigned lt_mask = (1u << wl) - 1u;
       const uint32_t nwarps = gridDim.x * (kBlock / 32);
-      uint32_t *ps = s_wbuf[wid], *pi = s_wbuf[wid] + 32;
+      uint32_t *ps = s_wbuf[wid], *pi = s_wbuf[wid] + 32, *pa = s_wbuf[wid] + 64;
       uint32_t ch = 0, csz = 32u;
       if (wl == 0) ch = atomicAdd(&ctl->next3, 32u);
       ch = __shfl_sync(0xFFFFFFFFu, ch, 0);
       uint32_t cslot = ch + wl < nact ? __ldcg(act + ch + wl) : MANTA_NONE;
+      uint32_t caddr = ch + wl < nact ? __ldcg(p.p3a + ch + wl) : MANTA_NONE;
       // the chunk after it: its counter value is taken one chunk ahead, so
       // installing a chunk never waits for the atomic (lane 0 holds it)
       uint32_t chn = 0, cszn = 32u;
       if (wl == 0) chn = atomicAdd(&ctl->next3, 32u);
-      uint32_t *rqb = s_wbuf[wid] + 64;
+      uint32_t *rqb = s_wbuf[wid] + 96;
       if (wl == 0) s_rqn[wid] = 0;
       int pn = 0, pu = 0;         // pool size and entries taken (warp-uniform)
       int st = 0;                 // 0 idle, 1 record requested, 2 walking
-      uint32_t s = 0, i = 0, lb = 0;
+      uint32_t s = 0, i = 0, lb = 0, a3 = MANTA_NONE;
       int cell = 0;
       Veh w;
       Walk wk;
@@ -824,12 +868,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
               const int q = __popc(vb & lt_mask);
               ps[q] = cslot;
               pi[q] = ch + (uint32_t)wl;
+              pa[q] = caddr;
             }
             pn = __popc(vb);
             pu = 0;
             ch = __shfl_sync(0xFFFFFFFFu, chn, 0);
             csz = __shfl_sync(0xFFFFFFFFu, cszn, 0);
-            cslot = (uint32_t)wl < csz && ch + wl < nact ? __ldcg(act + ch + wl) : MANTA_NONE;
+            const bool inb = (uint32_t)wl < csz && ch + wl < nact;
+            cslot = inb ? __ldcg(act + ch + wl) : MANTA_NONE;
+            caddr = inb ? __ldcg(p.p3a + ch + wl) : MANTA_NONE;
             if (wl == 0) {
               const uint32_t rem = ch < nact ? nact - ch : 0u;
               cszn = min(32u, max(4u, rem / (2u * nwarps)));
@@ -843,6 +890,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
           if (st == 0 && rank < take) {
             s = ps[pu + rank];
             i = pi[pu + rank];
+            a3 = pa[pu + rank];
             st = 1;
           }
           pu += take;
@@ -851,18 +899,22 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
         if (__ballot_sync(0xFFFFFFFFu, st != 0) == 0u) break;
         Fetch f;
         if (st == 1) {
-          const uint4 *va = reinterpret_cast<const uint4 *>(p.veh + s);
-          f.b.q[0] = __ldcg(va); f.b.q[1] = __ldcg(va + 1); f.b.q[2] = __ldcg(va + 2);
+          // the record and, in the same round trip, the first batch of its row
+          w = load_veh(p, s);
+          if (a3 != MANTA_NONE) {
+            const uint4 *ra = reinterpret_cast<const uint4 *>(cur + a3);
+            f.b.q[0] = __ldcg(ra); f.b.q[1] = __ldcg(ra + 1); f.b.q[2] = __ldcg(ra + 2); f.b.q[3] = __ldcg(ra + 3);
+          }
         } else if (st == 2) {
           walk_issue(p, cur, w, wk, f);
         }
         bool fin = false;
         if (st == 1) {
-          w = unpack_veh(f.b);
           lb = __ldg(p.lane_base + w.e);      // needed when the vehicle is done
           cell = (int)floorf(w.x);
           fin = walk_start(p, cur, k, w, cell, wk, sc, c_scan);
           st = 2;
+          if (!fin && a3 != MANTA_NONE) fin = walk_first(p, w, wk, f.b, cell, sc, c_scan);
         } else if (st == 2) {
           fin = walk_process(p, k, w, cell, wk, f, sc, c_scan, c_rr);
         }
