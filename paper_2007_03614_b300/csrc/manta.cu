@@ -379,7 +379,10 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, manta_step_kernel, kBlock, 0) != cudaSuccess || per_sm < 1) {
+  if (cudaFuncSetAttribute(manta_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, manta_step_kernel, kBlock, kDynSmem) != cudaSuccess ||
+      per_sm < 1) {
     manta_destroy(S);
     return fail(MANTA_E_CUDA, "occupancy query failed");
   }
@@ -535,8 +538,8 @@ manta_status manta_step(manta_sim *S, int64_t n_steps) {
     // the grid barrier's arrival counter starts from zero in every launch
     cudaError_t e = cudaMemsetAsync(&S->P.ctl->bar_count, 0, sizeof(unsigned), S->stream);
     if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("barrier reset: ") + cudaGetErrorString(e));
-    e = cudaLaunchCooperativeKernel((const void *)manta_step_kernel, dim3(S->grid), dim3(kBlock), args, 0,
-                                                S->stream);
+    e = cudaLaunchCooperativeKernel((const void *)manta_step_kernel, dim3(S->grid), dim3(kBlock), args, kDynSmem,
+                                    S->stream);
     if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
     S->k += chunk;
     n_steps -= chunk;

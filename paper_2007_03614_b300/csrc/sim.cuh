@@ -70,7 +70,7 @@ struct Ctl {
   uint32_t act_sel[2];    // which buffer holds the active list at even / odd steps
   uint32_t n_holes[2];    // holes (arrived vehicles) in that list
   uint32_t n_compact;     // entries written by a compaction pass
-  uint32_t next3;          // next batch of the active list for phase P3
+  uint32_t next3;          // next chunk of the active list for phase P3
   uint32_t n_dep[2];
   uint32_t n_req, n_arr, n_chg, n_depwin;
   uint32_t free_count, n_slots;

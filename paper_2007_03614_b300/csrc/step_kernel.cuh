@@ -32,6 +32,12 @@
 #endif
 constexpr int kBlock = MANTA_BLOCK;
 constexpr int kQueueWords = 64 * (int)sizeof(Veh) / 4;   // per-warp lane-change queue (64 records)
+// fields of a finish-queue entry
+enum { kFqX, kFqV, kFqId, kFqRc, kFqRend, kFqE, kFqLd, kFqRow0, kFqCnl, kFqLim, kFqDst, kFqS, kFqI, kFqCell, kFqLb,
+       kFqKind, kFqCL, kFqVL, kFqE2, kFqE2cnl, kFqFields };
+constexpr int kP3Words = 352 + kFqFields * 64;
+constexpr int kWarpWords = (kQueueWords + 64) > kP3Words ? (kQueueWords + 64) : kP3Words;
+constexpr size_t kDynSmem = (size_t)(kBlock / 32) * kWarpWords * 4;
 constexpr int kMinBlocksPerSM = MANTA_MIN_BLOCKS_PER_SM;
 
 __device__ __forceinline__ uint64_t globaltimer() {
@@ -633,11 +639,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
   __shared__ int s_ok;
   __shared__ unsigned long long s_cnt[CNT_N];
   __shared__ float s_sab2[8];                       // 2 sqrt(a b) per road class (Eq. 1)
-  // per-warp scratch, 3.25 KB: in P1 a queue of 64 lane-change candidates
-  // (vehicle records, then their list positions); in P3 the work pool (32
-  // slots, list indices, first-batch offsets) and 32 staged crossing requests
-  // (8 fields, field-major)
-  __shared__ __align__(16) uint32_t s_wbuf[kBlock / 32][kQueueWords + 64];
+  // per-warp scratch (dynamic shared memory, kWarpWords words per warp): in
+  // P1 a queue of 64 lane-change candidates (vehicle records, then their
+  // list positions); in P3 the work pool (32 slots, list indices, first-batch
+  // offsets), 32 staged crossing requests (8 fields, field-major) and the
+  // finish queue (kFqFields fields x 64 entries)
+  extern __shared__ __align__(16) uint32_t s_wbuf[];
   __shared__ int s_rqn[kBlock / 32];
   Ctl *ctl = p.ctl;
   if (threadIdx.x < CNT_N) s_cnt[threadIdx.x] = 0ull;
@@ -696,8 +703,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
     }
     {
       const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-      Veh *q = reinterpret_cast<Veh *>(s_wbuf[wid]);
-      uint32_t *qpos = s_wbuf[wid] + kQueueWords;   // list position of each queued vehicle
+      Veh *q = reinterpret_cast<Veh *>(s_wbuf + wid * kWarpWords);
+      uint32_t *qpos = s_wbuf + wid * kWarpWords + kQueueWords;   // list position of each queued vehicle
       int qn = 0;   // warp-uniform queue length
       uint32_t base = gtid - (uint32_t)lane;
       uint32_t s_nx = base + lane < nact ? __ldcg(act_in + base + lane) : MANTA_NONE;
@@ -835,91 +842,39 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
       const unsigned lt_mask = (1u << wl) - 1u;
       const uint32_t nwarps = gridDim.x * (kBlock / 32);
-      uint32_t *ps = s_wbuf[wid], *pi = s_wbuf[wid] + 32, *pa = s_wbuf[wid] + 64;
-      uint32_t ch = 0, csz = 32u;
-      if (wl == 0) ch = atomicAdd(&ctl->next3, 32u);
-      ch = __shfl_sync(0xFFFFFFFFu, ch, 0);
+      uint32_t *const wb = s_wbuf + wid * kWarpWords;
+      uint32_t *ps = wb, *pi = wb + 32, *pa = wb + 64;
+      uint32_t *fq = wb + 352;   // finish queue: kFqFields fields x 64 entries
+      const uint32_t dyn0 = 32u * nwarps;   // every warp's first chunk is fixed
+      uint32_t ch = gtid - (uint32_t)wl, csz = 32u;
       uint32_t cslot = ch + wl < nact ? __ldcg(act + ch + wl) : MANTA_NONE;
       uint32_t caddr = ch + wl < nact ? __ldcg(p.p3a + ch + wl) : MANTA_NONE;
       // the chunk after it: its counter value is taken one chunk ahead, so
       // installing a chunk never waits for the atomic (lane 0 holds it)
       uint32_t chn = 0, cszn = 32u;
-      if (wl == 0) chn = atomicAdd(&ctl->next3, 32u);
-      uint32_t *rqb = s_wbuf[wid] + 96;
+      if (wl == 0) chn = dyn0 + atomicAdd(&ctl->next3, 32u);
+      uint32_t *rqb = wb + 96;
       if (wl == 0) s_rqn[wid] = 0;
       int pn = 0, pu = 0;         // pool size and entries taken (warp-uniform)
       int st = 0;                 // 0 idle, 1 record requested, 2 walking
       uint32_t s = 0, i = 0, lb = 0, a3 = MANTA_NONE;
       int cell = 0;
-      Veh w;
-      Walk wk;
-      Scan sc;
-      for (;;) {
-        __syncwarp();
-        unsigned need = __ballot_sync(0xFFFFFFFFu, st == 0);
-        while (need != 0u) {
-          if (pu == pn) {
-            if (ch >= nact) break;
-            // install the prefetched chunk, then prefetch the next one
-            const bool valid = (uint32_t)wl < csz && cslot != MANTA_NONE;
-            const unsigned vb = __ballot_sync(0xFFFFFFFFu, valid);
-            __syncwarp();
-            if (valid) {
-              const int q = __popc(vb & lt_mask);
-              ps[q] = cslot;
-              pi[q] = ch + (uint32_t)wl;
-              pa[q] = caddr;
-            }
-            pn = __popc(vb);
-            pu = 0;
-            ch = __shfl_sync(0xFFFFFFFFu, chn, 0);
-            csz = __shfl_sync(0xFFFFFFFFu, cszn, 0);
-            const bool inb = (uint32_t)wl < csz && ch + wl < nact;
-            cslot = inb ? __ldcg(act + ch + wl) : MANTA_NONE;
-            caddr = inb ? __ldcg(p.p3a + ch + wl) : MANTA_NONE;
-            if (wl == 0) {
-              const uint32_t rem = ch < nact ? nact - ch : 0u;
-              cszn = min(32u, max(4u, rem / (2u * nwarps)));
-              chn = atomicAdd(&ctl->next3, cszn);
-            }
-            __syncwarp();
-            continue;
-          }
-          const int take = min(__popc(need), pn - pu);
-          const int rank = __popc(need & lt_mask);
-          if (st == 0 && rank < take) {
-            s = ps[pu + rank];
-            i = pi[pu + rank];
-            a3 = pa[pu + rank];
-            st = 1;
-          }
-          pu += take;
-          need = __ballot_sync(0xFFFFFFFFu, st == 0);
-        }
-        if (__ballot_sync(0xFFFFFFFFu, st != 0) == 0u) break;
-        Fetch f;
-        if (st == 1) {
-          // the record and, in the same round trip, the first batch of its row
-          w = load_veh(p, s);
-          if (a3 != MANTA_NONE) {
-            const uint4 *ra = reinterpret_cast<const uint4 *>(cur + a3);
-            f.b.q[0] = __ldcg(ra); f.b.q[1] = __ldcg(ra + 1); f.b.q[2] = __ldcg(ra + 2); f.b.q[3] = __ldcg(ra + 3);
-          }
-        } else if (st == 2) {
-          walk_issue(p, cur, w, wk, f);
-        }
-        bool fin = false;
-        if (st == 1) {
-          lb = __ldg(p.lane_base + w.e);      // needed when the vehicle is done
-          cell = (int)floorf(w.x);
-          fin = walk_start(p, cur, k, w, cell, wk, sc, c_scan);
-          st = 2;
-          if (!fin && a3 != MANTA_NONE) fin = walk_first(p, w, wk, f.b, cell, sc, c_scan);
-        } else if (st == 2) {
-          fin = walk_process(p, k, w, cell, wk, f, sc, c_scan, c_rr);
-        }
-        if (!fin) continue;
-        st = 0;
+      // The update of the vehicle in finish-queue entry j (Eq. 1, ballistic
+      // step, clamp, map write, requests, arrivals).
+      auto finish = [&](int j) {
+        Veh w;
+        w.x = __uint_as_float(fq[kFqX * 64 + j]); w.v = __uint_as_float(fq[kFqV * 64 + j]);
+        w.id = fq[kFqId * 64 + j]; w.rc = fq[kFqRc * 64 + j]; w.rend = fq[kFqRend * 64 + j];
+        w.e = fq[kFqE * 64 + j]; w.ld = fq[kFqLd * 64 + j]; w.pcell = MANTA_NONE;
+        w.em.row0 = fq[kFqRow0 * 64 + j]; w.em.cnl = fq[kFqCnl * 64 + j];
+        w.em.lim = __uint_as_float(fq[kFqLim * 64 + j]); w.em.dst = fq[kFqDst * 64 + j];
+        const uint32_t s = fq[kFqS * 64 + j], i = fq[kFqI * 64 + j], lb = fq[kFqLb * 64 + j];
+        const int cell = (int)fq[kFqCell * 64 + j];
+        Scan sc;
+        const uint32_t kd = fq[kFqKind * 64 + j];
+        sc.kind = (int)(kd & 3u); sc.reached_own = (kd >> 2) & 1u; sc.stop_only = (kd >> 3) & 1u; sc.nt_own = kd >> 4;
+        sc.cL = (int)fq[kFqCL * 64 + j]; sc.vL = __uint_as_float(fq[kFqVL * 64 + j]);
+        sc.e2 = fq[kFqE2 * 64 + j]; sc.e2cnl = fq[kFqE2cnl * 64 + j];
         const float x = w.x, v = w.v;
         const int lane = ld_lane(w.ld);
         const uint32_t dwell = ld_dwell(w.ld);
@@ -1035,7 +990,102 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
           if (rk == 0) s_rqn[wid] = nb + cnt;
           __syncwarp(am);
         }
+      };
+      int fqn = 0;                // finish-queue length (warp-uniform)
+      Veh w;
+      Walk wk;
+      Scan sc;
+      for (;;) {
+        __syncwarp();
+        unsigned need = __ballot_sync(0xFFFFFFFFu, st == 0);
+        while (need != 0u) {
+          if (pu == pn) {
+            if (ch >= nact) break;
+            // install the prefetched chunk, then prefetch the next one
+            const bool valid = (uint32_t)wl < csz && cslot != MANTA_NONE;
+            const unsigned vb = __ballot_sync(0xFFFFFFFFu, valid);
+            __syncwarp();
+            if (valid) {
+              const int q = __popc(vb & lt_mask);
+              ps[q] = cslot;
+              pi[q] = ch + (uint32_t)wl;
+              pa[q] = caddr;
+            }
+            pn = __popc(vb);
+            pu = 0;
+            ch = __shfl_sync(0xFFFFFFFFu, chn, 0);
+            csz = __shfl_sync(0xFFFFFFFFu, cszn, 0);
+            const bool inb = (uint32_t)wl < csz && ch + wl < nact;
+            cslot = inb ? __ldcg(act + ch + wl) : MANTA_NONE;
+            caddr = inb ? __ldcg(p.p3a + ch + wl) : MANTA_NONE;
+            if (wl == 0) {
+              const uint32_t rem = ch < nact ? nact - ch : 0u;
+              cszn = min(32u, max(4u, rem / (2u * nwarps)));
+              chn = dyn0 + atomicAdd(&ctl->next3, cszn);
+            }
+            __syncwarp();
+            continue;
+          }
+          const int take = min(__popc(need), pn - pu);
+          const int rank = __popc(need & lt_mask);
+          if (st == 0 && rank < take) {
+            s = ps[pu + rank];
+            i = pi[pu + rank];
+            a3 = pa[pu + rank];
+            st = 1;
+          }
+          pu += take;
+          need = __ballot_sync(0xFFFFFFFFu, st == 0);
+        }
+        if (__ballot_sync(0xFFFFFFFFu, st != 0) == 0u) break;
+        Fetch f;
+        if (st == 1) {
+          // the record and, in the same round trip, the first batch of its row
+          w = load_veh(p, s);
+          if (a3 != MANTA_NONE) {
+            const uint4 *ra = reinterpret_cast<const uint4 *>(cur + a3);
+            f.b.q[0] = __ldcg(ra); f.b.q[1] = __ldcg(ra + 1); f.b.q[2] = __ldcg(ra + 2); f.b.q[3] = __ldcg(ra + 3);
+          }
+        } else if (st == 2) {
+          walk_issue(p, cur, w, wk, f);
+        }
+        bool fin = false;
+        if (st == 1) {
+          lb = __ldg(p.lane_base + w.e);      // needed when the vehicle is done
+          cell = (int)floorf(w.x);
+          fin = walk_start(p, cur, k, w, cell, wk, sc, c_scan);
+          st = 2;
+          if (!fin && a3 != MANTA_NONE) fin = walk_first(p, w, wk, f.b, cell, sc, c_scan);
+        } else if (st == 2) {
+          fin = walk_process(p, k, w, cell, wk, f, sc, c_scan, c_rr);
+        }
+        // completed vehicles join the warp's finish queue; the update itself
+        // runs 32 at a time with the whole warp
+        const unsigned fb = __ballot_sync(0xFFFFFFFFu, fin);
+        if (fin) {
+          st = 0;
+          const int at = fqn + __popc(fb & lt_mask);
+          fq[kFqX * 64 + at] = __float_as_uint(w.x); fq[kFqV * 64 + at] = __float_as_uint(w.v);
+          fq[kFqId * 64 + at] = w.id; fq[kFqRc * 64 + at] = w.rc; fq[kFqRend * 64 + at] = w.rend;
+          fq[kFqE * 64 + at] = w.e; fq[kFqLd * 64 + at] = w.ld; fq[kFqRow0 * 64 + at] = w.em.row0;
+          fq[kFqCnl * 64 + at] = w.em.cnl; fq[kFqLim * 64 + at] = __float_as_uint(w.em.lim);
+          fq[kFqDst * 64 + at] = w.em.dst; fq[kFqS * 64 + at] = s; fq[kFqI * 64 + at] = i;
+          fq[kFqCell * 64 + at] = (uint32_t)cell; fq[kFqLb * 64 + at] = lb;
+          fq[kFqKind * 64 + at] = (uint32_t)sc.kind | ((uint32_t)sc.reached_own << 2) | ((uint32_t)sc.stop_only << 3) |
+                                  (sc.nt_own << 4);
+          fq[kFqCL * 64 + at] = (uint32_t)sc.cL; fq[kFqVL * 64 + at] = __float_as_uint(sc.vL);
+          fq[kFqE2 * 64 + at] = sc.e2; fq[kFqE2cnl * 64 + at] = sc.e2cnl;
+        }
+        fqn += __popc(fb);
+        if (fqn >= 32) {
+          __syncwarp();
+          finish(fqn - 32 + wl);
+          fqn -= 32;
+          __syncwarp();
+        }
       }
+      __syncwarp();
+      if (wl < fqn) finish(wl);
       __syncwarp();
       const int nb = s_rqn[wid];
       if (nb > 0) flush_requests(p, rqb, nb, 0xFFFFFFFFu, wl, 32);
