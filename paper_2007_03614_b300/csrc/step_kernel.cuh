@@ -1093,94 +1093,102 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
     if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
     if (timer) { const uint64_t t = globaltimer(); ph[2] += t - tp; tp = t; }
     // ================================================================ P4
-    // crossing requests: the lowest id among requests for the same target lane wins
+    // Crossing requests, departures, arrivals' cells and the trips due at
+    // k + 1 are independent of one another: they share one index space so
+    // that their dependent loads overlap instead of running one after another.
+    //  - crossing requests: the lowest id among requests for the same target
+    //    lane wins
+    //  - departures: the queue head wins unless a crossing with a lower id
+    //    targets lane 0
+    //  - arrivals leave the current map
+    //  - trips due at step k + 1 join their edge's departure queue
     const uint32_t nreq = ldv(&ctl->n_req);
-    for (uint32_t i = gtid; i < nreq; i += gsz) {
-      const uint32_t s = __ldcg(p.req + i);
-      const uint32_t gown = __ldcg(p.req_g + i), tgt = __ldcg(p.req_t + i);
-      const uint32_t e2 = __ldcg(p.req_e2 + i), n = __ldcg(p.req_n + i);
-      const uint32_t o0 = __ldg(p.nin_off + n), o1 = __ldg(p.nin_off + n + 1);
-      const unsigned long long dk = __ldcg(p.dep_key + e2);
-      const EdgeMeta em2 = load_em(p, e2);
-      Veh w = load_veh(p, s);
-      const int lane = ld_lane(w.ld);
-      const EdgeMeta em = w.em;
-      const uint32_t stride = stride_of(cells_of(em.cnl));
-      bool win_it = min_competitor(p, o0, o1, gown, tgt, tag) > w.id;
-      if (win_it && tgt == target_key(e2, 0u) && (uint32_t)(dk >> 32) == tag && (uint32_t)dk < w.id) win_it = false;
-      const uint32_t cell = (uint32_t)(int)floorf(w.x);
-      w.pcell = em.row0 + (uint32_t)lane * stride + cell;
-      float xf, vf;
-      uint32_t ef;
-      if (win_it) {
-        const int C = (int)cells_of(em.cnl);
-        if (__ldg(p.ntype + n) == 1 && ldv(p.permit + n) == w.id) p.permit[n] = MANTA_NONE;
-        atomicAdd(p.exitc + w.e, 1u);
-        atomicAdd(p.entry + e2, 1u);
-        xf = __ldcg(p.req_x + i) - __int2float_rn(C);
-        vf = __ldcg(p.req_v + i);
-        const uint32_t l2 = tgt & 15u;
-        w.e = e2; w.rc = w.rc + 1u;
-        w.ld = ld_for_entry(p, w.rc, l2);
-        w.em = em2;
-        nxt[em2.row0 + l2 * stride_of(cells_of(em2.cnl)) + (uint32_t)(int)floorf(xf)] = speed_code(vf);
-        ef = e2;
-      } else {
-        const int C = (int)cells_of(em.cnl);
-        xf = fmaxf(w.x, __int2float_rn(C - 1));
-        vf = 0.0f;
-        w.ld = (w.ld & kLdEdgeBits) | (uint32_t)lane | (__ldcg(p.req_dw + i) << 8);
-        nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xf)] = speed_code(vf);
-        ef = w.e;
-      }
-      w.x = xf; w.v = vf;
-      store_veh(p, s, w);
-      if (win >= 0) {
-        const size_t o = (size_t)win * p.E + ef;
-        atomicAdd(p.ssum + o, (unsigned long long)(vf * 1048576.0f));
-        atomicAdd(p.scnt + o, 1u);
-      }
-    }
-    // departures: the queue head wins unless a crossing with a lower id targets lane 0
-    for (uint32_t i = gtid; i < ndep; i += gsz) {
-      const uint32_t e = __ldcg(dep + i);
-      const unsigned long long dk = __ldcg(p.dep_key + e);
-      const uint32_t j = (uint32_t)dk;
-      bool won = (uint32_t)(dk >> 32) == tag;
-      if (won) {
-        const uint32_t n = __ldg(p.esrc + e);
-        won = min_competitor(p, __ldg(p.nin_off + n), __ldg(p.nin_off + n + 1), MANTA_NONE, target_key(e, 0u),
-                             tag) > j;
-      }
-      uint32_t s = MANTA_NONE;
-      bool keep = true;
-      if (won) {
-        const uint32_t wi = atomicAdd(&ctl->n_depwin, 1u);
-        const uint32_t fc = ldv(&ctl->free_count);
-        s = wi < fc ? __ldcg(p.freel + (fc - 1u - wi)) : ldv(&ctl->n_slots) + (wi - fc);
-        const EdgeMeta em = load_em(p, e);
-        Veh w;
-        w.x = 0.0f; w.v = 0.0f; w.id = j; w.rc = __ldg(p.route_off + j); w.rend = __ldg(p.route_off + j + 1u);
-        w.e = e; w.ld = ld_for_entry(p, w.rc, 0u); w.pcell = MANTA_NONE; w.em = em;
-        store_veh(p, s, w);
-        nxt[em.row0] = speed_code(0.0f);
-        atomicAdd(p.entry + e, 1u);
-        c_dep++;
-        p.q_pos[e] = __ldcg(p.q_pos + e) + 1u;
-        keep = atomicSub(p.pending + e, 1u) > 1u;
-      }
-      const uint32_t ia = warp_append(&ctl->n_act[cb ^ 1], won);
-      if (won) act[ia] = s;
-      const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], keep);
-      if (keep) dep_n[id2] = e;
-    }
-    // arrivals leave the current map
     const uint32_t narr = ldv(&ctl->n_arr);
-    for (uint32_t i = gtid; i < narr; i += gsz) cur[__ldcg(p.arr + i)] = (uint8_t)MANTA_EMPTY;
-    // trips due at step k + 1 join their edge's departure queue
-    {
-      const uint32_t lo = ldv(&ctl->due_pos), hi = ldv(&ctl->due_hi);
-      for (uint32_t i = lo + gtid; i < hi; i += gsz) {
+    const uint32_t due_lo = ldv(&ctl->due_pos), due_hi = ldv(&ctl->due_hi);
+    const uint32_t t_dep = nreq, t_arr = t_dep + ndep, t_due = t_arr + narr, t_end = t_due + (due_hi - due_lo);
+    for (uint32_t t = gtid; t < t_end; t += gsz) {
+      if (t < t_dep) {
+        const uint32_t i = t;
+        const uint32_t s = __ldcg(p.req + i);
+        const uint32_t gown = __ldcg(p.req_g + i), tgt = __ldcg(p.req_t + i);
+        const uint32_t e2 = __ldcg(p.req_e2 + i), n = __ldcg(p.req_n + i);
+        const uint32_t o0 = __ldg(p.nin_off + n), o1 = __ldg(p.nin_off + n + 1);
+        const unsigned long long dk = __ldcg(p.dep_key + e2);
+        const EdgeMeta em2 = load_em(p, e2);
+        Veh w = load_veh(p, s);
+        const int lane = ld_lane(w.ld);
+        const EdgeMeta em = w.em;
+        const uint32_t stride = stride_of(cells_of(em.cnl));
+        bool win_it = min_competitor(p, o0, o1, gown, tgt, tag) > w.id;
+        if (win_it && tgt == target_key(e2, 0u) && (uint32_t)(dk >> 32) == tag && (uint32_t)dk < w.id) win_it = false;
+        const uint32_t cell = (uint32_t)(int)floorf(w.x);
+        w.pcell = em.row0 + (uint32_t)lane * stride + cell;
+        float xf, vf;
+        uint32_t ef;
+        if (win_it) {
+          const int C = (int)cells_of(em.cnl);
+          if (__ldg(p.ntype + n) == 1 && ldv(p.permit + n) == w.id) p.permit[n] = MANTA_NONE;
+          atomicAdd(p.exitc + w.e, 1u);
+          atomicAdd(p.entry + e2, 1u);
+          xf = __ldcg(p.req_x + i) - __int2float_rn(C);
+          vf = __ldcg(p.req_v + i);
+          const uint32_t l2 = tgt & 15u;
+          w.e = e2; w.rc = w.rc + 1u;
+          w.ld = ld_for_entry(p, w.rc, l2);
+          w.em = em2;
+          nxt[em2.row0 + l2 * stride_of(cells_of(em2.cnl)) + (uint32_t)(int)floorf(xf)] = speed_code(vf);
+          ef = e2;
+        } else {
+          const int C = (int)cells_of(em.cnl);
+          xf = fmaxf(w.x, __int2float_rn(C - 1));
+          vf = 0.0f;
+          w.ld = (w.ld & kLdEdgeBits) | (uint32_t)lane | (__ldcg(p.req_dw + i) << 8);
+          nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xf)] = speed_code(vf);
+          ef = w.e;
+        }
+        w.x = xf; w.v = vf;
+        store_veh(p, s, w);
+        if (win >= 0) {
+          const size_t o = (size_t)win * p.E + ef;
+          atomicAdd(p.ssum + o, (unsigned long long)(vf * 1048576.0f));
+          atomicAdd(p.scnt + o, 1u);
+        }
+      } else if (t < t_arr) {
+        const uint32_t i = t - t_dep;
+        const uint32_t e = __ldcg(dep + i);
+        const unsigned long long dk = __ldcg(p.dep_key + e);
+        const uint32_t j = (uint32_t)dk;
+        bool won = (uint32_t)(dk >> 32) == tag;
+        if (won) {
+          const uint32_t n = __ldg(p.esrc + e);
+          won = min_competitor(p, __ldg(p.nin_off + n), __ldg(p.nin_off + n + 1), MANTA_NONE, target_key(e, 0u),
+                               tag) > j;
+        }
+        uint32_t s = MANTA_NONE;
+        bool keep = true;
+        if (won) {
+          const uint32_t wi = atomicAdd(&ctl->n_depwin, 1u);
+          const uint32_t fc = ldv(&ctl->free_count);
+          s = wi < fc ? __ldcg(p.freel + (fc - 1u - wi)) : ldv(&ctl->n_slots) + (wi - fc);
+          const EdgeMeta em = load_em(p, e);
+          Veh w;
+          w.x = 0.0f; w.v = 0.0f; w.id = j; w.rc = __ldg(p.route_off + j); w.rend = __ldg(p.route_off + j + 1u);
+          w.e = e; w.ld = ld_for_entry(p, w.rc, 0u); w.pcell = MANTA_NONE; w.em = em;
+          store_veh(p, s, w);
+          nxt[em.row0] = speed_code(0.0f);
+          atomicAdd(p.entry + e, 1u);
+          c_dep++;
+          p.q_pos[e] = __ldcg(p.q_pos + e) + 1u;
+          keep = atomicSub(p.pending + e, 1u) > 1u;
+        }
+        const uint32_t ia = warp_append(&ctl->n_act[cb ^ 1], won);
+        if (won) act[ia] = s;
+        const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], keep);
+        if (keep) dep_n[id2] = e;
+      } else if (t < t_due) {
+        cur[__ldcg(p.arr + (t - t_arr))] = (uint8_t)MANTA_EMPTY;
+      } else {
+        const uint32_t i = due_lo + (t - t_due);
         const uint32_t e = __ldg(p.due_edge + i);
         const bool first = atomicAdd(p.pending + e, 1u) == 0u;
         const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], first);
