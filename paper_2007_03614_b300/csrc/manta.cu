@@ -473,6 +473,10 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   P.act0 = dalloc<uint32_t>(S, NT, &ok); P.act1 = dalloc<uint32_t>(S, NT, &ok);
   P.freel = dalloc<uint32_t>(S, NT, &ok); P.chg = dalloc<uint32_t>(S, NT, &ok);
   P.p3a = dalloc<uint32_t>(S, NT, &ok); P.chg_pos = dalloc<uint32_t>(S, NT, &ok);
+  // candidate regions: every warp may list one candidate per entry it visits,
+  // 32 entries per grid-stride block
+  const size_t NC = NT + (size_t)S->grid * kBlock;
+  P.lcq = dalloc<Veh>(S, NC, &ok); P.lcq_pos = dalloc<uint32_t>(S, NC, &ok);
   P.req = dalloc<uint32_t>(S, NT, &ok); P.arr = dalloc<uint32_t>(S, NT, &ok);
   P.req_x = dalloc<float>(S, NT, &ok); P.req_v = dalloc<float>(S, NT, &ok); P.req_dw = dalloc<uint32_t>(S, NT, &ok);
   P.req_g = dalloc<uint32_t>(S, NT, &ok); P.req_t = dalloc<uint32_t>(S, NT, &ok);

@@ -71,11 +71,12 @@ struct Ctl {
   uint32_t n_holes[2];    // holes (arrived vehicles) in that list
   uint32_t n_compact;     // entries written by a compaction pass
   uint32_t next3;          // next chunk of the active list for phase P3
+  uint32_t pad[2];
   uint32_t n_dep[2];
   uint32_t n_req, n_arr, n_chg, n_depwin;
   uint32_t free_count, n_slots;
   uint32_t due_pos, due_hi;   // trips [due_pos, due_hi) of the due list join queues this step
-  uint32_t pad[2];
+
   unsigned long long cnt[CNT_N];
   unsigned long long phase_ns[4];   // device time of phases P1..P4 as seen by block 0
 };
@@ -109,6 +110,9 @@ struct Params {
   uint32_t *act0, *act1, *freel, *chg, *req, *arr, *dep0, *dep1;
   uint32_t *p3a;               // by active-list position: first lane-map batch of the leader scan
   uint32_t *chg_pos;           // active-list position of each lane changer
+  Veh *lcq;                    // lane-change candidates of the step by warp region (record copies,
+                               // slot in pcell)
+  uint32_t *lcq_pos;           // their active-list positions
   float *req_x, *req_v;
   uint32_t *req_dw, *req_g, *req_t, *req_e2, *req_n;
   // departure queues

@@ -31,12 +31,11 @@
 #define MANTA_BLOCK 384
 #endif
 constexpr int kBlock = MANTA_BLOCK;
-constexpr int kQueueWords = 64 * (int)sizeof(Veh) / 4;   // per-warp lane-change queue (64 records)
 // fields of a finish-queue entry
 enum { kFqX, kFqV, kFqId, kFqRc, kFqRend, kFqE, kFqLd, kFqRow0, kFqCnl, kFqLim, kFqDst, kFqS, kFqI, kFqCell, kFqLb,
        kFqKind, kFqCL, kFqVL, kFqE2, kFqE2cnl, kFqFields };
 constexpr int kP3Words = 352 + kFqFields * 64;
-constexpr int kWarpWords = (kQueueWords + 64) > kP3Words ? (kQueueWords + 64) : kP3Words;
+constexpr int kWarpWords = kP3Words;
 constexpr size_t kDynSmem = (size_t)(kBlock / 32) * kWarpWords * 4;
 constexpr int kMinBlocksPerSM = MANTA_MIN_BLOCKS_PER_SM;
 
@@ -138,6 +137,15 @@ __device__ __forceinline__ EdgeMeta load_em(const Params &p, uint32_t e) {
   EdgeMeta m;
   m.row0 = q.x; m.cnl = q.y; m.lim = __uint_as_float(q.z); m.dst = q.w;
   return m;
+}
+__device__ __forceinline__ Veh load_veh_at(const Veh *r) {
+  const uint4 *a = reinterpret_cast<const uint4 *>(r);
+  const uint4 q0 = __ldcg(a), q1 = __ldcg(a + 1), q2 = __ldcg(a + 2);
+  Veh w;
+  w.x = __uint_as_float(q0.x); w.v = __uint_as_float(q0.y); w.id = q0.z; w.rc = q0.w;
+  w.rend = q1.x; w.e = q1.y; w.ld = q1.z; w.pcell = q1.w;
+  w.em.row0 = q2.x; w.em.cnl = q2.y; w.em.lim = __uint_as_float(q2.z); w.em.dst = q2.w;
+  return w;
 }
 __device__ __forceinline__ Veh load_veh(const Params &p, uint32_t s) {
   const uint4 *a = reinterpret_cast<const uint4 *>(p.veh + s);
@@ -639,11 +647,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
   __shared__ int s_ok;
   __shared__ unsigned long long s_cnt[CNT_N];
   __shared__ float s_sab2[8];                       // 2 sqrt(a b) per road class (Eq. 1)
-  // per-warp scratch (dynamic shared memory, kWarpWords words per warp): in
-  // P1 a queue of 64 lane-change candidates (vehicle records, then their
-  // list positions); in P3 the work pool (32 slots, list indices, first-batch
-  // offsets), 32 staged crossing requests (8 fields, field-major) and the
-  // finish queue (kFqFields fields x 64 entries)
+  // per-warp scratch of P3 (dynamic shared memory, kWarpWords words per
+  // warp): the work pool (32 slots, list indices, first-batch offsets), 32
+  // staged crossing requests (8 fields, field-major) and the finish queue
+  // (kFqFields fields x 64 entries)
   extern __shared__ __align__(16) uint32_t s_wbuf[];
   __shared__ int s_rqn[kBlock / 32];
   Ctl *ctl = p.ctl;
@@ -702,10 +709,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
       if (threadIdx.x == 0) { ctl->due_pos = lo0; ctl->due_hi = lo; }
     }
     {
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-      Veh *q = reinterpret_cast<Veh *>(s_wbuf + wid * kWarpWords);
-      uint32_t *qpos = s_wbuf + wid * kWarpWords + kQueueWords;   // list position of each queued vehicle
-      int qn = 0;   // warp-uniform queue length
+      const int lane = threadIdx.x & 31;
+      // each warp lists its candidates in a region of its own (at most one
+      // per list entry it visits); it decides them after its record loop
+      const uint32_t wg = gtid >> 5;
+      const uint32_t reg0 = wg * 32u * ((nact + gsz - 1u) / gsz);
+      uint32_t ncand = 0;   // warp-uniform
       uint32_t base = gtid - (uint32_t)lane;
       uint32_t s_nx = base + lane < nact ? __ldcg(act_in + base + lane) : MANTA_NONE;
       for (; base < nact; base += gsz) {
@@ -733,39 +742,31 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
           const int lt = ln + ((k & 1) ? -1 : 1);
           cand = nl >= 2 && lt >= 0 && lt < nl &&
                  (w.v > 0.0f || !((ld_mask(w.ld) >> ln) & 1u) || closable(w.em) || ld_nxclo(w.ld));
-          if (cand) w.pcell = s;          // the queue entry carries the slot in pcell
+          if (cand) w.pcell = s;          // the list entry carries the slot in pcell
         }
+        // candidates join the warp's lane-change list (a copy of the record
+        // and the list position)
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
         if (cand) {
-          const int at = qn + __popc(bal & ((1u << lane) - 1u));
-          q[at] = w;
-          qpos[at] = pos;
+          const uint32_t at = reg0 + ncand + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+          p.lcq[at] = w;
+          p.lcq_pos[at] = pos;
         }
-        qn += __popc(bal);
-        __syncwarp();
-        if (qn >= 32) {
-          // a full warp of lane-change decisions
-          const Veh c = q[lane];
-          const uint32_t cpos = qpos[lane];
+        ncand += (uint32_t)__popc(bal);
+      }
+      // lane-change decisions on M_k, a full warp of candidates at a time
+      __syncwarp();
+      for (uint32_t b0 = 0; b0 < ncand; b0 += 32u) {
+        const uint32_t j = b0 + (uint32_t)lane;
+        if (j < ncand) {
+          const Veh c = load_veh_at(p.lcq + reg0 + j);
+          const uint32_t cpos = __ldcg(p.lcq_pos + reg0 + j);
           const int tgt = lc_decide(p, cur, k, c, c_lce);
           if (tgt >= 0) p.veh[c.pcell].ld = (c.ld & 0xFF00FFFFu) | ((uint32_t)tgt << 16);
           const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
           if (tgt >= 0) { p.chg[at] = c.pcell; p.chg_pos[at] = cpos; }
-          __syncwarp();
-          if (lane < qn - 32) { q[lane] = q[32 + lane]; qpos[lane] = qpos[32 + lane]; }
-          qn -= 32;
-          __syncwarp();
         }
       }
-      if (lane < qn) {
-        const Veh c = q[lane];
-        const uint32_t cpos = qpos[lane];
-        const int tgt = lc_decide(p, cur, k, c, c_lce);
-        if (tgt >= 0) p.veh[c.pcell].ld = (c.ld & 0xFF00FFFFu) | ((uint32_t)tgt << 16);
-        const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
-        if (tgt >= 0) { p.chg[at] = c.pcell; p.chg_pos[at] = cpos; }
-      }
-      __syncwarp();
     }
     for (uint32_t j = gtid; j < p.n_stop; j += gsz) {
       const uint32_t n = __ldg(p.stop_nodes + j);
