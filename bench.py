@@ -57,9 +57,14 @@ def algorithmic_bytes(d: dict) -> int:
 def kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
+    # over the sources with comments and blank lines removed, so that a
+    # comment edit does not invalidate counters taken on the same code
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f)) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
@@ -69,8 +74,9 @@ def measured_traffic_per_update():
     try:
         vals = {}
         for line in open(os.path.join(ROOT, TRAFFIC_PROFILE)):
-            if ":" in line and line.strip().startswith(("kernel_sha256", "dram_bytes_per_vehicle_update")):
-                k, v = line.strip().strip("-* `").split(":", 1)
+            line = line.strip().strip("-* `")
+            if ":" in line and line.startswith(("kernel_sha256", "dram_bytes_per_vehicle_update")):
+                k, v = line.split(":", 1)
                 vals[k.strip(" `")] = v.strip(" `")
         if vals.get("kernel_sha256") == kernel_hash():
             return float(vals["dram_bytes_per_vehicle_update"])

@@ -2,9 +2,10 @@
 //
 // One cooperative launch runs n_steps steps.  Per step k the grid goes
 // through four phases separated by grid barriers with bounded waits:
-//   P1  clear last step's cells in the spare map buffer; lane-change decision
-//       on M_k (Section II-D, Eqs. 2-4); stop-sign permits for this step;
-//       the departure-step range of the trips that join queues at k + 1
+//   P1  clear last step's cells in the spare map buffer; the first lane-map
+//       batch of every vehicle's leader scan; lane-change decisions on M_k
+//       (Section II-D, Eqs. 2-4); stop-sign permits for this step; the
+//       departure-step range of the trips that join queues at k + 1
 //   P2  lane-change apply in place, M_k -> M_k' (skipped when nobody changes)
 //   P3  leader scan along the route on M_k', IDM (Eq. 1), ballistic update,
 //       clamp; write M_{k+1} for vehicles that stay on their edge; crossing
@@ -16,11 +17,12 @@
 // every operation is one correctly rounded IEEE op.
 //
 // The path is latency-bound on dependent global loads (vehicle record ->
-// edge record -> lane-map row -> route entry -> next edge record -> next
-// row), so the code issues independent loads together: vehicle records are
-// one 32-byte record, lane-map scans issue four 16-byte loads per round trip,
-// and the next route edge and its edge record are fetched while the current
-// row is being scanned.
+// lane-map row -> node data -> next row), so the code keeps many independent
+// loads in flight: in P3 every lane runs its own vehicle through a state
+// machine of one round trip per iteration and takes a new vehicle as soon as
+// one is done; the vehicle record and its first row batch come back together;
+// lane-map scans issue four 16-byte loads per round trip; and the next
+// segment's node data comes with the batch that ends the current one.
 #include <stdint.h>
 #include "sim.cuh"
 
