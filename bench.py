@@ -72,12 +72,12 @@ def measured_traffic_per_update():
     """DRAM bytes per vehicle update from the committed ncu summary, if it was
     taken on the kernel as it is now (same source hash); else None."""
     try:
+        import re
         vals = {}
         for line in open(os.path.join(ROOT, TRAFFIC_PROFILE)):
-            line = line.strip().strip("-* `")
-            if ":" in line and line.startswith(("kernel_sha256", "dram_bytes_per_vehicle_update")):
-                k, v = line.split(":", 1)
-                vals[k.strip(" `")] = v.strip(" `")
+            m = re.match(r"\s*-\s*(kernel_sha256|dram_bytes_per_vehicle_update):\s*`([^`]*)`", line)
+            if m:
+                vals[m.group(1)] = m.group(2)
         if vals.get("kernel_sha256") == kernel_hash():
             return float(vals["dram_bytes_per_vehicle_update"])
     except Exception:
