@@ -361,8 +361,12 @@ def cpu_baseline(net, tr, n_steps):
 
 def run_ensemble(args):
     """64 uneven what-if scenarios, one simulated hour each (07:00-08:00), run
-    (a) batched: one simulation of the disjoint union, one launch per 2048 steps;
-    (b) sequential: one simulation per scenario, one after another.
+    (a) batched: one simulation of the disjoint union.  On a first instance
+        the autotuner times every launch shape of the step kernel (on the
+        live run) and picks one; every timed instance is then advanced by
+        replaying a CUDA graph captured for the whole hour (setup untimed);
+    (b) sequential: one simulation per scenario, one after another, with
+        plain step calls in the default shape.
     A bench step is one complete ensemble; value = scenarios/s of (a)."""
     import torch
 
@@ -380,30 +384,47 @@ def run_ensemble(args):
     t0 = int(7 * 3600 / 0.5)
     steps = 7200
 
-    def timed(sim):
+    def make(net, tr):
+        sim = manta.Sim(net, stream=stream, t0_step=t0, n_stats_windows=16)
+        sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+        return sim
+
+    def timed(fn):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        sim.step(steps)
+        fn()
         ev1.record(stream)
         ev1.synchronize()
         return ev0.elapsed_time(ev1) / 1000.0
 
-    batched, upd = [], 0
+    # autotune on a first instance of the union (2 rounds of 300 steps per shape)
+    sim = make(ens.net, ens.trips)
+    chosen, tune_ms = sim.autotune(trial_steps=300, rounds=2)
+    sim.close()
+    shapes = manta.variants()
+    batched, plain, upd = [], [], 0
     for it in range(args.warmup + args.steps):
-        sim = manta.Sim(ens.net, stream=stream, t0_step=t0, n_stats_windows=16)
-        sim.load_trips(ens.trips.route_off, ens.trips.route_edges, ens.trips.depart_time_s)
-        dt = timed(sim)
+        sim = make(ens.net, ens.trips)
+        sim.variant = chosen
+        gr = sim.graph(steps)
+        dt = timed(lambda: gr.launch(1))
         if it >= args.warmup:
             batched.append(dt)
             upd = sim.stats()["vehicle_updates"]
+        gr.close()
         sim.close()
+        if it == args.warmup:
+            # the same ensemble advanced by plain step calls, for comparison
+            sim = make(ens.net, ens.trips)
+            sim.variant = chosen
+            plain.append(timed(lambda: sim.step(steps)))
+            sim.close()
     seq = 0.0
     seq_upd = 0
     for net, tr in sc:
-        sim = manta.Sim(net, stream=stream, t0_step=t0, n_stats_windows=16)
-        sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
-        seq += timed(sim)
+        sim = make(net, tr)
+        seq += timed(lambda: sim.step(steps))
         seq_upd += sim.stats()["vehicle_updates"]
         sim.close()
     tb = sum(batched) / len(batched)
@@ -418,10 +439,14 @@ def run_ensemble(args):
                    "edges_per_scenario": [int(x) for x in np.diff(ens.edge_off)],
                    "trips_per_scenario": [int(x) for x in np.diff(ens.trip_off)],
                    "sim_steps": steps, "t0_step": t0},
+        "autotune": {"shapes": [list(x) for x in shapes],
+                     "ms_per_million_updates": [float(x) for x in tune_ms], "trial_steps": 300, "rounds": 2,
+                     "chosen": list(shapes[chosen])},
         "batched": {"seconds": tb, "scenarios_per_s": n / tb, "vehicle_updates": upd,
-                    "vehicle_updates_per_s": upd / tb},
+                    "vehicle_updates_per_s": upd / tb, "launch": "CUDA graph replay",
+                    "plain_step_calls_seconds": plain[0] if plain else None},
         "sequential": {"seconds": seq, "scenarios_per_s": n / seq, "vehicle_updates": seq_upd,
-                       "vehicle_updates_per_s": seq_upd / seq},
+                       "vehicle_updates_per_s": seq_upd / seq, "shape": list(shapes[0])},
         "batched_over_sequential": seq / tb,
         "gpu_launches": args.steps * ((steps + 2047) // 2048)}))
 

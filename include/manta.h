@@ -191,6 +191,48 @@ MANTA_API manta_status manta_lane_map(manta_sim *sim, uint8_t *out, int64_t cap,
  * the grid barrier that ends it.  A profiling aid. */
 MANTA_API manta_status manta_phase_times(manta_sim *sim, double *ms4);
 
+/* ---- launch shapes and autotuning ------------------------------------
+ * The step kernel exists in several launch shapes (threads per block,
+ * minimum blocks per SM: the second sets the register budget).  Every shape
+ * computes the same results bit for bit; only speed differs with the
+ * workload.  A new simulation uses shape 0. */
+MANTA_API int32_t manta_variant_count(void);
+/* Threads per block and minimum blocks per SM of shape v (either pointer may
+ * be NULL); MANTA_E_INVALID if v is out of range. */
+MANTA_API manta_status manta_variant_info(int32_t v, int32_t *threads, int32_t *min_blocks_per_sm);
+/* Selects the shape used by later manta_step calls and graph captures. */
+MANTA_API manta_status manta_set_variant(manta_sim *sim, int32_t v);
+/* Shape in use, or -1 for NULL. */
+MANTA_API int32_t manta_get_variant(const manta_sim *sim);
+/* Autotuner: runs `rounds` rounds in which every shape advances the
+ * simulation by `trial_steps` steps (in alternating order from round to
+ * round), timed with CUDA events on the sim's stream, and selects the shape
+ * with the least device time per vehicle update; returns it in *chosen.
+ * ms (optional, manta_variant_count() floats) receives each shape's score:
+ * milliseconds per million vehicle updates, or milliseconds per round if
+ * some shape's trials saw no vehicle.  The simulation really advances by
+ * rounds x count x trial_steps steps: tune on the live run, whose results
+ * do not depend on the shapes chosen.  Synchronises the stream; device
+ * errors are reported as by manta_stats. */
+MANTA_API manta_status manta_autotune(manta_sim *sim, int64_t trial_steps, int32_t rounds, int32_t *chosen,
+                                      float *ms);
+
+/* ---- CUDA graphs -------------------------------------------------------
+ * manta_graph_capture records the launches that advance the simulation by
+ * n_steps steps (barrier resets and cooperative step launches, in the shape
+ * selected now) into an executable CUDA graph, without running them; the
+ * sim must have been created on a non-default stream.  Every
+ * manta_graph_launch replays them on the sim's stream, asynchronously, and
+ * advances the simulation by n_steps: the kernels take their first step
+ * index from device memory, so replays continue where the previous work
+ * left off.  Replays and manta_step calls may be mixed.  The graph refers
+ * to the simulation and must be destroyed before it. */
+typedef struct manta_graph manta_graph;
+MANTA_API manta_status manta_graph_capture(manta_sim *sim, int64_t n_steps, manta_graph **out);
+MANTA_API manta_status manta_graph_launch(manta_graph *graph);
+/* Releases the graph (NULL is a no-op). */
+MANTA_API void manta_graph_destroy(manta_graph *graph);
+
 /* Bytes of the canonical lane map (sum over edges of cells x lanes). */
 MANTA_API int64_t manta_lane_map_bytes(const manta_sim *sim);
 

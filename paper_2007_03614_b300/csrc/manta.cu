@@ -69,8 +69,24 @@ struct manta_sim {
   std::vector<uint32_t> route_off_h;
   std::vector<EdgeMeta> em_h;
   std::vector<long long> clo_k0, clo_k1;
-  int grid = 0;
+  int grid[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // co-resident grid size of every launch shape
+  int variant = 0;                          // launch shape used by manta_step
 };
+
+// Launch shapes of the step kernel (threads per block, minimum blocks per
+// SM); the second number sets the register budget.  All shapes compute the
+// same results bit for bit; manta_autotune picks the fastest on the live run.
+struct StepVariant {
+  int threads, min_blocks;
+  const void *fn;
+};
+static const StepVariant kVariants[] = {
+    {384, 1, (const void *)manta_step_kernel<384, 1>},
+    {256, 1, (const void *)manta_step_kernel<256, 1>},
+    {256, 2, (const void *)manta_step_kernel<256, 2>},
+    {192, 2, (const void *)manta_step_kernel<192, 2>},
+};
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
 // Static device memory for manta_run_noalloc: every device that loads the
 // library holds these bytes until the process exits.
@@ -376,17 +392,21 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   P.E = (uint32_t)E; P.N = (uint32_t)N; P.n_stop = (uint32_t)stops.size(); P.mtab_n = (uint32_t)mtab.size();
   P.wait_limit_ns = kWaitLimitNs;
   S->k = cfg->t0_step;
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaFuncSetAttribute(manta_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem) !=
-          cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, manta_step_kernel, kBlock, kDynSmem) != cudaSuccess ||
-      per_sm < 1) {
-    manta_destroy(S);
-    return fail(MANTA_E_CUDA, "occupancy query failed");
+  for (int v = 0; v < kNumVariants; ++v) {
+    const StepVariant &sv = kVariants[v];
+    const size_t smem = step_smem_bytes(sv.threads);
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(sv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv.fn, sv.threads, smem) != cudaSuccess ||
+        per_sm < 1) {
+      manta_destroy(S);
+      return fail(MANTA_E_CUDA, "occupancy query failed");
+    }
+    S->grid[v] = sms * per_sm;
   }
-  S->grid = sms * per_sm;
   *out = S;
   return MANTA_OK;
 }
@@ -475,7 +495,9 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   P.p3a = dalloc<uint32_t>(S, NT, &ok); P.chg_pos = dalloc<uint32_t>(S, NT, &ok);
   // candidate regions: every warp may list one candidate per entry it visits,
   // 32 entries per grid-stride block
-  const size_t NC = NT + (size_t)S->grid * kBlock;
+  size_t gmax = 0;
+  for (int v = 0; v < kNumVariants; ++v) gmax = std::max(gmax, (size_t)S->grid[v] * kVariants[v].threads);
+  const size_t NC = NT + gmax;
   P.lcq = dalloc<Veh>(S, NC, &ok); P.lcq_pos = dalloc<uint32_t>(S, NC, &ok);
   P.req = dalloc<uint32_t>(S, NT, &ok); P.arr = dalloc<uint32_t>(S, NT, &ok);
   P.req_x = dalloc<float>(S, NT, &ok); P.req_v = dalloc<float>(S, NT, &ok); P.req_dw = dalloc<uint32_t>(S, NT, &ok);
@@ -488,6 +510,7 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   memset(&c0, 0, sizeof(c0));
   c0.due_pos = prime_hi;
   c0.due_hi = prime_hi;
+  c0.k_next = S->k;
   cp = cp && cudaMemcpyAsync(P.ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
   if (!cp) return fail(MANTA_E_CUDA, "upload failed in manta_load_trips");
   P.nclo = d_nclo;
@@ -527,30 +550,6 @@ manta_status manta_set_lane_closure(manta_sim *S, int32_t edge, int32_t lane, in
   return MANTA_OK;
 }
 
-manta_status manta_step(manta_sim *S, int64_t n_steps) {
-  g_err.clear();
-  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
-  if (!S->loaded) return fail(MANTA_E_STATE, "no trips loaded");
-  if (S->dead) return fail(MANTA_E_STATE, "simulation stopped after a device error");
-  if (n_steps < 0) return fail(MANTA_E_INVALID, "n_steps < 0");
-  while (n_steps > 0) {
-    const int32_t chunk = (int32_t)std::min<int64_t>(n_steps, kStepsPerLaunch);
-    Params P = S->P;
-    P.k0 = S->k;
-    P.n_steps = chunk;
-    void *args[] = {&P};
-    // the grid barrier's arrival counter starts from zero in every launch
-    cudaError_t e = cudaMemsetAsync(&S->P.ctl->bar_count, 0, sizeof(unsigned), S->stream);
-    if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("barrier reset: ") + cudaGetErrorString(e));
-    e = cudaLaunchCooperativeKernel((const void *)manta_step_kernel, dim3(S->grid), dim3(kBlock), args, kDynSmem,
-                                    S->stream);
-    if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
-    S->k += chunk;
-    n_steps -= chunk;
-  }
-  return MANTA_OK;
-}
-
 namespace {
 manta_status sync_and_check(manta_sim *S, Ctl *c) {
   cudaError_t e = cudaStreamSynchronize(S->stream);
@@ -562,6 +561,181 @@ manta_status sync_and_check(manta_sim *S, Ctl *c) {
   return MANTA_OK;
 }
 }  // namespace
+
+namespace {
+// Enqueues the launches for n_steps steps on the sim's stream: per launch of
+// at most kStepsPerLaunch steps, a reset of the barrier's arrival counter and
+// one cooperative launch.  With from_ctl the kernel takes its first step
+// index from the control block (which every launch advances), so the same
+// launches can be captured once and replayed.
+manta_status enqueue_steps(manta_sim *S, int64_t n_steps, bool from_ctl) {
+  const StepVariant &sv = kVariants[S->variant];
+  int64_t k = S->k;
+  while (n_steps > 0) {
+    const int32_t chunk = (int32_t)std::min<int64_t>(n_steps, kStepsPerLaunch);
+    Params P = S->P;
+    P.k0 = k;
+    P.k_from_ctl = from_ctl ? 1 : 0;
+    P.n_steps = chunk;
+    void *args[] = {&P};
+    cudaError_t e = cudaMemsetAsync(&S->P.ctl->bar_count, 0, sizeof(unsigned), S->stream);
+    if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("barrier reset: ") + cudaGetErrorString(e));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(S->grid[S->variant]);
+    lc.blockDim = dim3(sv.threads);
+    lc.dynamicSmemBytes = step_smem_bytes(sv.threads);
+    lc.stream = S->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    e = cudaLaunchKernelExC(&lc, sv.fn, args);
+    if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+    k += chunk;
+    n_steps -= chunk;
+  }
+  return MANTA_OK;
+}
+manta_status check_steppable(const manta_sim *S) {
+  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
+  if (!S->loaded) return fail(MANTA_E_STATE, "no trips loaded");
+  if (S->dead) return fail(MANTA_E_STATE, "simulation stopped after a device error");
+  return MANTA_OK;
+}
+}  // namespace
+
+manta_status manta_step(manta_sim *S, int64_t n_steps) {
+  g_err.clear();
+  manta_status st = check_steppable(S);
+  if (st != MANTA_OK) return st;
+  if (n_steps < 0) return fail(MANTA_E_INVALID, "n_steps < 0");
+  st = enqueue_steps(S, n_steps, false);
+  if (st == MANTA_OK) S->k += n_steps;
+  return st;
+}
+
+int32_t manta_variant_count(void) { return kNumVariants; }
+
+manta_status manta_variant_info(int32_t v, int32_t *threads, int32_t *min_blocks_per_sm) {
+  g_err.clear();
+  if (v < 0 || v >= kNumVariants) return fail(MANTA_E_INVALID, "variant out of range");
+  if (threads) *threads = kVariants[v].threads;
+  if (min_blocks_per_sm) *min_blocks_per_sm = kVariants[v].min_blocks;
+  return MANTA_OK;
+}
+
+manta_status manta_set_variant(manta_sim *S, int32_t v) {
+  g_err.clear();
+  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
+  if (v < 0 || v >= kNumVariants) return fail(MANTA_E_INVALID, "variant out of range");
+  S->variant = v;
+  return MANTA_OK;
+}
+
+int32_t manta_get_variant(const manta_sim *S) { return S ? S->variant : -1; }
+
+manta_status manta_autotune(manta_sim *S, int64_t trial_steps, int32_t rounds, int32_t *chosen, float *ms) {
+  g_err.clear();
+  manta_status st = check_steppable(S);
+  if (st != MANTA_OK) return st;
+  if (trial_steps < 1 || rounds < 1) return fail(MANTA_E_INVALID, "trial_steps and rounds must be >= 1");
+  // device time and vehicle updates of every shape's trials; the load of
+  // the live run changes from trial to trial, so shapes are ranked by time
+  // per vehicle update, and the order of the shapes alternates by round
+  std::vector<double> tms(kNumVariants, 0.0), upd(kNumVariants, 0.0);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(MANTA_E_CUDA, "event creation failed");
+  }
+  Ctl c;
+  st = sync_and_check(S, &c);
+  unsigned long long u0 = c.cnt[CNT_UPD];
+  for (int r = 0; r < rounds && st == MANTA_OK; ++r) {
+    for (int j = 0; j < kNumVariants && st == MANTA_OK; ++j) {
+      const int v = (r & 1) ? kNumVariants - 1 - j : j;
+      S->variant = v;
+      cudaEventRecord(e0, S->stream);
+      st = enqueue_steps(S, trial_steps, false);
+      if (st != MANTA_OK) break;
+      S->k += trial_steps;
+      cudaEventRecord(e1, S->stream);
+      st = sync_and_check(S, &c);
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e0, e1);
+      tms[v] += t;
+      upd[v] += (double)(c.cnt[CNT_UPD] - u0);
+      u0 = c.cnt[CNT_UPD];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MANTA_OK) return st;
+  // milliseconds per million vehicle updates (per round when a shape saw none)
+  std::vector<double> score(kNumVariants);
+  bool any_empty = false;
+  for (int v = 0; v < kNumVariants; ++v) any_empty = any_empty || upd[v] <= 0.0;
+  for (int v = 0; v < kNumVariants; ++v) score[v] = any_empty ? tms[v] / rounds : tms[v] / (upd[v] * 1e-6);
+  int best = 0;
+  for (int v = 1; v < kNumVariants; ++v)
+    if (score[v] < score[best]) best = v;
+  S->variant = best;
+  if (chosen) *chosen = best;
+  if (ms)
+    for (int v = 0; v < kNumVariants; ++v) ms[v] = (float)score[v];
+  return MANTA_OK;
+}
+
+struct manta_graph {
+  manta_sim *sim;
+  int64_t n_steps;
+  cudaGraphExec_t exec;
+};
+
+manta_status manta_graph_capture(manta_sim *S, int64_t n_steps, manta_graph **out) {
+  g_err.clear();
+  if (!out) return fail(MANTA_E_INVALID, "out is NULL");
+  *out = nullptr;
+  manta_status st = check_steppable(S);
+  if (st != MANTA_OK) return st;
+  if (n_steps < 1) return fail(MANTA_E_INVALID, "n_steps < 1");
+  if (!S->stream) return fail(MANTA_E_INVALID, "graph capture needs a created (non-default) stream");
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(MANTA_E_CUDA, "stream capture could not begin");
+  st = enqueue_steps(S, n_steps, true);
+  const cudaError_t ee = cudaStreamEndCapture(S->stream, &g);
+  if (st != MANTA_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (ee != cudaSuccess || !g) return fail(MANTA_E_CUDA, std::string("stream capture: ") + cudaGetErrorString(ee));
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return fail(MANTA_E_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(ei));
+  *out = new manta_graph{S, n_steps, ex};
+  return MANTA_OK;
+}
+
+manta_status manta_graph_launch(manta_graph *G) {
+  g_err.clear();
+  if (!G) return fail(MANTA_E_INVALID, "graph is NULL");
+  manta_status st = check_steppable(G->sim);
+  if (st != MANTA_OK) return st;
+  const cudaError_t e = cudaGraphLaunch(G->exec, G->sim->stream);
+  if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  G->sim->k += G->n_steps;
+  return MANTA_OK;
+}
+
+void manta_graph_destroy(manta_graph *G) {
+  if (!G) return;
+  cudaGraphExecDestroy(G->exec);
+  delete G;
+}
+
 
 manta_status manta_stats(manta_sim *S, manta_stats_t *out) {
   g_err.clear();

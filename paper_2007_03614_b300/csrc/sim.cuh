@@ -72,6 +72,7 @@ struct Ctl {
   uint32_t n_compact;     // entries written by a compaction pass
   uint32_t next3;          // next chunk of the active list for phase P3
   uint32_t pad[2];
+  long long k_next;        // step index the next launch starts from (each launch advances it)
   uint32_t n_dep[2];
   uint32_t n_req, n_arr, n_chg, n_depwin;
   uint32_t free_count, n_slots;
@@ -142,5 +143,6 @@ struct Params {
   // launch
   int64_t k0;
   int32_t n_steps;
+  int32_t k_from_ctl;          // take the first step index from ctl->k_next instead of k0
   uint64_t wait_limit_ns;
 };

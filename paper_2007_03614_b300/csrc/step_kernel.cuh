@@ -26,20 +26,17 @@
 #include <stdint.h>
 #include "sim.cuh"
 
-#ifndef MANTA_MIN_BLOCKS_PER_SM
-#define MANTA_MIN_BLOCKS_PER_SM 1
-#endif
-#ifndef MANTA_BLOCK
-#define MANTA_BLOCK 384
-#endif
-constexpr int kBlock = MANTA_BLOCK;
+// Threads per block of the helper kernels.  The step kernel is a template
+// over its launch shape (threads per block, minimum blocks per SM), which
+// sets its register budget; every shape computes the same results.
+constexpr int kBlock = 256;
 // fields of a finish-queue entry
 enum { kFqX, kFqV, kFqId, kFqRc, kFqRend, kFqE, kFqLd, kFqRow0, kFqCnl, kFqLim, kFqDst, kFqS, kFqI, kFqCell, kFqLb,
        kFqKind, kFqCL, kFqVL, kFqE2, kFqE2cnl, kFqFields };
 constexpr int kP3Words = 352 + kFqFields * 64;
 constexpr int kWarpWords = kP3Words;
-constexpr size_t kDynSmem = (size_t)(kBlock / 32) * kWarpWords * 4;
-constexpr int kMinBlocksPerSM = MANTA_MIN_BLOCKS_PER_SM;
+// dynamic shared memory of a step-kernel block of `threads` threads
+constexpr size_t step_smem_bytes(int threads) { return (size_t)(threads / 32) * kWarpWords * 4; }
 
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
@@ -645,7 +642,8 @@ __device__ __forceinline__ void flush_requests(const Params &p, const uint32_t *
 }
 
 // ------------------------------------------------------------ the kernel
-__global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Params p) {
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
   __shared__ int s_ok;
   __shared__ unsigned long long s_cnt[CNT_N];
   __shared__ float s_sab2[8];                       // 2 sqrt(a b) per road class (Eq. 1)
@@ -654,7 +652,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
   // staged crossing requests (8 fields, field-major) and the finish queue
   // (kFqFields fields x 64 entries)
   extern __shared__ __align__(16) uint32_t s_wbuf[];
-  __shared__ int s_rqn[kBlock / 32];
+  __shared__ int s_rqn[BLOCK / 32];
   Ctl *ctl = p.ctl;
   if (threadIdx.x < CNT_N) s_cnt[threadIdx.x] = 0ull;
   if (threadIdx.x < 8) s_sab2[threadIdx.x] = 2.0f * sqrtf(p.a[threadIdx.x] * p.b[threadIdx.x]);
@@ -669,9 +667,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
   const int L = p.L;
   bool alive = ldvi(&ctl->err) == 0;
   unsigned bar_target = 0;
+  // first step of this launch: from the host, or from the control block when
+  // the launch is replayed from a captured graph
+  const int64_t kbase = p.k_from_ctl ? (int64_t)(*(const volatile long long *)&ctl->k_next) : p.k0;
   uint64_t tp = timer ? globaltimer() : 0;
   for (int it = 0; it < p.n_steps && alive; ++it) {
-    const int64_t k = p.k0 + it;
+    const int64_t k = kbase + it;
     const int cb = (int)(k & 1);
     uint8_t *cur = cb ? p.atlas1 : p.atlas0;
     uint8_t *nxt = cb ? p.atlas0 : p.atlas1;
@@ -844,7 +845,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
     {
       const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
       const unsigned lt_mask = (1u << wl) - 1u;
-      const uint32_t nwarps = gridDim.x * (kBlock / 32);
+      const uint32_t nwarps = gridDim.x * (BLOCK / 32);
       uint32_t *const wb = s_wbuf + wid * kWarpWords;
       uint32_t *ps = wb, *pi = wb + 32, *pa = wb + 64;
       uint32_t *fq = wb + 352;   // finish queue: kFqFields fields x 64 entries
@@ -1213,6 +1214,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) manta_step_kernel(Par
   atomicAdd(&s_cnt[CNT_ARR], (unsigned long long)c_arr);
   __syncthreads();
   if (threadIdx.x < CNT_N && s_cnt[threadIdx.x]) atomicAdd(&ctl->cnt[threadIdx.x], s_cnt[threadIdx.x]);
-  if (timer)
+  if (timer) {
     for (int q = 0; q < 4; ++q) ctl->phase_ns[q] += ph[q];
+    if (alive) ctl->k_next = kbase + p.n_steps;
+  }
 }

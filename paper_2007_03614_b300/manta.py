@@ -48,7 +48,9 @@ class MantaStats(C.Structure):
 EXPORTS = ("manta_default_config", "manta_create", "manta_load_trips", "manta_step", "manta_stats",
            "manta_edge_counters", "manta_snapshot", "manta_lane_map", "manta_lane_map_bytes",
            "manta_destroy", "manta_last_error", "manta_selftest_barrier_timeout", "manta_run_noalloc",
-           "manta_phase_times", "manta_set_lane_closure")
+           "manta_phase_times", "manta_set_lane_closure", "manta_variant_count", "manta_variant_info",
+           "manta_set_variant", "manta_get_variant", "manta_autotune", "manta_graph_capture",
+           "manta_graph_launch", "manta_graph_destroy")
 
 _lib = None
 
@@ -96,6 +98,21 @@ def load_library():
         lib.manta_phase_times.argtypes = [P, P]
         lib.manta_selftest_barrier_timeout.restype = C.c_int
         lib.manta_selftest_barrier_timeout.argtypes = [C.c_int32, P]
+        lib.manta_variant_count.restype = C.c_int32
+        lib.manta_variant_count.argtypes = []
+        lib.manta_variant_info.restype = C.c_int
+        lib.manta_variant_info.argtypes = [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        lib.manta_set_variant.restype = C.c_int
+        lib.manta_set_variant.argtypes = [P, C.c_int32]
+        lib.manta_get_variant.restype = C.c_int32
+        lib.manta_get_variant.argtypes = [P]
+        lib.manta_autotune.restype = C.c_int
+        lib.manta_autotune.argtypes = [P, C.c_int64, C.c_int32, C.POINTER(C.c_int32), P]
+        lib.manta_graph_capture.restype = C.c_int
+        lib.manta_graph_capture.argtypes = [P, C.c_int64, C.POINTER(P)]
+        lib.manta_graph_launch.restype = C.c_int
+        lib.manta_graph_launch.argtypes = [P]
+        lib.manta_graph_destroy.argtypes = [P]
         _lib = lib
     return _lib
 
@@ -211,12 +228,72 @@ class Sim:
         _check(self._lib.manta_phase_times(self._h, _p(out)))
         return out
 
+    @property
+    def variant(self) -> int:
+        return int(self._lib.manta_get_variant(self._h))
+
+    @variant.setter
+    def variant(self, v):
+        _check(self._lib.manta_set_variant(self._h, int(v)))
+
+    def autotune(self, trial_steps=60, rounds=1):
+        """Times every launch shape on the live run (which advances by
+        rounds x shapes x trial_steps steps) and keeps the one with the least
+        time per vehicle update; returns (chosen shape, score of every shape
+        in ms per million vehicle updates)."""
+        n = int(self._lib.manta_variant_count())
+        ms = np.zeros(n, np.float32)
+        ch = C.c_int32()
+        _check(self._lib.manta_autotune(self._h, int(trial_steps), int(rounds), C.byref(ch), _p(ms)))
+        return ch.value, ms
+
+    def graph(self, n_steps) -> "Graph":
+        return Graph(self, n_steps)
+
     def lane_map(self) -> np.ndarray:
         nb = int(self._lib.manta_lane_map_bytes(self._h))
         buf = np.zeros(max(nb, 1), np.uint8)
         cnt = C.c_int64()
         _check(self._lib.manta_lane_map(self._h, _p(buf), buf.size, C.byref(cnt)))
         return buf[:cnt.value]
+
+
+def variants() -> list:
+    """Launch shapes of the step kernel as (threads per block, min blocks per SM)."""
+    lib = load_library()
+    out = []
+    for v in range(lib.manta_variant_count()):
+        t, b = C.c_int32(), C.c_int32()
+        _check(lib.manta_variant_info(v, C.byref(t), C.byref(b)))
+        out.append((t.value, b.value))
+    return out
+
+
+class Graph:
+    """Captured launches advancing a Sim by n_steps per replay (include/manta.h)."""
+
+    def __init__(self, sim, n_steps):
+        self._lib = sim._lib
+        self.sim = sim
+        self.n_steps = int(n_steps)
+        h = C.c_void_p()
+        _check(self._lib.manta_graph_capture(sim._h, self.n_steps, C.byref(h)))
+        self._h = h
+
+    def launch(self, times=1):
+        for _ in range(times):
+            _check(self._lib.manta_graph_launch(self._h))
+
+    def close(self):
+        if self._h:
+            self._lib.manta_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def selftest_barrier_timeout(limit_ms=100, stream=None) -> int:
