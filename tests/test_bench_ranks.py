@@ -46,3 +46,31 @@ def test_two_rank_aggregation_gloo():
 def test_single_process_aggregation_is_identity():
     import bench
     assert bench.aggregate_ranks(1.5, 42) == (1.5, 42.0)
+
+
+def test_traffic_figure_is_read_only_for_the_profiled_kernel(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu summary only while the
+    kernel code hash matches the one the counters were taken on."""
+    import bench
+    prof = tmp_path / "prof.md"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", "prof.md")
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", [])
+    prof.write_text(f"# x\n\n- kernel_sha256: `{bench.kernel_hash()}` (comment-free code)\n"
+                    "- dram_bytes_per_vehicle_update: `123.5`\n")
+    assert bench.measured_traffic_per_update() == 123.5
+    prof.write_text("- kernel_sha256: `0000000000000000`\n- dram_bytes_per_vehicle_update: `123.5`\n")
+    assert bench.measured_traffic_per_update() is None
+
+
+def test_kernel_hash_ignores_comments(tmp_path, monkeypatch):
+    import bench
+    src = tmp_path / "k.cuh"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", ["k.cuh"])
+    src.write_text("int f() { return 1; }  // one\n")
+    h1 = bench.kernel_hash()
+    src.write_text("// a comment\nint f() { return 1; }  // two\n\n")
+    assert bench.kernel_hash() == h1
+    src.write_text("int f() { return 2; }\n")
+    assert bench.kernel_hash() != h1
