@@ -233,6 +233,82 @@ MANTA_API manta_status manta_graph_launch(manta_graph *graph);
 /* Releases the graph (NULL is a no-op). */
 MANTA_API void manta_graph_destroy(manta_graph *graph);
 
+/* ---- checkpoints ------------------------------------------------------
+ * manta_checkpoint_save copies the simulation's whole mutable device state
+ * (lane maps, vehicle records, lists, queues, request and stop slots,
+ * permits, statistics, control block) into a new device buffer,
+ * asynchronously on the sim's stream; manta_checkpoint_restore copies it
+ * back, and the run continues from the saved step as if it had never left
+ * it (results are bit-identical).  Checkpoints belong to the simulation they
+ * were taken from and must be destroyed before it. */
+typedef struct manta_checkpoint manta_checkpoint;
+MANTA_API manta_status manta_checkpoint_save(manta_sim *sim, manta_checkpoint **out);
+MANTA_API manta_status manta_checkpoint_restore(manta_sim *sim, const manta_checkpoint *ckpt);
+/* Step index of the saved state, or -1 for NULL. */
+MANTA_API int64_t manta_checkpoint_step(const manta_checkpoint *ckpt);
+/* Device bytes held by the checkpoint. */
+MANTA_API int64_t manta_checkpoint_bytes(const manta_checkpoint *ckpt);
+MANTA_API void manta_checkpoint_destroy(manta_checkpoint *ckpt);
+
+/* ---- event tape and adjoint (calibration of Eq. 1's parameters) --------
+ * manta_tape_start makes the next n_steps steps (from the current one)
+ * record, per trip and step, the continuous state entering the step and
+ * the discrete events of it: leader gap and speed (or stop line), the
+ * ballistic branch, the clamp, the node outcome (crossed, held, arrived)
+ * and the statistics cell of the speed sample taken after it.  The tape
+ * holds n_steps x n_trips records of 40 bytes in device memory (reused by
+ * later calls); recording stops by itself after n_steps steps, or at
+ * manta_tape_stop.  The simulation itself is unchanged by recording.
+ *
+ * With every event held fixed, the run is a smooth map of the per-class
+ * IDM parameters theta = (v0f, T, a, b, s0) for each road class.
+ *
+ * manta_adjoint: reverse sweep over the recorded segment (all its steps
+ * must have been run), with the sim's own parameters.  All pointers are
+ * device pointers to binary64 arrays:
+ *   seed [n_stats_windows x n_edges]: dLoss/d(one speed sample) of each
+ *        statistics cell (window * n_edges + edge), e.g. dLoss/d(mean) / count;
+ *   lam_x, lam_v [n_trips]: in, the adjoint of every trip's position and
+ *        speed after the segment (zero after the last segment); out, the
+ *        adjoint of the state entering it;
+ *   grad [5 x n_classes]: dLoss/dtheta is added, index 5 * class + j with j
+ *        over (v0f, T, a, b, s0).
+ * Asynchronous on the sim's stream.
+ *
+ * manta_replay: forward replay of the recorded segment with the events held
+ * fixed and parameters theta (host, binary64, 5 x n_classes in the order
+ * above), for finite differences.  Device arrays: x, v [n_trips] binary64
+ * and present [n_trips] (0/1) carry every trip's state into and out of the
+ * segment (all zero before the first); sums [n_stats_windows x n_edges]
+ * binary64 accumulates the replayed speed of every sample.  Asynchronous on
+ * the sim's stream.
+ *
+ * Both return MANTA_E_STATE when no tape was recorded or its segment has
+ * not been run completely. */
+/* One record of the event tape (40 bytes): index (k - k0) * n_trips + trip
+ * for step k of the recorded segment [k0, k0 + n_steps).  flags: bit 0 on
+ * the network at the start of the step; bits 1-2 kind (0 free road, 1
+ * interacting with gap s and leader speed vL, 2 stopped in place); bit 3
+ * v + acc dt >= 0 (else the ballistic step stops the vehicle); bits 4-5
+ * clamp (0 none, 1 old position kept, 2 set to bnd); bits 6-8 outcome (0
+ * stayed on its edge, 1 crossed the node, 2 held at its old position, 3
+ * held at the stop line, 4 arrived); bits 12-15 road class.  sample is the
+ * statistics cell (window * n_edges + edge) of the speed sample taken after
+ * the step, or 0xFFFFFFFF. */
+typedef struct {
+  float x, v, s, vL, bnd, lim;
+  uint32_t cells, flags, sample, pad;
+} manta_tape_record;
+MANTA_API manta_status manta_tape_start(manta_sim *sim, int64_t n_steps);
+MANTA_API manta_status manta_tape_stop(manta_sim *sim);
+/* Copies the recorded segment (n_steps x n_trips records, synchronising the
+ * sim's stream) to host memory of capacity `cap` records; *n_out receives
+ * the number copied.  MANTA_E_INVALID if cap is too small. */
+MANTA_API manta_status manta_tape_copy(manta_sim *sim, manta_tape_record *out, int64_t cap, int64_t *n_out);
+MANTA_API manta_status manta_adjoint(manta_sim *sim, const double *seed, double *lam_x, double *lam_v, double *grad);
+MANTA_API manta_status manta_replay(manta_sim *sim, const double *theta, double *x, double *v, uint8_t *present,
+                                    double *sums);
+
 /* Bytes of the canonical lane map (sum over edges of cells x lanes). */
 MANTA_API int64_t manta_lane_map_bytes(const manta_sim *sim);
 

@@ -114,6 +114,13 @@ typedef struct {
   /* scratch */
   int32_t *lc_tgt;
   uint32_t *best;
+  /* optional event tape of steps [tp_k0, tp_k0 + tp_len), arrays [step][trip]
+   * owned by the caller: the state entering each step and the events of it
+   * (see oracle_set_tape) */
+  int64_t tp_k0, tp_len;
+  float *tp_x, *tp_v, *tp_s, *tp_vL, *tp_bnd, *tp_lim;
+  int32_t *tp_C, *tp_flags;
+  int64_t *tp_sample;
 } osim;
 
 /* ------------------------------------------------------------------------ */
@@ -565,6 +572,24 @@ static scan_t leader_scan(osim *S, int64_t id) {
 /* ------------------------------------------------------------------ step -- */
 typedef struct { int64_t id; float xn, vn; uint8_t dwn; int kind; int64_t tgt_lane; int32_t e2, l2; } upd_t;
 
+/* Event tape for the calibration adjoint (test infrastructure): for every
+ * trip and every step k in [k0, k0 + len), element (k - k0) * n_trips + id
+ * receives the state entering the step (x, v), the leader gap s and speed vL
+ * when the vehicle is interacting, the clamp bound, the edge's speed limit
+ * and cells, and flags = present | kind << 1 | ballistic << 3 | clamp << 4 |
+ * outcome << 6 | class << 9, with kind 0 free / 1 interacting / 2 stopped in
+ * place, ballistic 1 when v + acc dt >= 0, clamp 0 none / 1 old position
+ * kept / 2 bound, outcome 0 stayed / 1 crossed / 2 held at its old position
+ * / 3 held at the stop line / 4 arrived; sample = window * E + edge of the
+ * speed sample taken after the step, or -1.  Entries of trips not on the
+ * network stay as the caller initialised them (flags 0).  NULL x disables. */
+OR_API void oracle_set_tape(osim *S, int64_t k0, int64_t len, float *x, float *v, float *s, float *vL, float *bnd,
+                            float *lim, int32_t *C, int32_t *flags, int64_t *sample) {
+  S->tp_k0 = k0; S->tp_len = x ? len : 0;
+  S->tp_x = x; S->tp_v = v; S->tp_s = s; S->tp_vL = vL; S->tp_bnd = bnd; S->tp_lim = lim;
+  S->tp_C = C; S->tp_flags = flags; S->tp_sample = sample;
+}
+
 OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
   if (!S) return -1;
   if (!S->loaded) { set_err(err, errlen, "no trips loaded"); return -3; }
@@ -631,12 +656,14 @@ OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
           acc = a * ((1.0f - r4) - qq * qq);
         }
       }
+      int t_ball = 0, t_clamp = 0;   /* events of the step, for the tape */
+      float t_bnd = 0.0f;
       if (stop_in_place) { xn = x; vn = 0.0f; }
       else {
         /* "double integrating": ballistic update (position with the mean speed over dt) */
         const float vt = v + acc * dt;
         float xt, vv;
-        if (vt >= 0.0f) { xt = x + (v * dt + (0.5f * acc) * (dt * dt)); vv = vt; }
+        if (vt >= 0.0f) { xt = x + (v * dt + (0.5f * acc) * (dt * dt)); vv = vt; t_ball = 1; }
         else { xt = x - (v * v) / (2.0f * acc); vv = 0.0f; }
         int has_bound = 0; int64_t bnd = 0;
         if (sc.kind != SC_FREE) { has_bound = 1; bnd = sc.cL - L; }
@@ -644,7 +671,10 @@ OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
           int64_t cap = (int64_t)Ce + S->C[S->route[V->r + 1]] - 1;   /* at most one node per step */
           if (!has_bound || cap < bnd) { has_bound = 1; bnd = cap; }
         }
-        if (has_bound && xt > (float)bnd) { xn = fmaxf(x, (float)bnd); vn = 0.0f; S->st.clamps++; }
+        if (has_bound && xt > (float)bnd) {
+          xn = fmaxf(x, (float)bnd); vn = 0.0f; S->st.clamps++;
+          t_bnd = (float)bnd; t_clamp = x > t_bnd ? 1 : 2;
+        }
         else { xn = xt; vn = vv; }
       }
       /* stop-sign dwell: held at the stop line by the stop sign alone */
@@ -654,6 +684,16 @@ OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
         const int32_t zone = Ce - 1 - ((int32_t)ceilf(s0) + 2);
         if (!last && sc.reached_own && sc.stop_only && (int32_t)floorf(xn) >= zone && vn < cf->stop_v_eps)
           dwn = V->dwell < 255 ? (uint8_t)(V->dwell + 1) : 255;
+      }
+      if (S->tp_len > 0 && k >= S->tp_k0 && k < S->tp_k0 + S->tp_len) {
+        const size_t ti = (size_t)(k - S->tp_k0) * (size_t)S->NT + (size_t)id;
+        const int32_t kind = sc.kind == SC_FREE ? 0 : (stop_in_place ? 2 : 1);
+        S->tp_x[ti] = x; S->tp_v[ti] = v;
+        S->tp_s[ti] = sc.kind == SC_FREE ? 0.0f : (float)(sc.cL - cell - L);
+        S->tp_vL[ti] = sc.kind == SC_FREE ? 0.0f : sc.vL;
+        S->tp_bnd[ti] = t_bnd; S->tp_lim[ti] = S->lim[e]; S->tp_C[ti] = Ce;
+        S->tp_flags[ti] = 1 | (kind << 1) | (t_ball << 3) | (t_clamp << 4) | ((int32_t)S->cls[e] << 9);
+        S->tp_sample[ti] = -1;
       }
       upd_t *u = &U[q];
       u->id = id; u->xn = xn; u->vn = vn; u->dwn = dwn; u->kind = 0; u->tgt_lane = -1;
@@ -681,19 +721,26 @@ OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
       veh_t *V = &S->V[u->id];
       const int32_t cell = (int32_t)floorf(V->x);
       row(S, S->map_cur, V->e, V->l)[cell] = EMPTY;
+      const int taped = S->tp_len > 0 && k >= S->tp_k0 && k < S->tp_k0 + S->tp_len;
+      const size_t ti = taped ? (size_t)(k - S->tp_k0) * (size_t)S->NT + (size_t)u->id : 0;
+      int32_t outcome = 0;
       if (u->kind == 2) {
         S->exitc[V->e]++; S->st.arrived++; V->status = 2;
+        if (taped) S->tp_flags[ti] |= 4 << 6;
         continue;
       }
       if (u->kind == 1) {
         if (S->best[u->tgt_lane] == (uint32_t)u->id) {
+          outcome = 1;
           const int32_t n = S->dst[V->e];
           if (S->ntype[n] == NODE_STOP && S->permit[n] == (uint32_t)u->id) S->permit[n] = NONE_ID;
           S->exitc[V->e]++; S->entry[u->e2]++;
           V->x = u->xn - (float)S->C[V->e];
           V->e = u->e2; V->l = u->l2; V->r++; V->v = u->vn; V->dwell = 0;
         } else {
-          V->x = fmaxf(V->x, (float)(S->C[V->e] - 1)); V->v = 0.0f; V->dwell = u->dwn;
+          const float held = fmaxf(V->x, (float)(S->C[V->e] - 1));
+          outcome = held == V->x ? 2 : 3;
+          V->x = held; V->v = 0.0f; V->dwell = u->dwn;
         }
       } else {
         V->x = u->xn; V->v = u->vn; V->dwell = u->dwn;
@@ -702,6 +749,10 @@ OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
       if (in_window) {
         S->ssum[(size_t)w * S->E + V->e] += (uint64_t)(V->v * 1048576.0f);
         S->scnt[(size_t)w * S->E + V->e]++;
+      }
+      if (taped) {
+        S->tp_flags[ti] |= outcome << 6;
+        S->tp_sample[ti] = in_window ? (int64_t)w * S->E + V->e : -1;
       }
     }
     for (int32_t e = 0; e < S->E; ++e) {

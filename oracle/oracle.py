@@ -105,6 +105,7 @@ def _load():
         lib.oracle_check.restype = C.c_int
         lib.oracle_check.argtypes = [P, C.c_char_p, C.c_int]
         lib.oracle_destroy.argtypes = [P]
+        lib.oracle_set_tape.argtypes = [P, C.c_int64, C.c_int64] + [P] * 9
         lib.oracle_set_lane_closure.restype = C.c_int
         lib.oracle_set_lane_closure.argtypes = [P, C.c_int32, C.c_int32, C.c_int64, C.c_int64]
         lib.oracle_splitmix64.restype = C.c_uint64
@@ -224,6 +225,25 @@ class OracleSim:
         rc = self._lib.oracle_set_lane_closure(self._h, int(edge), int(lane), int(k0), int(k1))
         if rc != 0:
             raise OracleError(f"set_lane_closure {rc}")
+
+    def record_tape(self, n_steps):
+        """Record the event tape of the next n_steps steps (oracle_set_tape);
+        returns the dict of arrays, shape (n_steps, n_trips), filled as the
+        steps run."""
+        T, N = int(n_steps), max(self.n_trips, 1)
+        st = self.stats()["step"]
+        tape = {k: np.zeros((T, N), np.float32) for k in ("x", "v", "s", "vL", "bnd", "lim")}
+        tape["C"] = np.zeros((T, N), np.int32)
+        tape["flags"] = np.zeros((T, N), np.int32)
+        tape["sample"] = np.full((T, N), -1, np.int64)
+        tape["k0"] = st
+        self._tape = tape
+        self._lib.oracle_set_tape(self._h, st, T, *[_p(tape[k]) for k in
+                                                   ("x", "v", "s", "vL", "bnd", "lim", "C", "flags", "sample")])
+        return tape
+
+    def stop_tape(self):
+        self._lib.oracle_set_tape(self._h, 0, 0, *([None] * 9))
 
     def check(self):
         msg = C.create_string_buffer(256)

@@ -15,7 +15,9 @@
 
 #include "manta.h"
 #include "sim.cuh"
+#include <cstddef>
 #include "step_kernel.cuh"
+#include "adjoint.cuh"
 
 namespace {
 
@@ -71,6 +73,11 @@ struct manta_sim {
   std::vector<long long> clo_k0, clo_k1;
   int grid[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // co-resident grid size of every launch shape
   int variant = 0;                          // launch shape used by manta_step
+  // event tape (calibration): device records, capacity, recorded segment
+  TapeRec *tape = nullptr;
+  size_t tape_cap = 0;
+  int64_t tape_k0 = 0;
+  int32_t tape_len = 0;
 };
 
 // Launch shapes of the step kernel (threads per block, minimum blocks per
@@ -186,8 +193,9 @@ const char *manta_last_error(void) { return g_err.c_str(); }
 
 void manta_destroy(manta_sim *S) {
   if (!S) return;
-  if (S->stream || true) cudaStreamSynchronize(S->stream);
+  cudaStreamSynchronize(S->stream);
   for (void *p : S->allocs) cudaFree(p);
+  if (S->tape) cudaFree(S->tape);
   delete S;
 }
 
@@ -930,3 +938,182 @@ manta_status manta_run_noalloc(int32_t n_nodes, int32_t n_edges, const int32_t *
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- checkpoints
+namespace {
+// Every device array whose content carries over from one step to the next
+// (the rest is rewritten within each step before it is read, or is input).
+std::vector<std::pair<void *, size_t>> mutable_state(const manta_sim *S) {
+  const Params &P = S->P;
+  const size_t E = (size_t)S->E, N = (size_t)S->N, G = (size_t)std::max<uint32_t>(S->n_lanes, 1);
+  const size_t W = (size_t)S->cfg.n_stats_windows, NT = (size_t)std::max<int64_t>(S->n_trips, 1);
+  const size_t map = (size_t)S->atlas_bytes + kMapPad;
+  return {{P.atlas0, map}, {P.atlas1, map}, {P.permit, 4 * N}, {P.rr, 4 * N},
+          {P.req_key, 8 * G}, {P.req_tgt, 4 * G}, {P.slot_td, 4 * G}, {P.slot_id, 4 * G},
+          {P.entry, 4 * E}, {P.exitc, 4 * E}, {P.ssum, 8 * E * W}, {P.scnt, 4 * E * W},
+          {P.pending, 4 * E}, {P.q_pos, 4 * E}, {P.dep_key, 8 * E}, {P.dep0, 4 * E}, {P.dep1, 4 * E},
+          {P.ctl, sizeof(Ctl)}, {P.veh, sizeof(Veh) * NT}, {P.act0, 4 * NT}, {P.act1, 4 * NT},
+          {P.freel, 4 * NT}};
+}
+}  // namespace
+
+struct manta_checkpoint {
+  const manta_sim *sim;
+  int64_t k;
+  size_t bytes;
+  unsigned char *buf;
+};
+
+manta_status manta_checkpoint_save(manta_sim *S, manta_checkpoint **out) {
+  g_err.clear();
+  if (!out) return fail(MANTA_E_INVALID, "out is NULL");
+  *out = nullptr;
+  manta_status st = check_steppable(S);
+  if (st != MANTA_OK) return st;
+  const auto parts = mutable_state(S);
+  size_t total = 0;
+  for (const auto &q : parts) total += (q.second + 255u) & ~(size_t)255u;
+  unsigned char *buf = nullptr;
+  if (cudaMalloc(&buf, total) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MANTA_E_OOM, "checkpoint allocation failed");
+  }
+  size_t off = 0;
+  for (const auto &q : parts) {
+    if (cudaMemcpyAsync(buf + off, q.first, q.second, cudaMemcpyDeviceToDevice, S->stream) != cudaSuccess) {
+      cudaFree(buf);
+      return fail(MANTA_E_CUDA, "checkpoint copy failed");
+    }
+    off += (q.second + 255u) & ~(size_t)255u;
+  }
+  *out = new manta_checkpoint{S, S->k, total, buf};
+  return MANTA_OK;
+}
+
+manta_status manta_checkpoint_restore(manta_sim *S, const manta_checkpoint *c) {
+  g_err.clear();
+  manta_status st = check_steppable(S);
+  if (st != MANTA_OK) return st;
+  if (!c || c->sim != S) return fail(MANTA_E_INVALID, "checkpoint is NULL or belongs to another simulation");
+  const auto parts = mutable_state(S);
+  size_t off = 0;
+  for (const auto &q : parts) {
+    if (cudaMemcpyAsync(q.first, c->buf + off, q.second, cudaMemcpyDeviceToDevice, S->stream) != cudaSuccess)
+      return fail(MANTA_E_CUDA, "checkpoint copy failed");
+    off += (q.second + 255u) & ~(size_t)255u;
+  }
+  S->k = c->k;
+  return MANTA_OK;
+}
+
+int64_t manta_checkpoint_step(const manta_checkpoint *c) { return c ? c->k : -1; }
+int64_t manta_checkpoint_bytes(const manta_checkpoint *c) { return c ? (int64_t)c->bytes : 0; }
+
+void manta_checkpoint_destroy(manta_checkpoint *c) {
+  if (!c) return;
+  cudaFree(c->buf);
+  delete c;
+}
+
+// ---------------------------------------------------------------- event tape and adjoint
+manta_status manta_tape_start(manta_sim *S, int64_t n_steps) {
+  g_err.clear();
+  manta_status st = check_steppable(S);
+  if (st != MANTA_OK) return st;
+  if (n_steps < 1 || n_steps > (1 << 30)) return fail(MANTA_E_INVALID, "n_steps out of range");
+  const size_t need = (size_t)n_steps * (size_t)std::max<int64_t>(S->n_trips, 1);
+  if (need > S->tape_cap) {
+    cudaStreamSynchronize(S->stream);
+    if (S->tape) cudaFree(S->tape);
+    S->tape = nullptr;
+    S->tape_cap = 0;
+    if (cudaMalloc(&S->tape, need * sizeof(TapeRec)) != cudaSuccess) {
+      cudaGetLastError();
+      S->tape = nullptr;
+      return fail(MANTA_E_OOM, "tape allocation failed");
+    }
+    S->tape_cap = need;
+  }
+  if (cudaMemsetAsync(S->tape, 0, need * sizeof(TapeRec), S->stream) != cudaSuccess)
+    return fail(MANTA_E_CUDA, "tape reset failed");
+  S->tape_k0 = S->k;
+  S->tape_len = (int32_t)n_steps;
+  S->P.tape = S->tape;
+  S->P.tape_k0 = S->k;
+  S->P.tape_len = (int32_t)n_steps;
+  return MANTA_OK;
+}
+
+manta_status manta_tape_stop(manta_sim *S) {
+  g_err.clear();
+  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
+  S->P.tape = nullptr;
+  return MANTA_OK;
+}
+
+namespace {
+IdmTheta theta_of(const manta_config &c) {
+  IdmTheta t;
+  for (int i = 0; i < 8; ++i) {
+    t.v0f[i] = c.v0f[i]; t.T[i] = c.T[i]; t.a[i] = c.a[i]; t.b[i] = c.b[i]; t.s0[i] = c.s0[i];
+  }
+  return t;
+}
+manta_status check_tape(const manta_sim *S) {
+  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
+  if (!S->tape || S->tape_len < 1) return fail(MANTA_E_STATE, "no tape recorded");
+  if (S->k < S->tape_k0 + S->tape_len) return fail(MANTA_E_STATE, "the tape segment has not been fully stepped");
+  return MANTA_OK;
+}
+}  // namespace
+
+static_assert(sizeof(TapeRec) == sizeof(manta_tape_record), "tape record layout");
+static_assert(offsetof(TapeRec, C) == offsetof(manta_tape_record, cells), "tape record layout");
+static_assert(offsetof(TapeRec, sample) == offsetof(manta_tape_record, sample), "tape record layout");
+
+manta_status manta_tape_copy(manta_sim *S, manta_tape_record *out, int64_t cap, int64_t *n_out) {
+  g_err.clear();
+  if (!S || !out || !n_out) return fail(MANTA_E_INVALID, "NULL argument");
+  if (!S->tape || S->tape_len < 1) return fail(MANTA_E_STATE, "no tape recorded");
+  const int64_t n = (int64_t)S->tape_len * std::max<int64_t>(S->n_trips, 1);
+  if (cap < n) return fail(MANTA_E_INVALID, "capacity too small for the tape");
+  if (cudaStreamSynchronize(S->stream) != cudaSuccess ||
+      cudaMemcpy(out, S->tape, (size_t)n * sizeof(TapeRec), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(MANTA_E_CUDA, "tape copy failed");
+  *n_out = n;
+  return MANTA_OK;
+}
+
+manta_status manta_adjoint(manta_sim *S, const double *seed, double *lam_x, double *lam_v, double *grad) {
+  g_err.clear();
+  manta_status st = check_tape(S);
+  if (st != MANTA_OK) return st;
+  if (!seed || !lam_x || !lam_v || !grad) return fail(MANTA_E_INVALID, "NULL argument");
+  const uint32_t n = (uint32_t)std::max<int64_t>(S->n_trips, 1);
+  const int blocks = (int)std::min<uint32_t>((n + 255u) / 256u, 4096u);
+  adjoint_kernel<<<blocks, 256, 0, S->stream>>>(S->tape, S->tape_len, (uint32_t)S->n_trips, (double)S->cfg.dt,
+                                                theta_of(S->cfg), seed, lam_x, lam_v, grad);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
+  return MANTA_OK;
+}
+
+manta_status manta_replay(manta_sim *S, const double *theta, double *x, double *v, uint8_t *present, double *sums) {
+  g_err.clear();
+  manta_status st = check_tape(S);
+  if (st != MANTA_OK) return st;
+  if (!theta || !x || !v || !present || !sums) return fail(MANTA_E_INVALID, "NULL argument");
+  IdmTheta th;
+  memset(&th, 0, sizeof(th));
+  for (int c = 0; c < S->cfg.n_classes && c < 8; ++c) {
+    th.v0f[c] = theta[5 * c]; th.T[c] = theta[5 * c + 1]; th.a[c] = theta[5 * c + 2];
+    th.b[c] = theta[5 * c + 3]; th.s0[c] = theta[5 * c + 4];
+  }
+  const uint32_t n = (uint32_t)std::max<int64_t>(S->n_trips, 1);
+  const int blocks = (int)std::min<uint32_t>((n + 255u) / 256u, 4096u);
+  replay_kernel<<<blocks, 256, 0, S->stream>>>(S->tape, S->tape_len, (uint32_t)S->n_trips, (double)S->cfg.dt, th,
+                                               x, v, present, sums);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("replay launch: ") + cudaGetErrorString(e));
+  return MANTA_OK;
+}

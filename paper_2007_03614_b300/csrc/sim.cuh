@@ -61,6 +61,31 @@ struct __align__(16) Veh {
   EdgeMeta em;     // record of edge e
 };
 
+// One vehicle-step of the event tape (calibration, Eq. 1 adjoint): the
+// continuous state entering the step and the discrete events the adjoint
+// holds fixed.  Written in P3 (and completed in P4 for crossing requests) at
+// index (k - tape_k0) * n_trips + trip id; zero flags mean "not on the
+// network at the start of step k".
+struct TapeRec {
+  float x, v;        // position (cells from the start of the edge) and speed entering the step
+  float s, vL;       // gap to the leader or stop line (cells) and the leader's speed, when interacting
+  float bnd;         // clamp bound (cell), when clamped
+  float lim;         // speed limit of the edge (v0 = lim * v0f[class])
+  uint32_t C;        // cells of the edge
+  uint32_t flags;    // TF_* below
+  uint32_t sample;   // statistics index (window * E + edge) of the speed sample after the step, or none
+  uint32_t pad;
+};
+#define TF_PRESENT 0x1u
+#define TF_KIND_SHIFT 1          // 0 free road, 1 interacting (Eq. 1 with gap s), 2 stopped in place
+#define TF_BALLISTIC 0x8u        // v + acc dt >= 0 (else the vehicle stops within the step)
+#define TF_CLAMP_SHIFT 4         // 0 none, 1 held at its old position, 2 set to the bound
+#define TF_OUT_SHIFT 6           // 0 stays on its edge, 1 crossed, 2 held (old position kept),
+                                 // 3 held at the stop line, 4 arrived, 5 crossing request pending
+#define TF_CLASS_SHIFT 12
+enum { TK_FREE = 0, TK_INTERACT = 1, TK_STOP = 2 };
+enum { TO_STAY = 0, TO_CROSS = 1, TO_HELD_KEEP = 2, TO_HELD_LINE = 3, TO_ARRIVE = 4, TO_PENDING = 5 };
+
 struct Ctl {
   unsigned bar_count;
   unsigned bar_gen;
@@ -144,5 +169,9 @@ struct Params {
   int64_t k0;
   int32_t n_steps;
   int32_t k_from_ctl;          // take the first step index from ctl->k_next instead of k0
+  // event tape (none when tape == nullptr)
+  TapeRec *tape;
+  int64_t tape_k0;
+  int32_t tape_len;
   uint64_t wait_limit_ns;
 };

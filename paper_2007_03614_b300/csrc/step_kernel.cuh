@@ -894,10 +894,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         float xn, vn;
         bool stop_in_place = false;
         float acc = 0.0f;
+        float tsg = 0.0f, tbnd = 0.0f;
+        uint32_t tflags = 0;     // event-tape flags of this step
         if (sc.kind == SC_FREE) {
           acc = a * (1.0f - r4);
         } else {
           const float sg = __int2float_rn(sc.cL - cell - L);
+          tsg = sg;
           if (sg <= 0.0f) {
             stop_in_place = true;
           } else {
@@ -912,10 +915,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         }
         if (stop_in_place) {
           xn = x; vn = 0.0f;
+          tflags = (uint32_t)TK_STOP << TF_KIND_SHIFT;
         } else {
           const float dt = p.dt;
           const float vt = v + acc * dt;
           float xt, vv;
+          tflags = ((uint32_t)(sc.kind == SC_FREE ? TK_FREE : TK_INTERACT) << TF_KIND_SHIFT) |
+                   (vt >= 0.0f ? TF_BALLISTIC : 0u);
           if (vt >= 0.0f) { xt = x + (v * dt + (0.5f * acc) * (dt * dt)); vv = vt; }
           else { xt = x - (v * v) / (2.0f * acc); vv = 0.0f; }
           bool has_bound = sc.kind != SC_FREE;
@@ -928,8 +934,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
             const int cap = C + (int)cells_of(cnl2) - 1;
             if (!has_bound || cap < bnd) { has_bound = true; bnd = cap; }
           }
-          if (has_bound && xt > __int2float_rn(bnd)) { xn = fmaxf(x, __int2float_rn(bnd)); vn = 0.0f; c_clamp++; }
-          else { xn = xt; vn = vv; }
+          if (has_bound && xt > __int2float_rn(bnd)) {
+            xn = fmaxf(x, __int2float_rn(bnd)); vn = 0.0f; c_clamp++;
+            tbnd = __int2float_rn(bnd);
+            tflags |= (x > tbnd ? 1u : 2u) << TF_CLAMP_SHIFT;
+          } else { xn = xt; vn = vv; }
         }
         uint32_t dwn = 0;
         if (has_next && sc.reached_own && sc.stop_only) {
@@ -993,6 +1002,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           __syncwarp(am);
           if (rk == 0) s_rqn[wid] = nb + cnt;
           __syncwarp(am);
+        }
+        if (p.tape) {
+          const int64_t tk = k - p.tape_k0;
+          if (tk >= 0 && tk < p.tape_len) {
+            const uint32_t out = arrive ? TO_ARRIVE : (request ? TO_PENDING : TO_STAY);
+            TapeRec r;
+            r.x = x; r.v = v; r.s = tsg; r.vL = sc.vL; r.bnd = tbnd; r.lim = em.lim; r.C = (uint32_t)C;
+            r.flags = TF_PRESENT | tflags | (out << TF_OUT_SHIFT) | ((uint32_t)cls << TF_CLASS_SHIFT);
+            r.sample = (out == TO_STAY && win >= 0) ? (uint32_t)((size_t)win * p.E + w.e) : MANTA_NONE;
+            r.pad = 0u;
+            p.tape[(size_t)tk * p.n_trips + w.id] = r;
+          }
         }
       };
       int fqn = 0;                // finish-queue length (warp-uniform)
@@ -1149,6 +1170,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           w.ld = (w.ld & kLdEdgeBits) | (uint32_t)lane | (__ldcg(p.req_dw + i) << 8);
           nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xf)] = speed_code(vf);
           ef = w.e;
+        }
+        if (p.tape) {
+          const int64_t tk = k - p.tape_k0;
+          if (tk >= 0 && tk < p.tape_len) {
+            TapeRec *r = p.tape + (size_t)tk * p.n_trips + w.id;
+            // held: xf = max(old x, C - 1) keeps the old position or sets the stop line
+            const uint32_t out = win_it ? TO_CROSS : (w.x == xf ? TO_HELD_KEEP : TO_HELD_LINE);
+            r->flags = (r->flags & ~(7u << TF_OUT_SHIFT)) | (out << TF_OUT_SHIFT);
+            r->sample = win >= 0 ? (uint32_t)((size_t)win * p.E + ef) : MANTA_NONE;
+          }
         }
         w.x = xf; w.v = vf;
         store_veh(p, s, w);

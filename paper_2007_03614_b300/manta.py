@@ -50,7 +50,9 @@ EXPORTS = ("manta_default_config", "manta_create", "manta_load_trips", "manta_st
            "manta_destroy", "manta_last_error", "manta_selftest_barrier_timeout", "manta_run_noalloc",
            "manta_phase_times", "manta_set_lane_closure", "manta_variant_count", "manta_variant_info",
            "manta_set_variant", "manta_get_variant", "manta_autotune", "manta_graph_capture",
-           "manta_graph_launch", "manta_graph_destroy")
+           "manta_graph_launch", "manta_graph_destroy", "manta_checkpoint_save", "manta_checkpoint_restore",
+           "manta_checkpoint_step", "manta_checkpoint_bytes", "manta_checkpoint_destroy", "manta_tape_start",
+           "manta_tape_stop", "manta_tape_copy", "manta_adjoint", "manta_replay")
 
 _lib = None
 
@@ -113,6 +115,25 @@ def load_library():
         lib.manta_graph_launch.restype = C.c_int
         lib.manta_graph_launch.argtypes = [P]
         lib.manta_graph_destroy.argtypes = [P]
+        lib.manta_checkpoint_save.restype = C.c_int
+        lib.manta_checkpoint_save.argtypes = [P, C.POINTER(P)]
+        lib.manta_checkpoint_restore.restype = C.c_int
+        lib.manta_checkpoint_restore.argtypes = [P, P]
+        lib.manta_checkpoint_step.restype = C.c_int64
+        lib.manta_checkpoint_step.argtypes = [P]
+        lib.manta_checkpoint_bytes.restype = C.c_int64
+        lib.manta_checkpoint_bytes.argtypes = [P]
+        lib.manta_checkpoint_destroy.argtypes = [P]
+        lib.manta_tape_start.restype = C.c_int
+        lib.manta_tape_start.argtypes = [P, C.c_int64]
+        lib.manta_tape_stop.restype = C.c_int
+        lib.manta_tape_stop.argtypes = [P]
+        lib.manta_tape_copy.restype = C.c_int
+        lib.manta_tape_copy.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
+        lib.manta_adjoint.restype = C.c_int
+        lib.manta_adjoint.argtypes = [P, P, P, P, P]
+        lib.manta_replay.restype = C.c_int
+        lib.manta_replay.argtypes = [P, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -136,6 +157,11 @@ def default_config(**over) -> MantaConfig:
     return c
 
 
+def _torch():
+    import torch
+    return torch
+
+
 def _p(a):
     return None if a is None else a.ctypes.data
 
@@ -146,6 +172,12 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)     # torch.cuda.Stream
+
+
+# one record of the event tape (manta_tape_record in include/manta.h)
+TAPE_DTYPE = np.dtype([("x", np.float32), ("v", np.float32), ("s", np.float32), ("vL", np.float32),
+                       ("bnd", np.float32), ("lim", np.float32), ("cells", np.uint32), ("flags", np.uint32),
+                       ("sample", np.uint32), ("pad", np.uint32)])
 
 
 class Sim:
@@ -247,6 +279,44 @@ class Sim:
         _check(self._lib.manta_autotune(self._h, int(trial_steps), int(rounds), C.byref(ch), _p(ms)))
         return ch.value, ms
 
+    def checkpoint(self) -> "Checkpoint":
+        return Checkpoint(self)
+
+    def restore(self, ckpt: "Checkpoint"):
+        _check(self._lib.manta_checkpoint_restore(self._h, ckpt._h))
+
+    def tape_start(self, n_steps):
+        _check(self._lib.manta_tape_start(self._h, int(n_steps)))
+
+    def tape_stop(self):
+        _check(self._lib.manta_tape_stop(self._h))
+
+    def tape_copy(self, n_steps) -> dict:
+        """The recorded tape as arrays of shape (n_steps, n_trips)."""
+        N = max(self.n_trips, 1)
+        rec = np.zeros(int(n_steps) * N, dtype=TAPE_DTYPE)
+        n = C.c_int64()
+        _check(self._lib.manta_tape_copy(self._h, rec.ctypes.data, rec.size, C.byref(n)))
+        return {k: rec[k].reshape(int(n_steps), N) for k in TAPE_DTYPE.names}
+
+    def adjoint(self, seed, lam_x, lam_v, grad):
+        """Reverse sweep over the recorded tape segment; arguments are CUDA
+        float64 tensors (see manta_adjoint in include/manta.h)."""
+        for t in (seed, lam_x, lam_v, grad):
+            assert t.is_cuda and t.dtype == _torch().float64 and t.is_contiguous()
+        _check(self._lib.manta_adjoint(self._h, seed.data_ptr(), lam_x.data_ptr(), lam_v.data_ptr(),
+                                       grad.data_ptr()))
+
+    def replay(self, theta, x, v, present, sums):
+        """Frozen-event replay of the recorded segment with parameters theta
+        (5 x n_classes, host); x, v, sums CUDA float64, present CUDA uint8."""
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
+        for t in (x, v, sums):
+            assert t.is_cuda and t.dtype == _torch().float64 and t.is_contiguous()
+        assert present.is_cuda and present.dtype == _torch().uint8
+        _check(self._lib.manta_replay(self._h, th.ctypes.data, x.data_ptr(), v.data_ptr(), present.data_ptr(),
+                                      sums.data_ptr()))
+
     def graph(self, n_steps) -> "Graph":
         return Graph(self, n_steps)
 
@@ -287,6 +357,35 @@ class Graph:
     def close(self):
         if self._h:
             self._lib.manta_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Checkpoint:
+    """Saved device state of a Sim (include/manta.h); destroy before the Sim."""
+
+    def __init__(self, sim):
+        self._lib = sim._lib
+        h = C.c_void_p()
+        _check(self._lib.manta_checkpoint_save(sim._h, C.byref(h)))
+        self._h = h
+
+    @property
+    def step(self) -> int:
+        return int(self._lib.manta_checkpoint_step(self._h))
+
+    @property
+    def nbytes(self) -> int:
+        return int(self._lib.manta_checkpoint_bytes(self._h))
+
+    def close(self):
+        if self._h:
+            self._lib.manta_checkpoint_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -252,6 +252,21 @@ def tiny_trips(net: Network, n_trips=1000, seed=1) -> Trips:
                       t_hi_s=600.0, seed=seed, pool_per_zone=0)
 
 
+def calib_network(seed=3) -> Network:
+    """Calibration case: 20x20 grid, 100 m edges, three road classes (local
+    1 lane 40 km/h; arterial every 5th line, 2 lanes 70 km/h; freeway every
+    10th line, 4 lanes 105 km/h), fixed-time signals at arterial crossings."""
+    return lattice(20, 20, arterial_every=5, freeway_every=10, len_median_m=100.0, len_sigma=0.0,
+                   len_min_m=100.0, len_max_m=100.0, speed_mps=(11.111, 19.444, 29.167), lanes=(1, 2, 4),
+                   signals_at=1, seed=seed)
+
+
+def calib_trips(net: Network, n_trips=20_000, seed=3) -> Trips:
+    """Uniform-random OD node pairs, departures uniform over the first 20 min."""
+    return make_trips(net, n_trips, od_model="uniform", depart="uniform", t_lo_s=0.0,
+                      t_hi_s=1200.0, seed=seed, pool_per_zone=0)
+
+
 METRO_SIDE = 482
 
 
