@@ -451,6 +451,151 @@ def run_ensemble(args):
         "gpu_launches": args.steps * ((steps + 2047) // 2048)}))
 
 
+def run_calibrate(args):
+    """Calibration case: 20x20 grid (3 road classes), 20k trips over 20 min,
+    3,600 steps; loss = mean squared error of the 5-minute link speeds against
+    those of a hidden, seed-drawn parameter set.  Reports the time of one
+    gradient (forward run with a checkpoint every 120 steps, then the
+    checkpointed adjoint), the agreement of the adjoint with central finite
+    differences (h = 1e-3) of the frozen-event replay of the whole run, and a
+    few gradient steps from the default parameters."""
+    import torch
+
+    from paper_2007_03614_b300 import calibrate, manta, synth
+    from paper_2007_03614_b300.build import build
+    rank, world = _dist()
+    if rank != 0:
+        return
+    build()
+    manta.load_library()
+    torch.cuda.set_device(0)
+    net = synth.calib_network()
+    tr = synth.calib_trips(net)
+    steps, K = 3600, 120
+    run = calibrate.LinkSpeedRun(net, tr, n_steps=steps, window_steps=600, checkpoint_every=K)
+    rng = np.random.default_rng(2024)
+    hidden = np.stack([rng.uniform(0.9, 1.1, 3), rng.uniform(1.0, 2.0, 3), rng.uniform(1.0, 2.5, 3),
+                       rng.uniform(1.5, 3.5, 3), rng.uniform(1.5, 3.0, 3)], axis=1)
+    with torch.no_grad():
+        target = calibrate.link_speeds(torch.as_tensor(hidden), run).clone()
+    obs = run.cnt > 0
+    cfg = manta.default_config()
+    theta0 = np.array([[cfg.v0f[c], cfg.T[c], cfg.a[c], cfg.b[c], cfg.s0[c]] for c in range(3)], np.float64)
+
+    def loss_of(th):
+        m = calibrate.link_speeds(th, run)
+        return ((m - target)[obs] ** 2).mean()
+
+    # timing of one gradient
+    fw, bw = [], []
+    for it in range(max(1, args.warmup) + max(1, args.steps)):
+        th = torch.as_tensor(theta0).clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L = loss_of(th)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        upd = run.sim.stats()["vehicle_updates"]     # before the backward pass rewinds the run
+        torch.cuda.synchronize()
+        t1b = time.perf_counter()
+        L.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if it >= max(1, args.warmup):
+            fw.append(t1 - t0)
+            bw.append(t2 - t1b)
+    grad_ckpt = th.grad.detach().numpy().copy()
+    with torch.no_grad():
+        m_run = calibrate.link_speeds(torch.as_tensor(theta0), run).reshape(-1).clone()
+    # finite differences of the frozen-event replay over the whole run
+    dev = torch.device("cuda")
+    g = manta.Sim(net, stream=run.stream, stats_window_steps=600, n_stats_windows=6)
+    g.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+    g.tape_start(steps)
+    g.step(steps)
+    E, N = net.n_edges, tr.n_trips
+    cnt = run.cnt.reshape(-1)
+    obs_f = obs.reshape(-1)
+    tgt = target.reshape(-1)
+
+    def replay_loss(th):
+        x = torch.zeros(N, dtype=torch.float64, device=dev)
+        v = torch.zeros(N, dtype=torch.float64, device=dev)
+        pr = torch.zeros(N, dtype=torch.uint8, device=dev)
+        sums = torch.zeros(6 * E, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        g.replay(th, x, v, pr, sums)
+        torch.cuda.synchronize()
+        m = torch.where(obs_f, sums / cnt.clamp(min=1.0), torch.zeros_like(sums))
+        return m, float(((m - tgt)[obs_f] ** 2).mean())
+
+    m0, _ = replay_loss(theta0)
+    seed = torch.where(obs_f, 2.0 * (m0 - tgt) / (obs_f.sum() * cnt.clamp(min=1.0)), torch.zeros_like(m0))
+    lx = torch.zeros(N, dtype=torch.float64, device=dev)
+    lv = torch.zeros(N, dtype=torch.float64, device=dev)
+    gr = torch.zeros(40, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    ta = time.perf_counter()
+    g.adjoint(seed.contiguous(), lx, lv, gr)
+    torch.cuda.synchronize()
+    adjoint_ms = 1000.0 * (time.perf_counter() - ta)
+    adj = gr[:15].cpu().numpy().reshape(3, 5)
+    # the same reverse sweep seeded from the run's own (fixed-point) means, as the
+    # checkpointed backward pass is: the two must agree to rounding
+    seed_run = torch.where(obs_f, 2.0 * (m_run - tgt) / (obs_f.sum() * cnt.clamp(min=1.0)), torch.zeros_like(m_run))
+    lx.zero_(); lv.zero_()
+    gr2 = torch.zeros(40, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    g.adjoint(seed_run.contiguous(), lx, lv, gr2)
+    torch.cuda.synchronize()
+    adj_run = gr2[:15].cpu().numpy().reshape(3, 5)
+    fd = np.zeros((3, 5))
+    h = 1e-3
+    for c in range(3):
+        for j in range(5):
+            tp, tm = theta0.copy(), theta0.copy()
+            tp[c, j] += h
+            tm[c, j] -= h
+            fd[c, j] = (replay_loss(tp)[1] - replay_loss(tm)[1]) / (2 * h)
+    scale = float(np.max(np.abs(adj)))
+    rel = np.abs(fd - adj) / np.maximum(np.abs(fd), 1e-3 * scale)
+    g.close()
+    # a few gradient steps (Adam) from the default parameters
+    th = torch.as_tensor(theta0).clone().requires_grad_(True)
+    opt = torch.optim.Adam([th], lr=0.02)
+    losses = []
+    for _ in range(args.calib_iters):
+        opt.zero_grad()
+        L = loss_of(th)
+        losses.append(float(L.detach()))
+        L.backward()
+        opt.step()
+        with torch.no_grad():
+            th[:, 0].clamp_(0.5, 1.5)
+            th[:, 1].clamp_(0.1, 2.0)      # bounds of Section III-A
+            th[:, 2].clamp_(1.0, 10.0)
+            th[:, 3].clamp_(1.0, 10.0)
+            th[:, 4].clamp_(1.0, 5.0)
+    run.close()
+    t_grad = float(np.mean(fw) + np.mean(bw))
+    print(json.dumps({
+        "metric": "calibration gradients/s (20x20 grid, 3 road classes, 20k trips, 3,600 steps, "
+                  "checkpoint every 120 steps)",
+        "value": 1.0 / t_grad, "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_grad, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 simulation, f64 adjoint", "data": "synthetic",
+        "config": {"workload": "calibrate", "edges": int(E), "trips": int(N), "sim_steps": steps,
+                   "checkpoint_every": K, "windows": 6, "params": list(calibrate.PARAMS)},
+        "forward_s": float(np.mean(fw)), "backward_s": float(np.mean(bw)), "vehicle_updates": int(upd),
+        "adjoint_kernel_ms_full_tape": adjoint_ms,
+        "fd_check": {"h": h, "max_rel_err": float(np.max(rel)), "adjoint": adj.tolist(), "fd": fd.tolist()},
+        "checkpointed_vs_full_tape_max_rel": float(np.max(np.abs(grad_ckpt - adj_run) /
+                                                          np.maximum(np.abs(adj_run), 1e-3 * scale))),
+        "descent": {"optimizer": "Adam lr 0.02", "loss": losses, "hidden": hidden.tolist(),
+                    "theta_final": th.detach().numpy().tolist()},
+        "gpu_launches": None}))
+
+
 def run_reference(args):
     rank, world = _dist()
     if rank != 0:
@@ -493,8 +638,9 @@ def main():
     ap.add_argument("--ref-chunk", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="metro", choices=["metro", "ensemble"])
+    ap.add_argument("--workload", default="metro", choices=["metro", "ensemble", "calibrate"])
     ap.add_argument("--scenarios", type=int, default=64)
+    ap.add_argument("--calib-iters", type=int, default=6, help="gradient steps of --workload calibrate")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: 07:30-08:00 trips, 1200-step warm-up launch, then --steps launches")
     ap.add_argument("--profile-peak", action="store_true",
@@ -507,6 +653,8 @@ def main():
         run_reference(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "calibrate":
+        run_calibrate(args)
     else:
         run_gpu(args)
 
