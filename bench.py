@@ -560,22 +560,38 @@ def run_calibrate(args):
     scale = float(np.max(np.abs(adj)))
     rel = np.abs(fd - adj) / np.maximum(np.abs(fd), 1e-3 * scale)
     g.close()
-    # a few gradient steps (Adam) from the default parameters
-    th = torch.as_tensor(theta0).clone().requires_grad_(True)
-    opt = torch.optim.Adam([th], lr=0.02)
-    losses = []
+    # gradient steps from the default parameters with a backtracking line
+    # search on the simulated (not frozen) loss: a step is taken only if it
+    # lowers the loss, else the step length halves (the frozen-event gradient
+    # is exact locally, but a step can move events)
+    lo = np.array([0.5, 0.1, 1.0, 1.0, 1.0])
+    hi = np.array([1.5, 2.0, 10.0, 10.0, 5.0])     # v0f, then the bounds of Section III-A
+    th_np = theta0.copy()
+    losses, accepted = [], []
+    step = 0.2
     for _ in range(args.calib_iters):
-        opt.zero_grad()
+        th = torch.as_tensor(th_np).clone().requires_grad_(True)
         L = loss_of(th)
-        losses.append(float(L.detach()))
         L.backward()
-        opt.step()
-        with torch.no_grad():
-            th[:, 0].clamp_(0.5, 1.5)
-            th[:, 1].clamp_(0.1, 2.0)      # bounds of Section III-A
-            th[:, 2].clamp_(1.0, 10.0)
-            th[:, 3].clamp_(1.0, 10.0)
-            th[:, 4].clamp_(1.0, 5.0)
+        Lv = float(L.detach())
+        losses.append(Lv)
+        d = -th.grad.numpy()
+        d = d / max(np.max(np.abs(d)), 1e-30)
+        took = None
+        for _ in range(5):
+            cand = np.clip(th_np + step * d, lo, hi)
+            with torch.no_grad():
+                Lc = float(loss_of(torch.as_tensor(cand)))
+            if Lc < Lv:
+                took = step
+                th_np = cand
+                break
+            step *= 0.5
+        accepted.append(took)
+        if took is None:
+            break
+    with torch.no_grad():
+        losses.append(float(loss_of(torch.as_tensor(th_np))))
     run.close()
     t_grad = float(np.mean(fw) + np.mean(bw))
     print(json.dumps({
@@ -591,9 +607,134 @@ def run_calibrate(args):
         "fd_check": {"h": h, "max_rel_err": float(np.max(rel)), "adjoint": adj.tolist(), "fd": fd.tolist()},
         "checkpointed_vs_full_tape_max_rel": float(np.max(np.abs(grad_ckpt - adj_run) /
                                                           np.maximum(np.abs(adj_run), 1e-3 * scale))),
-        "descent": {"optimizer": "Adam lr 0.02", "loss": losses, "hidden": hidden.tolist(),
-                    "theta_final": th.detach().numpy().tolist()},
+        "descent": {"method": "normalised gradient steps, backtracking on the simulated loss",
+                    "loss": losses, "accepted_step": accepted, "hidden": hidden.tolist(),
+                    "theta_final": th_np.tolist()},
         "gpu_launches": None}))
+
+
+def hourly_speeds(sim, n_windows, mps_to_mph=2.2369362920544):
+    """Per statistics window: mean over edges of each edge's mean speed, and
+    the sample-weighted mean speed, in mph."""
+    out = []
+    for w in range(n_windows):
+        ec = sim.edge_counters(w)
+        s = ec["speed_sum"].astype(np.float64) / 1048576.0
+        c = ec["speed_cnt"].astype(np.float64)
+        m = c > 0
+        out.append({"edge_mean_mph": float(np.mean(s[m] / c[m]) * mps_to_mph) if m.any() else None,
+                    "sample_mean_mph": float(s.sum() / max(c.sum(), 1.0) * mps_to_mph),
+                    "edges_observed": int(m.sum()), "samples": int(c.sum())})
+    return out
+
+
+def run_redgreen(args):
+    """Section IV-C experiment on the metro-shaped workload: every node a
+    flashing red (stop: 2 s stop, then one vehicle at a time in round robin)
+    against every node green, same trips and routes, 05:00-12:00.  Reports
+    hourly link speeds of both and the trend (red slower than green in the
+    05:00-06:00 and 08:00-09:00 slices; both slower at the peak)."""
+    import dataclasses
+
+    import torch
+
+    from paper_2007_03614_b300 import manta
+    from paper_2007_03614_b300.build import build
+    rank, world = _dist()
+    if rank != 0:
+        return
+    build()
+    manta.load_library()
+    torch.cuda.set_device(0)
+    net, tr = workload()
+    stream = torch.cuda.Stream()
+    res = {}
+    for name, ntype in (("green", 0), ("red", 1)):
+        n2 = dataclasses.replace(net, node_type=np.full_like(net.node_type, ntype))
+        sim = manta.Sim(n2, stream=stream, t0_step=T0_STEP, stats_window_steps=7200, n_stats_windows=7)
+        sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sim.step(50400)
+        ev1.record(stream)
+        ev1.synchronize()
+        st = sim.stats()
+        res[name] = {"wall_s": ev0.elapsed_time(ev1) / 1000.0, "stats": st, "hourly": hourly_speeds(sim, 7)}
+        sim.close()
+    g, r = res["green"]["hourly"], res["red"]["hourly"]
+    trend = {
+        "red_slower_05_06": r[0]["edge_mean_mph"] < g[0]["edge_mean_mph"],
+        "red_slower_08_09": r[3]["edge_mean_mph"] < g[3]["edge_mean_mph"],
+        "green_drop_05_06_to_08_09_mph": g[0]["edge_mean_mph"] - g[3]["edge_mean_mph"],
+        "red_drop_05_06_to_08_09_mph": r[0]["edge_mean_mph"] - r[3]["edge_mean_mph"],
+    }
+    print(json.dumps({
+        "metric": "Section IV-C red-light / green-light link speeds (metro-shaped morning)",
+        "value": r[3]["edge_mean_mph"], "unit": "mph (red, 08:00-09:00, mean of edge means)", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "redgreen", "hours": ["05-06", "06-07", "07-08", "08-09", "09-10", "10-11", "11-12"]},
+        "green": res["green"], "red": res["red"], "trend": trend,
+        "paper_mph": {"green": {"05-06": 24.5, "08-09": 17.8}, "red": {"05-06": 17.5, "08-09": 12.9}}}))
+
+
+def run_search(args):
+    """The paper's calibration loop (Section III-A) on the calibration case
+    (20x20 grid, 20k trips, 3,600 steps): 5 parameter sets {a, b, T, s0} per
+    iteration run batched as 5 copies of the network in one simulation,
+    against link speeds of a hidden parameter set; also times the same 5 sets
+    run one after another."""
+    import torch
+
+    from paper_2007_03614_b300 import calibrate, manta, synth
+    from paper_2007_03614_b300.build import build
+    rank, world = _dist()
+    if rank != 0:
+        return
+    build()
+    manta.load_library()
+    torch.cuda.set_device(0)
+    net = synth.calib_network()
+    tr = synth.calib_trips(net)
+    steps, W = 3600, 6
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(2025)
+    hidden = {"a": float(rng.uniform(1.0, 2.5)), "b": float(rng.uniform(1.5, 3.5)),
+              "T": float(rng.uniform(1.0, 2.0)), "s0": float(rng.uniform(1.5, 3.0))}
+    one = calibrate.copies(net, tr, 1)
+
+    def single(th):
+        g = manta.Sim(one.net, stream=stream, stats_window_steps=600, n_stats_windows=W, n_classes=1, v0f=[1.0],
+                      a=[th["a"]], b=[th["b"]], T=[th["T"]], s0=[th["s0"]])
+        g.load_trips(one.trips.route_off, one.trips.route_edges, one.trips.depart_time_s)
+        g.step(steps)
+        out = calibrate.link_speed_cells(g, W, 0, int(net.n_edges))
+        g.close()
+        return out
+
+    target, tcnt = single(hidden)
+    cfg = manta.default_config()
+    theta0 = {"a": cfg.a[0], "b": cfg.b[0], "T": cfg.T[0], "s0": cfg.s0[0]}
+    t0 = time.perf_counter()
+    res = calibrate.perturbation_search(net, tr, target, tcnt, theta0, iters=args.calib_iters, sets=5,
+                                        n_steps=steps, window_steps=600, seed=1, stream=stream)
+    t_batched = (time.perf_counter() - t0) / len(res["history"])
+    # the same five sets of the first iteration, one simulation each
+    t1 = time.perf_counter()
+    for c in range(5):
+        single({k: v for k, v in theta0.items()})
+    t_seq = time.perf_counter() - t1
+    mph = 2.2369362920544
+    print(json.dumps({
+        "metric": "calibration iterations/s (Section III-A loop: 5 parameter sets per iteration, batched)",
+        "value": 1.0 / t_batched, "unit": "iterations/s", "n_gpus": 1, "steps": len(res["history"]),
+        "warmup": 0, "ms_per_step": 1000.0 * t_batched, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "search", "edges": int(net.n_edges), "trips": int(tr.n_trips), "sim_steps": steps,
+                   "sets": 5, "windows": W},
+        "seconds_per_iteration": {"batched_5_copies": t_batched, "sequential_5_runs": t_seq},
+        "hidden": hidden, "start": theta0,
+        "objective_mph": [h["objective"] * mph for h in res["history"]],
+        "history": res["history"], "gpu_launches": None}))
 
 
 def run_reference(args):
@@ -638,7 +779,8 @@ def main():
     ap.add_argument("--ref-chunk", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="metro", choices=["metro", "ensemble", "calibrate"])
+    ap.add_argument("--workload", default="metro",
+                    choices=["metro", "ensemble", "calibrate", "redgreen", "search"])
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--calib-iters", type=int, default=6, help="gradient steps of --workload calibrate")
     ap.add_argument("--profile-case", action="store_true",
@@ -655,6 +797,10 @@ def main():
         run_ensemble(args)
     elif args.workload == "calibrate":
         run_calibrate(args)
+    elif args.workload == "redgreen":
+        run_redgreen(args)
+    elif args.workload == "search":
+        run_search(args)
     else:
         run_gpu(args)
 

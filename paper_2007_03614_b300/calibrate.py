@@ -152,3 +152,94 @@ def link_speeds(theta, run: LinkSpeedRun):
     if _LinkSpeeds is None:
         _LinkSpeeds = _function()
     return _LinkSpeeds.apply(theta, run)
+
+
+# ------------------------------------------------------------------ random search
+SEARCH_PARAMS = ("a", "b", "T", "s0")
+# Section III-A: a, b in [1, 10] m/s^2, T in [0.1, 2] s, s0 in [1, 5] m
+SEARCH_BOUNDS = {"a": (1.0, 10.0), "b": (1.0, 10.0), "T": (0.1, 2.0), "s0": (1.0, 5.0)}
+
+
+def copies(net, trips, n):
+    """Disjoint union of n copies of (net, trips) in which every edge of copy
+    i carries road class i, so that copy i runs with the IDM parameters of
+    class i.  Returns (Ensemble, edge offsets)."""
+    from . import synth
+    ens = synth.union([(net, trips)] * n)
+    cls = np.zeros(ens.net.n_edges, np.uint8)
+    for i in range(n):
+        cls[ens.edge_off[i]:ens.edge_off[i + 1]] = i
+    ens.net.edge_class = cls
+    return ens
+
+
+def link_speed_cells(sim, n_windows, edge_lo, edge_hi):
+    """Mean speed and sample count of every (window, edge) cell of edges
+    [edge_lo, edge_hi), as (n_windows, edges) arrays."""
+    m = np.zeros((n_windows, edge_hi - edge_lo))
+    c = np.zeros_like(m)
+    for w in range(n_windows):
+        ec = sim.edge_counters(w)
+        s = ec["speed_sum"][edge_lo:edge_hi].astype(np.float64) / 1048576.0
+        c[w] = ec["speed_cnt"][edge_lo:edge_hi]
+        m[w] = np.where(c[w] > 0, s / np.maximum(c[w], 1.0), 0.0)
+    return m, c
+
+
+def perturbation_search(net, trips, target, target_cnt, theta0, *, iters=5, sets=5, r0=1.0, decay=0.1,
+                        n_steps, t0_step=0, window_steps=600, n_windows=None, tol_mps=0.05 / 2.2369362920544,
+                        seed=0, stream=None, **cfg):
+    """The paper's calibration loop (Section III-A, Eq. 5).
+
+    Every iteration runs `sets` parameter sets {a, b, T, s0} (one set for all
+    vehicles): the current nominal and sets - 1 perturbations of it, each
+    parameter moved by U[-r, r] and clipped to the bounds of Section III-A,
+    with r = r0 at the first iteration and 10x smaller at each next one.  The
+    sets run together as one simulation of the disjoint union of `sets` copies
+    of the network and trips (copy i with the parameters of set i; the
+    nominal runs in copy 0, whose trip ids, and so random draws, are those of
+    a single run).  The objective of a set is the mean absolute difference
+    between its link speeds and `target` over the (window, edge) cells observed
+    in both (Eq. 5, the L1 norm over matched edges).  The best set becomes the
+    next nominal; the loop stops early once the objective is below tol_mps
+    (0.05 mph).
+
+    theta0: dict of the four starting values.  target, target_cnt: (windows,
+    edges) arrays of mean speeds (m/s) and sample counts.  Returns a dict with
+    the nominal and objective after each iteration."""
+    import torch
+    rng = np.random.default_rng(seed)
+    n_windows = int(n_windows if n_windows is not None else -(-int(n_steps) // int(window_steps)))
+    stream = stream if stream is not None else torch.cuda.Stream()
+    ens = copies(net, trips, sets)
+    E = int(net.n_edges)
+    nominal = {k: float(theta0[k]) for k in SEARCH_PARAMS}
+    history = []
+    r = float(r0)
+    for it in range(iters):
+        cand = [dict(nominal)]
+        for _ in range(sets - 1):
+            th = {}
+            for k in SEARCH_PARAMS:
+                lo, hi = SEARCH_BOUNDS[k]
+                th[k] = float(np.clip(nominal[k] + rng.uniform(-r, r), lo, hi))
+            cand.append(th)
+        per = {k: [c[k] for c in cand] for k in SEARCH_PARAMS}
+        sim = manta.Sim(ens.net, stream=stream, t0_step=t0_step, stats_window_steps=window_steps,
+                        n_stats_windows=n_windows, n_classes=sets, v0f=[1.0] * sets, **per, **cfg)
+        sim.load_trips(ens.trips.route_off, ens.trips.route_edges, ens.trips.depart_time_s)
+        sim.step(int(n_steps))
+        obj = []
+        for i in range(sets):
+            m, c = link_speed_cells(sim, n_windows, int(ens.edge_off[i]), int(ens.edge_off[i]) + E)
+            both = (c > 0) & (target_cnt > 0)
+            obj.append(float(np.mean(np.abs(m[both] - target[both]))) if both.any() else float("inf"))
+        sim.close()
+        best = int(np.argmin(obj))
+        nominal = cand[best]
+        history.append({"iteration": it, "range": r, "objective": obj[best], "objectives": obj,
+                        "nominal": dict(nominal)})
+        if obj[best] < tol_mps:
+            break
+        r *= decay
+    return {"nominal": nominal, "history": history}

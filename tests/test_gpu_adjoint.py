@@ -252,3 +252,28 @@ def test_autograd_gives_a_descent_direction():
             better.append(float(loss_of(theta.detach() + eps * d)) < float(L0))
     assert any(better), (float(L0), better)
     run.close()
+
+
+def test_perturbation_search_reduces_the_objective():
+    """The paper's calibration loop (Section III-A): 5 parameter sets per
+    iteration, run batched as copies of the network; the objective (Eq. 5,
+    mean absolute link-speed difference) ends below where it started."""
+    import torch
+    net = synth.calib_network()
+    tr = synth.calib_trips(net, n_trips=3000)
+    hidden = {"a": 2.2, "b": 3.0, "T": 1.1, "s0": 2.6}
+    one = calibrate.copies(net, tr, 1)
+    g = manta.Sim(one.net, stream=torch.cuda.Stream(), stats_window_steps=600, n_stats_windows=2, n_classes=1,
+                  v0f=[1.0], a=[hidden["a"]], b=[hidden["b"]], T=[hidden["T"]], s0=[hidden["s0"]])
+    g.load_trips(one.trips.route_off, one.trips.route_edges, one.trips.depart_time_s)
+    g.step(1200)
+    target, tcnt = calibrate.link_speed_cells(g, 2, 0, int(net.n_edges))
+    g.close()
+    cfg = manta.default_config()
+    theta0 = {"a": cfg.a[0], "b": cfg.b[0], "T": cfg.T[0], "s0": cfg.s0[0]}
+    out = calibrate.perturbation_search(net, tr, target, tcnt, theta0, iters=4, sets=5, n_steps=1200,
+                                        window_steps=600, seed=5)
+    h = out["history"]
+    start = h[0]["objectives"][0]           # the starting set, run in copy 0
+    assert h[-1]["objective"] < start, [x["objective"] for x in h]
+    assert all(x["range"] == pytest.approx(0.1 ** i) for i, x in enumerate(h))

@@ -151,3 +151,28 @@ def test_shape_and_graph_argument_errors(tiny):
     with pytest.raises(manta.MantaError):
         g.autotune(trial_steps=0)
     g.close()
+
+
+def test_red_light_is_slower_than_green_light():
+    """Section IV-C trend on a small grid: every node a flashing red (2 s stop,
+    one vehicle at a time) against every node green, same trips and routes:
+    red is slower, in the first and in the busiest statistics window."""
+    import dataclasses
+    net = synth.calib_network()
+    tr = synth.calib_trips(net, n_trips=4000)
+    speeds = {}
+    for name, t in (("green", 0), ("red", 1)):
+        n2 = dataclasses.replace(net, node_type=np.full_like(net.node_type, t))
+        g = manta.Sim(n2, stats_window_steps=600, n_stats_windows=4)
+        nets.load(g, tr)
+        g.step(2400)
+        w = []
+        for k in range(4):
+            ec = g.edge_counters(k)
+            c = ec["speed_cnt"].astype(np.float64)
+            w.append((ec["speed_sum"].astype(np.float64).sum() / 1048576.0 / max(c.sum(), 1.0), c.sum()))
+        speeds[name] = w
+        g.close()
+    busiest = int(np.argmax([c for _, c in speeds["green"]]))
+    assert speeds["red"][0][0] < speeds["green"][0][0]
+    assert speeds["red"][busiest][0] < speeds["green"][busiest][0]
