@@ -737,6 +737,67 @@ def run_search(args):
         "history": res["history"], "gpu_launches": None}))
 
 
+def run_stress(args):
+    """Stress configuration: the metro generator on ~3x the area (~1.6M
+    edges), 10M trips departing 04:00-13:00 (bimodal), lane 0 closed on 200
+    random freeway edges 07:30-09:00; the whole 9 h (64,800 steps) timed in
+    launches of 1800 steps."""
+    import torch
+
+    from paper_2007_03614_b300 import manta, synth
+    from paper_2007_03614_b300.build import build
+    rank, world = _dist()
+    if rank != 0:
+        return
+    build()
+    manta.load_library()
+    torch.cuda.set_device(0)
+    tg = time.perf_counter()
+    net = synth.stress_network()
+    tr = synth.stress_trips(net)
+    gen_s = time.perf_counter() - tg
+    clo = synth.incident_closures(net)
+    stream = torch.cuda.Stream()
+    t0 = int(4 * 3600 / 0.5)
+    steps = 64800
+    sim = manta.Sim(net, stream=stream, t0_step=t0, stats_window_steps=7200, n_stats_windows=9)
+    for (e, l, k0, k1) in clo:
+        sim.set_lane_closure(e, l, k0, k1)
+    sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    times = []
+    with Clocks(0) as clk:
+        for i in range(steps // args.chunk):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            sim.step(args.chunk)
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1) / 1000.0)
+    d = sim.stats()
+    el = float(sum(times))
+    peak, peak_kind = _peaks()
+    ab = algorithmic_bytes(d)
+    hourly = hourly_speeds(sim, 9)
+    sim.close()
+    print(json.dumps({
+        "metric": "vehicle-updates/s & wall-time of the 10M-trip megaregion day at dt=0.5 s; % HBM peak",
+        "value": d["vehicle_updates"] / el, "unit": "vehicle-updates/s", "n_gpus": 1, "steps": len(times),
+        "warmup": 0, "ms_per_step": 1000.0 * el / len(times), "higher_is_better": True, "data": "synthetic",
+        "dtype": "f32",
+        "config": {"workload": "stress: ~3x metro extent, 10M trips 04:00-13:00 bimodal, 200 freeway lane "
+                               "closures 07:30-09:00", "edges": int(net.n_edges), "nodes": int(net.n_nodes),
+                   "trips": int(tr.n_trips), "route_entries": int(tr.route_edges.size), "sim_steps": steps,
+                   "t0_step": t0, "l2": "flushed between launches (256 MB write)"},
+        "wall_s": el, "generation_s": gen_s, "counters": d,
+        "roofline": {"bound": "hbm", "achieved": ab / el / 1e9, "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": ab / el / 1e9 / peak, "algorithmic_bytes": int(ab)},
+        "hourly": hourly, "clocks": clk.summary(), "gpu_launches": len(times)}))
+
+
 def run_reference(args):
     rank, world = _dist()
     if rank != 0:
@@ -780,7 +841,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="metro",
-                    choices=["metro", "ensemble", "calibrate", "redgreen", "search"])
+                    choices=["metro", "ensemble", "calibrate", "redgreen", "search", "stress"])
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--calib-iters", type=int, default=6, help="gradient steps of --workload calibrate")
     ap.add_argument("--profile-case", action="store_true",
@@ -801,6 +862,8 @@ def main():
         run_redgreen(args)
     elif args.workload == "search":
         run_search(args)
+    elif args.workload == "stress":
+        run_stress(args)
     else:
         run_gpu(args)
 

@@ -300,6 +300,35 @@ def metro_trips(net: Network, n_trips=3_200_000, seed=2, t_lo_s=5 * 3600.0, t_hi
                       mean_s=8 * 3600.0, sd_s=75 * 60.0, seed=seed, n_threads=n_threads)
 
 
+STRESS_SIDE = 822
+
+
+def stress_network(seed=4, side=STRESS_SIDE) -> Network:
+    """Megaregion-shaped synthetic network: the metro generator on a lattice
+    about 3x the area (822 x 822 nodes, about 1.6M directed edges)."""
+    return lattice(side, side, arterial_every=8, freeway_every=32, local_keep=0.57,
+                   len_median_m=120.0, len_sigma=0.8, len_min_m=20.0, len_max_m=2000.0,
+                   speed_mps=(11.111, 19.444, 29.167), lanes=(1, 2, 4),
+                   signals_at=1, limited_access=True, seed=seed)
+
+
+def stress_trips(net: Network, n_trips=10_000_000, seed=4, n_threads=None) -> Trips:
+    """Gravity OD as for the metro workload; departures bimodal, 0.6 N(07:45,
+    60 min) + 0.4 N(11:00, 60 min), truncated to [04:00, 13:00)."""
+    return make_trips(net, n_trips, od_model="gravity", zones=(20, 25), pool_per_zone=16,
+                      spacing_km=0.15, beta_km=METRO_BETA_KM, depart="bimodal", t_lo_s=4 * 3600.0,
+                      t_hi_s=13 * 3600.0, mean_s=7.75 * 3600.0, sd_s=3600.0, mean2_s=11 * 3600.0, sd2_s=3600.0,
+                      w2=0.4, seed=seed, n_threads=n_threads)
+
+
+def incident_closures(net: Network, n=200, k0=int(7.5 * 7200), k1=9 * 7200, seed=4):
+    """Lane 0 closed on n random freeway edges over steps [k0, k1) (07:30-09:00
+    at dt = 0.5 s): (edge, lane, k0, k1) tuples."""
+    fw = np.nonzero(net.edge_class == 2)[0]
+    pick = np.random.default_rng(seed).choice(fw, size=min(n, fw.size), replace=False)
+    return [(int(e), 0, int(k0), int(k1)) for e in np.sort(pick)]
+
+
 # ------------------------------------------------------------------ ensemble --
 @dataclass
 class Ensemble:
