@@ -653,9 +653,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
   // (kFqFields fields x 64 entries)
   extern __shared__ __align__(16) uint32_t s_wbuf[];
   __shared__ int s_rqn[BLOCK / 32];
+  __shared__ uint32_t s_lcn, s_lct;                 // lane-change candidates of the block; batches taken
   Ctl *ctl = p.ctl;
   if (threadIdx.x < CNT_N) s_cnt[threadIdx.x] = 0ull;
   if (threadIdx.x < 8) s_sab2[threadIdx.x] = 2.0f * sqrtf(p.a[threadIdx.x] * p.b[threadIdx.x]);
+  if (threadIdx.x == 0) { s_lcn = 0u; s_lct = 0u; }
   __syncthreads();
   // per-thread counters fit 32 bits over one launch (at most 2048 steps)
   uint32_t c_upd = 0, c_scan = 0, c_clamp = 0, c_lc = 0, c_lce = 0, c_rr = 0, c_dep = 0, c_arr = 0;
@@ -713,11 +715,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     }
     {
       const int lane = threadIdx.x & 31;
-      // each warp lists its candidates in a region of its own (at most one
-      // per list entry it visits); it decides them after its record loop
-      const uint32_t wg = gtid >> 5;
-      const uint32_t reg0 = wg * 32u * ((nact + gsz - 1u) / gsz);
-      uint32_t ncand = 0;   // warp-uniform
+      // the block lists its candidates in a region of its own (at most one
+      // per list entry its threads visit); after the record loops its warps
+      // decide them, taking batches of 32 from the block's list
+      const uint32_t reg0 = blockIdx.x * (uint32_t)BLOCK * ((nact + gsz - 1u) / gsz);
       uint32_t base = gtid - (uint32_t)lane;
       uint32_t s_nx = base + lane < nact ? __ldcg(act_in + base + lane) : MANTA_NONE;
       for (; base < nact; base += gsz) {
@@ -747,19 +748,26 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
                  (w.v > 0.0f || !((ld_mask(w.ld) >> ln) & 1u) || closable(w.em) || ld_nxclo(w.ld));
           if (cand) w.pcell = s;          // the list entry carries the slot in pcell
         }
-        // candidates join the warp's lane-change list (a copy of the record
+        // candidates join the block's lane-change list (a copy of the record
         // and the list position)
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
+        uint32_t b = 0;
+        if (lane == 0 && bal) b = atomicAdd(&s_lcn, (uint32_t)__popc(bal));
+        b = __shfl_sync(0xFFFFFFFFu, b, 0);
         if (cand) {
-          const uint32_t at = reg0 + ncand + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+          const uint32_t at = reg0 + b + (uint32_t)__popc(bal & ((1u << lane) - 1u));
           p.lcq[at] = w;
           p.lcq_pos[at] = pos;
         }
-        ncand += (uint32_t)__popc(bal);
       }
       // lane-change decisions on M_k, a full warp of candidates at a time
-      __syncwarp();
-      for (uint32_t b0 = 0; b0 < ncand; b0 += 32u) {
+      __syncthreads();
+      const uint32_t ncand = s_lcn;
+      for (;;) {
+        uint32_t b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&s_lct, 32u);
+        b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+        if (b0 >= ncand) break;
         const uint32_t j = b0 + (uint32_t)lane;
         if (j < ncand) {
           const Veh c = load_veh_at(p.lcq + reg0 + j);
@@ -1231,6 +1239,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       }
     }
     if (gtid == 0) ctl->n_compact = 0u;
+    if (threadIdx.x == 0) { s_lcn = 0u; s_lct = 0u; }   // the block's lane-change list of the next step
     if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
     if (timer) { const uint64_t t = globaltimer(); ph[3] += t - tp; tp = t; }
   }
