@@ -1,5 +1,6 @@
-"""Build the in-tree native libraries: libmanta.so (CUDA, sm_103a) and the
-synthetic-input generator.  Cross-compiles without a GPU."""
+"""Build the in-tree native libraries: libmanta.so (CUDA, sm_103a), its
+fast-math variant libmanta_fast.so, and the synthetic-input generator.
+Cross-compiles without a GPU."""
 from __future__ import annotations
 
 import os
@@ -10,6 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libmanta.so")
+LIB_FAST = os.path.join(PKG, "libmanta_fast.so")
 
 # The product build is the bit-exact build: no FMA contraction, IEEE division
 # and square root.  The path is memory-bound, so this costs nothing measurable.
@@ -17,8 +19,14 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", 
               "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
               "-Xcompiler", "-fPIC,-fvisibility=hidden", "-shared"]
 
+# The fast-math variant: FMA contraction, approximate division and square
+# root, flush-to-zero.  Same sources and ABI; its trajectories agree with the
+# bit-exact build to within the tolerance tested, not bit for bit.
+NVCC_FAST_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+                   "--use_fast_math", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-shared"]
+
 SOURCES = ["manta.cu"]
-DEPS = ["manta.cu", "sim.cuh", "step_kernel.cuh"]
+DEPS = ["manta.cu", "sim.cuh", "step_kernel.cuh", "adjoint.cuh"]
 
 
 def _stale(out, deps):
@@ -28,13 +36,15 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, fast: bool = True) -> str:
     deps = [os.path.join(CSRC, d) for d in DEPS] + [os.path.join(INCLUDE, "manta.h")]
-    if force or _stale(LIB, deps):
-        cmd = ["nvcc", *NVCC_FLAGS, "-I", INCLUDE, "-o", LIB, *[os.path.join(CSRC, s) for s in SOURCES]]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        subprocess.check_call(cmd)
+    todo = [(LIB, NVCC_FLAGS)] + ([(LIB_FAST, NVCC_FAST_FLAGS)] if fast else [])
+    for out, flags in todo:
+        if force or _stale(out, deps):
+            cmd = ["nvcc", *flags, "-I", INCLUDE, "-o", out, *[os.path.join(CSRC, s) for s in SOURCES]]
+            if verbose:
+                cmd.insert(1, "-Xptxas=-v")
+            subprocess.check_call(cmd)
     from . import synth
     synth.build(force=force)
     return LIB
