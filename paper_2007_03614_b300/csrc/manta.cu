@@ -1021,6 +1021,8 @@ manta_status manta_tape_start(manta_sim *S, int64_t n_steps) {
   manta_status st = check_steppable(S);
   if (st != MANTA_OK) return st;
   if (n_steps < 1 || n_steps > (1 << 30)) return fail(MANTA_E_INVALID, "n_steps out of range");
+  if ((double)n_steps * (double)std::max<int64_t>(S->n_trips, 1) * (double)sizeof(TapeRec) > 1.0e15)
+    return fail(MANTA_E_INVALID, "tape larger than 1 PB: record fewer steps per segment");
   const size_t need = (size_t)n_steps * (size_t)std::max<int64_t>(S->n_trips, 1);
   if (need > S->tape_cap) {
     cudaStreamSynchronize(S->stream);

@@ -107,3 +107,43 @@ def test_create_rejects_bad_network(lib):
     net = nets.line(2)
     net.edge_class = np.array([0, 5], np.uint8)          # class >= n_classes
     assert _create(net)[0] == manta.E_INVALID
+
+
+def test_calls_on_null_handles_fail_cleanly(lib):
+    """Every entry point that takes a simulation, graph or checkpoint rejects
+    NULL with MANTA_E_INVALID (or a documented sentinel) without touching CUDA."""
+    P = C.c_void_p
+    out = P()
+    lib.manta_step.argtypes = [P, C.c_int64]
+    assert lib.manta_step(None, 1) == manta.E_INVALID
+    assert lib.manta_load_trips(None, 0, None, None, None) == manta.E_INVALID
+    assert lib.manta_set_lane_closure(None, 0, 0, 0, 1) == manta.E_INVALID
+    assert lib.manta_set_variant(None, 0) == manta.E_INVALID
+    assert lib.manta_get_variant(None) == -1
+    assert lib.manta_autotune(None, 10, 1, None, None) == manta.E_INVALID
+    assert lib.manta_graph_capture(None, 10, C.byref(out)) == manta.E_INVALID and not out.value
+    assert lib.manta_graph_launch(None) == manta.E_INVALID
+    assert lib.manta_checkpoint_save(None, C.byref(out)) == manta.E_INVALID and not out.value
+    assert lib.manta_checkpoint_restore(None, None) == manta.E_INVALID
+    assert lib.manta_checkpoint_step(None) == -1 and lib.manta_checkpoint_bytes(None) == 0
+    assert lib.manta_tape_start(None, 10) == manta.E_INVALID
+    assert lib.manta_tape_stop(None) == manta.E_INVALID
+    n = C.c_int64()
+    assert lib.manta_tape_copy(None, None, 0, C.byref(n)) == manta.E_INVALID
+    assert lib.manta_adjoint(None, None, None, None, None) == manta.E_INVALID
+    assert lib.manta_replay(None, None, None, None, None, None) == manta.E_INVALID
+    # releasing NULL is a no-op
+    lib.manta_graph_destroy(None)
+    lib.manta_checkpoint_destroy(None)
+    lib.manta_destroy(None)
+
+
+def test_launch_shape_table(lib):
+    n = lib.manta_variant_count()
+    assert n >= 2
+    t, b = C.c_int32(), C.c_int32()
+    for v in range(n):
+        assert lib.manta_variant_info(v, C.byref(t), C.byref(b)) == manta.OK
+        assert t.value % 32 == 0 and b.value >= 1
+    assert lib.manta_variant_info(n, C.byref(t), C.byref(b)) == manta.E_INVALID
+    assert lib.manta_variant_info(-1, None, None) == manta.E_INVALID
