@@ -259,3 +259,40 @@ def test_ensemble_union_bit_exact():
     ec = g.edge_counters(0)
     for s in range(len(sc)):
         assert int(ec["entries"][ens.edge_off[s]:ens.edge_off[s + 1]].sum()) > 0
+
+
+def test_stress_day_properties():
+    """The stress configuration at full size (~1.6M edges, 10M trips, lane 0
+    closed on 200 freeway edges 07:30-09:00), run from 04:00 to 08:30 in the
+    launch size the benchmark uses: conservation, lane-map occupancy equal to
+    the on-network count, fronts at least L apart in every lane, and no
+    vehicle beyond the mid-edge obstacle of a closed lane."""
+    net = synth.stress_network()
+    tr = synth.stress_trips(net)
+    clo = synth.incident_closures(net)
+    g = manta.Sim(net, t0_step=int(4 * 7200))
+    for (e, l, k0, k1) in clo:
+        g.set_lane_closure(e, l, k0, k1)
+    nets.load(g, tr)
+    n = int(8.5 * 7200) - int(4 * 7200)
+    while n > 0:
+        g.step(min(1800, n))
+        n -= 1800
+    st = g.stats()
+    assert st["departed"] == st["arrived"] + st["on_network"]
+    assert st["loaded"] == st["departed"] + st["waiting"]
+    assert st["on_network"] > 500_000
+    m = g.lane_map()
+    occ = np.nonzero(m != 0xFF)[0]
+    assert len(occ) == st["on_network"]
+    cells = np.maximum(np.floor(net.edge_length_m.astype(np.float64) + 0.5).astype(np.int64), 5 + 2 + 1)
+    row_len = np.repeat(cells, net.edge_lanes.astype(np.int64))
+    row_start = np.concatenate([[0], np.cumsum(row_len)[:-1]])
+    row_of = np.searchsorted(row_start, occ, side="right") - 1
+    same = row_of[1:] == row_of[:-1]
+    assert np.all(np.diff(occ)[same] >= 5)
+    lane0 = np.concatenate([[0], np.cumsum(net.edge_lanes.astype(np.int64))[:-1]])
+    for (e, l, k0, k1) in clo:
+        r = int(lane0[e]) + l
+        C = int(row_len[r])
+        assert np.all(m[row_start[r] + C // 2: row_start[r] + C] == 0xFF), e
