@@ -195,7 +195,8 @@ MANTA_API manta_status manta_phase_times(manta_sim *sim, double *ms4);
  * The step kernel exists in several launch shapes (threads per block,
  * minimum blocks per SM: the second sets the register budget).  Every shape
  * computes the same results bit for bit; only speed differs with the
- * workload.  A new simulation uses shape 0. */
+ * workload.  A new simulation uses shape 0.  (No counterpart in the paper:
+ * these concern only how the step kernel is launched.) */
 MANTA_API int32_t manta_variant_count(void);
 /* Threads per block and minimum blocks per SM of shape v (either pointer may
  * be NULL); MANTA_E_INVALID if v is out of range. */
@@ -226,7 +227,11 @@ MANTA_API manta_status manta_autotune(manta_sim *sim, int64_t trial_steps, int32
  * advances the simulation by n_steps: the kernels take their first step
  * index from device memory, so replays continue where the previous work
  * left off.  Replays and manta_step calls may be mixed.  The graph refers
- * to the simulation and must be destroyed before it. */
+ * to the simulation and must be destroyed before it.  (No counterpart in
+ * the paper.)  Errors: MANTA_E_INVALID for NULL arguments, n_steps < 1 or a
+ * sim on the default stream; MANTA_E_STATE before manta_load_trips or after
+ * a device error; MANTA_E_CUDA if capture or instantiation fails (nothing
+ * was launched then). */
 typedef struct manta_graph manta_graph;
 MANTA_API manta_status manta_graph_capture(manta_sim *sim, int64_t n_steps, manta_graph **out);
 MANTA_API manta_status manta_graph_launch(manta_graph *graph);
@@ -240,7 +245,12 @@ MANTA_API void manta_graph_destroy(manta_graph *graph);
  * asynchronously on the sim's stream; manta_checkpoint_restore copies it
  * back, and the run continues from the saved step as if it had never left
  * it (results are bit-identical).  Checkpoints belong to the simulation they
- * were taken from and must be destroyed before it. */
+ * were taken from and must be destroyed before it.  They serve the
+ * checkpointed adjoint below (re-running segments of a run) and resuming a
+ * run; the paper has no counterpart.  Errors: MANTA_E_INVALID for NULL
+ * arguments or a checkpoint of another simulation; MANTA_E_STATE before
+ * manta_load_trips or after a device error; MANTA_E_OOM if the device
+ * buffer cannot be allocated. */
 typedef struct manta_checkpoint manta_checkpoint;
 MANTA_API manta_status manta_checkpoint_save(manta_sim *sim, manta_checkpoint **out);
 MANTA_API manta_status manta_checkpoint_restore(manta_sim *sim, const manta_checkpoint *ckpt);
