@@ -47,6 +47,8 @@ BYTES_PER_ROUTE_READ = 29
 BYTES_PER_LC_EVAL = 64
 KERNEL_SOURCES = ("paper_2007_03614_b300/csrc/step_kernel.cuh", "paper_2007_03614_b300/csrc/sim.cuh")
 TRAFFIC_PROFILE = "profiles/metro_step_kernel_ncu.md"
+WORKLOAD = ("metro-shaped morning: ~550k directed edges / ~218k nodes, 3.2M trips, "
+            "05:00-12:00 departures N(08:00, 75 min), dt = 0.5 s")
 
 
 def algorithmic_bytes(d: dict) -> int:
@@ -308,8 +310,7 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded metro-shaped lattice network and gravity-model trips)",
-        "config": {"workload": "metro-shaped morning: ~550k directed edges / ~218k nodes, 3.2M trips, "
-                               "05:00-12:00 departures N(08:00, 75 min), dt = 0.5 s",
+        "config": {"workload": WORKLOAD,
                    "sim_steps_per_bench_step": chunk, "t0_step": T0_STEP,
                    "timed_sim_window": [T0_STEP + args.warmup * chunk, T0_STEP + (args.warmup + args.steps) * chunk],
                    "l2": "flushed between timed steps (256 MB write) and working set > L2",
@@ -824,7 +825,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * dt / max(1, args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "metro-shaped network, CPU oracle sample", "sim_steps_per_bench_step": per},
+        "config": {"workload": WORKLOAD, "sim_steps_per_bench_step": per,
+                   "sample": "the oracle on a bounded sample of the workload (see cpu_baseline.sample)"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
