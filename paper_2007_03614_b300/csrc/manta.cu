@@ -32,6 +32,45 @@ constexpr int32_t kStepsPerLaunch = 2048;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per grid barrier wait
 constexpr uint64_t kMapPad = 64;                    // lane-map padding after the last row
 
+// Marks the first route entry of every trip in a bitmap.
+__global__ void trip_start_kernel(const uint32_t *roff, uint32_t n, uint32_t *bits) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t q = roff[j];
+    atomicOr(bits + (q >> 5), 1u << (q & 31));
+  }
+}
+
+// Turns the raw route edges into route entries, in place: entry q becomes
+// edge | (lane mask toward the next edge of the trip) << 24, and bit q of
+// nclo is set when that next edge has a closure window.  The edge bits of an
+// entry are the same before and after, so reading a neighbour's entry while
+// it is being rewritten is safe.  The first failing entry (edge out of range,
+// or not followed by an edge leaving its head node) goes to *bad.
+__global__ void route_kernel(uint32_t *route, uint64_t nr, const uint32_t *start_bits, uint32_t E,
+                             const uint32_t *esrc, const EdgeMeta *em, const uint32_t *out_off, const uint32_t *out_e,
+                             const uint32_t *conn_off, const uint32_t *conn, uint32_t *nclo,
+                             unsigned long long *bad) {
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nr; q += (uint64_t)gridDim.x * blockDim.x) {
+    const int32_t raw = (int32_t)route[q];
+    if (raw < 0 || (uint32_t)raw >= E) { atomicMin(bad, (unsigned long long)q); continue; }
+    const uint32_t e = (uint32_t)raw;
+    const bool last = q + 1 == nr || ((start_bits[(q + 1) >> 5] >> ((q + 1) & 31)) & 1u);
+    uint32_t mask = 0xFFu;
+    if (!last) {
+      const uint32_t e2 = route[q + 1] & MANTA_EDGE_MASK;
+      const uint32_t nd = em[e].dst & ~MANTA_CLOSABLE;
+      int64_t idx = -1;
+      if (e2 < E && esrc[e2] == nd)
+        for (uint32_t z = out_off[nd]; z < out_off[nd + 1]; ++z)
+          if (out_e[z] == e2) { idx = (int64_t)(z - out_off[nd]); break; }
+      if (idx < 0) { atomicMin(bad, (unsigned long long)q); continue; }
+      mask = conn[conn_off[e] + (uint32_t)idx];
+      if (em[e2].dst & MANTA_CLOSABLE) atomicOr(nclo + (q >> 5), 1u << (q & 31));
+    }
+    route[q] = e | (mask << MANTA_EDGE_BITS);
+  }
+}
+
 __global__ void prime_kernel(Params p, uint32_t hi, int cb) {
   uint32_t *dep = cb ? p.dep1 : p.dep0;
   const uint32_t gsz = gridDim.x * blockDim.x;
@@ -429,29 +468,18 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   if (n > 0 && route_off[0] != 0) return fail(MANTA_E_ROUTE, "route_off[0] != 0");
   const int64_t nr = n > 0 ? route_off[n] : 0;
   if (nr < 0 || nr > 0xFFFFFFF0ll) return fail(MANTA_E_ROUTE, "too many route entries");
-  std::vector<uint32_t> route((size_t)nr), roff((size_t)n + 1);
+  // per trip on the host: route bounds, first edge, departure step; the
+  // route entries themselves are checked and converted on the device
+  std::vector<uint32_t> roff((size_t)n + 1), first((size_t)n);
   std::vector<int64_t> dstep((size_t)n);
   const double dt = S->cfg.dt;
   for (int64_t j = 0; j < n; ++j) {
     const int64_t a = route_off[j], b = route_off[j + 1];
     if (b <= a || b > nr) return fail(MANTA_E_ROUTE, "empty or unordered route of trip " + std::to_string(j));
     roff[j] = (uint32_t)a;
-    for (int64_t q = a; q < b; ++q) {
-      const int32_t e = route_edges[q];
-      if (e < 0 || e >= S->E) return fail(MANTA_E_ROUTE, "route edge out of range in trip " + std::to_string(j));
-      uint32_t mask = 0xFFu;
-      if (q + 1 < b) {
-        const int32_t e2 = route_edges[q + 1];
-        if (e2 < 0 || e2 >= S->E || S->edst[e] != S->esrc[e2])
-          return fail(MANTA_E_ROUTE, "route of trip " + std::to_string(j) + " is not contiguous");
-        const int32_t nd = S->edst[e];
-        int64_t idx = -1;
-        for (int64_t z = S->out_off[nd]; z < S->out_off[nd + 1]; ++z)
-          if (S->out_e[z] == e2) { idx = z - S->out_off[nd]; break; }
-        mask = S->conn[S->conn_off[e] + idx];
-      }
-      route[q] = (uint32_t)e | (mask << MANTA_EDGE_BITS);
-    }
+    const int32_t e = route_edges[a];
+    if (e < 0 || e >= S->E) return fail(MANTA_E_ROUTE, "route edge out of range in trip " + std::to_string(j));
+    first[j] = (uint32_t)e;
     const float t = depart_time_s[j];
     if (!(t == t) || std::fabs((double)t / dt) > 2.0e9) return fail(MANTA_E_INVALID, "bad departure time of trip " + std::to_string(j));
     dstep[j] = (int64_t)std::ceil((double)t / dt);
@@ -460,7 +488,7 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   // departure queues per first edge, ordered by (step, id)
   std::vector<uint32_t> order((size_t)n);
   std::iota(order.begin(), order.end(), 0u);
-  auto first_edge = [&](uint32_t j) { return route[roff[j]] & MANTA_EDGE_MASK; };
+  auto first_edge = [&](uint32_t j) { return first[j]; };
   std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
     const uint32_t ea = first_edge(a), eb = first_edge(b);
     if (ea != eb) return ea < eb;
@@ -482,15 +510,20 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
     due_edge[i] = first_edge(dorder[i]);
     if (d <= S->k) prime_hi = (uint32_t)(i + 1);
   }
-  // bit q: the edge after route entry q has a closure window (read by lane changes)
-  std::vector<uint32_t> nclo(((size_t)nr + 31) / 32 + 1, 0u);
-  for (int64_t j = 0; j < n; ++j)
-    for (int64_t q = roff[j]; q + 1 < (int64_t)roff[j + 1]; ++q)
-      if (S->em_h[route[q + 1] & MANTA_EDGE_MASK].dst & MANTA_CLOSABLE) nclo[q >> 5] |= 1u << (q & 31);
   Params &P = S->P;
   bool ok = true;
-  uint32_t *d_nclo = dalloc<uint32_t>(S, nclo.size(), &ok);
-  uint32_t *d_route = dalloc<uint32_t>(S, route.size(), &ok);
+  const size_t nbits = ((size_t)nr + 31) / 32 + 1;   // bitmaps over route entries
+  uint32_t *d_nclo = dalloc<uint32_t>(S, nbits, &ok);
+  uint32_t *d_starts = dalloc<uint32_t>(S, nbits, &ok);
+  uint32_t *d_route = dalloc<uint32_t>(S, (size_t)nr, &ok);
+  // out-edges of every node and lane masks per (in-edge, out-edge), for the route conversion
+  std::vector<uint32_t> h_out_off(S->out_off.begin(), S->out_off.end()), h_out_e(S->out_e.begin(), S->out_e.end());
+  std::vector<uint32_t> h_conn_off(S->conn_off.begin(), S->conn_off.end());
+  uint32_t *d_out_off = dalloc<uint32_t>(S, h_out_off.size(), &ok);
+  uint32_t *d_out_e = dalloc<uint32_t>(S, h_out_e.size(), &ok);
+  uint32_t *d_conn_off = dalloc<uint32_t>(S, h_conn_off.size(), &ok);
+  uint32_t *d_conn = dalloc<uint32_t>(S, S->conn.size(), &ok);
+  unsigned long long *d_bad = dalloc<unsigned long long>(S, 1, &ok);
   uint32_t *d_roff = dalloc<uint32_t>(S, roff.size(), &ok);
   uint32_t *d_qoff = dalloc<uint32_t>(S, q_off.size(), &ok);
   uint32_t *d_qtrip = dalloc<uint32_t>(S, order.size(), &ok);
@@ -512,8 +545,32 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   P.req_g = dalloc<uint32_t>(S, NT, &ok); P.req_t = dalloc<uint32_t>(S, NT, &ok);
   P.req_e2 = dalloc<uint32_t>(S, NT, &ok); P.req_n = dalloc<uint32_t>(S, NT, &ok);
   if (!ok) return fail(MANTA_E_OOM, "device allocation failed in manta_load_trips");
-  bool cp = upload(S, d_nclo, nclo) && upload(S, d_route, route) && upload(S, d_roff, roff) && upload(S, d_qoff, q_off) &&
-            upload(S, d_qtrip, order) && upload(S, d_due, due_step) && upload(S, d_due_e, due_edge);
+  bool cp = upload(S, d_roff, roff) && upload(S, d_qoff, q_off) && upload(S, d_qtrip, order) &&
+            upload(S, d_due, due_step) && upload(S, d_due_e, due_edge) && upload(S, d_out_off, h_out_off) &&
+            upload(S, d_out_e, h_out_e) && upload(S, d_conn_off, h_conn_off) && upload(S, d_conn, S->conn);
+  cp = cp && (nr == 0 || cudaMemcpyAsync(d_route, route_edges, (size_t)nr * 4, cudaMemcpyHostToDevice, S->stream) ==
+                             cudaSuccess);
+  cp = cp && cudaMemsetAsync(d_nclo, 0, nbits * 4, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(d_starts, 0, nbits * 4, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(d_bad, 0xFF, sizeof(unsigned long long), S->stream) == cudaSuccess;
+  if (!cp) return fail(MANTA_E_CUDA, "upload failed in manta_load_trips");
+  if (nr > 0) {
+    const int bt = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    trip_start_kernel<<<bt, 256, 0, S->stream>>>(d_roff, (uint32_t)n, d_starts);
+    const int br = (int)std::min<int64_t>((nr + 255) / 256, 65536);
+    route_kernel<<<br, 256, 0, S->stream>>>(d_route, (uint64_t)nr, d_starts, (uint32_t)S->E, P.esrc, P.em, d_out_off,
+                                           d_out_e, d_conn_off, d_conn, d_nclo, d_bad);
+    unsigned long long bad = ~0ull;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, S->stream) != cudaSuccess ||
+        cudaStreamSynchronize(S->stream) != cudaSuccess)
+      return fail(MANTA_E_CUDA, "route conversion failed in manta_load_trips");
+    if (bad != ~0ull) {
+      const int64_t j = (int64_t)(std::upper_bound(roff.begin(), roff.end() - 1, (uint32_t)bad) - roff.begin()) - 1;
+      return fail(MANTA_E_ROUTE, "route of trip " + std::to_string(j) +
+                                     " has an edge out of range or is not contiguous");
+    }
+  }
   Ctl c0;
   memset(&c0, 0, sizeof(c0));
   c0.due_pos = prime_hi;

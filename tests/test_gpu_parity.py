@@ -144,6 +144,14 @@ def test_error_statuses():
     with pytest.raises(manta.MantaError) as ei:
         g.load_trips(np.array([0, 0], np.int64), np.zeros(0, np.int32), np.array([0.0], np.float32))
     assert ei.value.status == manta.E_ROUTE       # empty route
+    with pytest.raises(manta.MantaError) as ei:     # second trip: an edge out of range after its first
+        g.load_trips(np.array([0, 2, 4], np.int64), np.array([0, 1, 0, 7], np.int32),
+                     np.array([0.0, 0.0], np.float32))
+    assert ei.value.status == manta.E_ROUTE and "trip 1" in str(ei.value)
+    with pytest.raises(manta.MantaError) as ei:     # third trip: not contiguous in its middle
+        g.load_trips(np.array([0, 2, 3, 6], np.int64), np.array([0, 1, 1, 0, 1, 0], np.int32),
+                     np.array([0.0, 0.0, 0.0], np.float32))
+    assert ei.value.status == manta.E_ROUTE and "trip 2" in str(ei.value)
     g.load_trips(np.array([0, 2], np.int64), np.array([0, 1], np.int32), np.array([0.0], np.float32))
     with pytest.raises(manta.MantaError) as ei:
         g.load_trips(np.array([0, 2], np.int64), np.array([0, 1], np.int32), np.array([0.0], np.float32))
