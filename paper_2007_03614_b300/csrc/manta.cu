@@ -485,22 +485,36 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
     dstep[j] = (int64_t)std::ceil((double)t / dt);
   }
   roff[n] = (uint32_t)nr;
-  // departure queues per first edge, ordered by (step, id)
-  std::vector<uint32_t> order((size_t)n);
-  std::iota(order.begin(), order.end(), 0u);
   auto first_edge = [&](uint32_t j) { return first[j]; };
-  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
-    const uint32_t ea = first_edge(a), eb = first_edge(b);
-    if (ea != eb) return ea < eb;
-    return dstep[a] < dstep[b];
-  });
+  // trips in departure-step order (ties by id): a counting sort when the
+  // steps span a modest range, else a stable comparison sort
+  std::vector<uint32_t> dorder((size_t)n);
+  {
+    int64_t lo = INT64_MAX, hi = INT64_MIN;
+    for (int64_t j = 0; j < n; ++j) { lo = std::min(lo, dstep[j]); hi = std::max(hi, dstep[j]); }
+    if (n > 0 && hi - lo < 4 * n + 1024) {
+      std::vector<uint32_t> cnt((size_t)(hi - lo) + 2, 0u);
+      for (int64_t j = 0; j < n; ++j) cnt[(size_t)(dstep[j] - lo) + 1]++;
+      for (size_t i = 1; i < cnt.size(); ++i) cnt[i] += cnt[i - 1];
+      for (int64_t j = 0; j < n; ++j) dorder[cnt[(size_t)(dstep[j] - lo)]++] = (uint32_t)j;
+    } else {
+      std::iota(dorder.begin(), dorder.end(), 0u);
+      std::stable_sort(dorder.begin(), dorder.end(), [&](uint32_t a, uint32_t b) { return dstep[a] < dstep[b]; });
+    }
+  }
+  // departure queues per first edge, ordered by (step, id): a stable counting
+  // sort by first edge of the trips in departure-step order
   std::vector<uint32_t> q_off(S->E + 1, 0);
   for (int64_t j = 0; j < n; ++j) q_off[first_edge((uint32_t)j) + 1]++;
   for (int32_t e = 0; e < S->E; ++e) q_off[e + 1] += q_off[e];
-  // trips in departure-step order
-  std::vector<uint32_t> dorder((size_t)n);
-  std::iota(dorder.begin(), dorder.end(), 0u);
-  std::stable_sort(dorder.begin(), dorder.end(), [&](uint32_t a, uint32_t b) { return dstep[a] < dstep[b]; });
+  std::vector<uint32_t> order((size_t)n);
+  {
+    std::vector<uint32_t> at(q_off.begin(), q_off.end() - 1);
+    for (int64_t i = 0; i < n; ++i) {
+      const uint32_t j = dorder[i];
+      order[at[first_edge(j)]++] = j;
+    }
+  }
   std::vector<int32_t> due_step((size_t)n);
   std::vector<uint32_t> due_edge((size_t)n);
   uint32_t prime_hi = 0;
