@@ -358,6 +358,9 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   }
   std::vector<uint32_t> esrc_u(E);
   for (int32_t e = 0; e < E; ++e) esrc_u[e] = (uint32_t)edge_src[e];
+  // in-lane range of each edge's tail node: a departure's competitors
+  std::vector<uint2> src_in(E);
+  for (int32_t e = 0; e < E; ++e) src_in[e] = make_uint2(nin_off[edge_src[e]], nin_off[edge_src[e] + 1]);
   std::vector<uint32_t> lane_base_e(S->lane_base.begin(), S->lane_base.end() - 1);
   std::vector<uint8_t> ntype(node_type, node_type + N);
   // device allocations
@@ -368,6 +371,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   EdgeSig *d_es = dalloc<EdgeSig>(S, E, &ok);
   uint8_t *d_nt = dalloc<uint8_t>(S, N, &ok);
   uint32_t *d_esrc = dalloc<uint32_t>(S, E, &ok);
+  uint2 *d_src_in = dalloc<uint2>(S, E, &ok);
   uint32_t *d_lb = dalloc<uint32_t>(S, E, &ok);
   uint32_t *d_nin_off = dalloc<uint32_t>(S, N + 1, &ok);
   uint32_t *d_nin = dalloc<uint32_t>(S, lanes_total, &ok);
@@ -394,6 +398,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   P.ctl = dalloc<Ctl>(S, 1, &ok);
   if (!ok) { manta_destroy(S); return fail(MANTA_E_OOM, "device allocation failed in manta_create"); }
   bool cp = upload(S, d_em, em) && upload(S, d_es, es) && upload(S, d_nt, ntype) && upload(S, d_esrc, esrc_u) &&
+            upload(S, d_src_in, src_in) &&
             upload(S, d_lb, lane_base_e) && upload(S, d_nin_off, nin_off) && upload(S, d_nin, nin) &&
             upload(S, d_stops, stops) && upload(S, d_mtab, mtab);
   cp = cp && cudaMemsetAsync(P.atlas0, 0xFF, bytes + kMapPad, S->stream) == cudaSuccess &&
@@ -425,7 +430,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
     return fail(MANTA_E_OOM, "device allocation failed in manta_create");
   }
   P.clo_k0 = d_ck0; P.clo_k1 = d_ck1;
-  P.em = d_em; P.es = d_es; P.ntype = d_nt; P.esrc = d_esrc; P.lane_base = d_lb;
+  P.em = d_em; P.es = d_es; P.ntype = d_nt; P.esrc = d_esrc; P.src_in = d_src_in; P.lane_base = d_lb;
   P.nin_off = d_nin_off; P.nin = d_nin; P.stop_nodes = d_stops; P.mtab = d_mtab;
   P.dt = cfg->dt; P.L = cfg->veh_len_cells; P.H = cfg->horizon_cells;
   for (int i = 0; i < 8; ++i) {

@@ -113,6 +113,7 @@ struct Params {
   const EdgeSig *es;
   const uint8_t *ntype;
   const uint32_t *esrc;        // tail node of each edge
+  const uint2 *src_in;         // in-lane range [x, y) in nin of each edge's tail node
   const uint32_t *lane_base;   // first global lane index of each edge
   const uint32_t *nin_off;     // in-lanes (global lane ids) of each node, (edge, lane) order
   const uint32_t *nin;

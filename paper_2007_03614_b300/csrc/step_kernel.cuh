@@ -666,6 +666,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t gsz = gridDim.x * blockDim.x;
+  // the same threads numbered so that consecutive warps of 32 lie in
+  // different blocks: short item lists (lane changes, departures, merges)
+  // spread over every SM instead of queueing on the first few SMs' load units
+  const uint32_t gspr = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u + (threadIdx.x & 31u);
   const int L = p.L;
   bool alive = ldvi(&ctl->err) == 0;
   unsigned bar_target = 0;
@@ -779,7 +783,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         }
       }
     }
-    for (uint32_t j = gtid; j < p.n_stop; j += gsz) {
+    for (uint32_t j = gspr; j < p.n_stop; j += gsz) {
       const uint32_t n = __ldg(p.stop_nodes + j);
       if (ldv(p.permit + n) != MANTA_NONE) continue;
       const uint32_t o = __ldg(p.nin_off + n), m = __ldg(p.nin_off + n + 1) - o;
@@ -800,7 +804,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     // ================================================================ P2
     const uint32_t nchg = ldv(&ctl->n_chg);
     if (nchg) {
-      for (uint32_t i = gtid; i < nchg; i += gsz) {
+      for (uint32_t i = gspr; i < nchg; i += gsz) {
         const uint32_t s = __ldcg(p.chg + i);
         const uint32_t pos = __ldcg(p.chg_pos + i);
         const Veh w = load_veh(p, s);
@@ -827,15 +831,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     const uint32_t tag = (uint32_t)(k + 1);
     // departure requests on M_k'
     const uint32_t ndep = ldv(&ctl->n_dep[cb]);
-    for (uint32_t i = gtid; i < ndep; i += gsz) {
+    for (uint32_t i = gspr; i < ndep; i += gsz) {
       const uint32_t e = __ldcg(dep + i);
+      // the queue head (an edge on this list has a trip waiting) loads with
+      // the edge record, and the head's trip id with the entry cells
       const EdgeMeta em = load_em(p, e);
+      const uint32_t lb = __ldg(p.lane_base + e);
+      const uint32_t qh = __ldg(p.q_off + e) + __ldcg(p.q_pos + e);
+      const uint32_t j = __ldg(p.q_trip + qh);
       const int C = (int)cells_of(em.cnl);
       const int need = min(C, L + p.s0c[class_of(em.cnl)]);
-      if (closable(em) && lane_closed(p, __ldg(p.lane_base + e), k)) continue;
+      if (closable(em) && lane_closed(p, lb, k)) continue;
       uint32_t byte;
       if (first_up(cur + em.row0, 0, need - 1, byte) >= 0) continue;
-      const uint32_t j = __ldg(p.q_trip + __ldg(p.q_off + e) + __ldcg(p.q_pos + e));
       p.dep_key[e] = ((unsigned long long)tag << 32) | j;
     }
     // vehicles
@@ -862,9 +870,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       uint32_t cslot = ch + wl < nact ? __ldcg(act + ch + wl) : MANTA_NONE;
       uint32_t caddr = ch + wl < nact ? __ldcg(p.p3a + ch + wl) : MANTA_NONE;
       // the chunk after it: its counter value is taken one chunk ahead, so
-      // installing a chunk never waits for the atomic (lane 0 holds it)
+      // installing a chunk never waits for the atomic (lane 0 holds it).  chn
+      // is the raw counter; dyn0 is added only when the chunk is installed, as
+      // an add inside lane 0's branch would wait there for the atomic's return
+      // and hold the whole warp at the reconvergence point
       uint32_t chn = 0, cszn = 32u;
-      if (wl == 0) chn = dyn0 + atomicAdd(&ctl->next3, 32u);
+      if (wl == 0) chn = atomicAdd(&ctl->next3, 32u);
       uint32_t *rqb = wb + 96;
       if (wl == 0) s_rqn[wid] = 0;
       int pn = 0, pu = 0;         // pool size and entries taken (warp-uniform)
@@ -1046,7 +1057,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
             }
             pn = __popc(vb);
             pu = 0;
-            ch = __shfl_sync(0xFFFFFFFFu, chn, 0);
+            ch = dyn0 + __shfl_sync(0xFFFFFFFFu, chn, 0);
             csz = __shfl_sync(0xFFFFFFFFu, cszn, 0);
             const bool inb = (uint32_t)wl < csz && ch + wl < nact;
             cslot = inb ? __ldcg(act + ch + wl) : MANTA_NONE;
@@ -1054,7 +1065,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
             if (wl == 0) {
               const uint32_t rem = ch < nact ? nact - ch : 0u;
               cszn = min(32u, max(4u, rem / (2u * nwarps)));
-              chn = dyn0 + atomicAdd(&ctl->next3, cszn);
+              chn = atomicAdd(&ctl->next3, cszn);
             }
             __syncwarp();
             continue;
@@ -1135,13 +1146,21 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     //    targets lane 0
     //  - arrivals leave the current map
     //  - trips due at step k + 1 join their edge's departure queue
+    // Within each kind, loads that depend on the same earlier value go out
+    // together, and independent counter updates overlap, so that the longest
+    // chain of dependent round trips stays short.
     const uint32_t nreq = ldv(&ctl->n_req);
     const uint32_t narr = ldv(&ctl->n_arr);
     const uint32_t due_lo = ldv(&ctl->due_pos), due_hi = ldv(&ctl->due_hi);
+    // free slots: constant during this phase (arrivals freed theirs in P3)
+    const uint32_t fc = ldv(&ctl->free_count), n_slots = ldv(&ctl->n_slots);
     const uint32_t t_dep = nreq, t_arr = t_dep + ndep, t_due = t_arr + narr, t_end = t_due + (due_hi - due_lo);
-    for (uint32_t t = gtid; t < t_end; t += gsz) {
+    for (uint32_t t = gspr; t < t_end; t += gsz) {
       if (t < t_dep) {
         const uint32_t i = t;
+        // round trip 1: the request; 2: the records it names; 3: the
+        // competitors' slots and the route entry after the crossing; 4: their
+        // requests
         const uint32_t s = __ldcg(p.req + i);
         const uint32_t gown = __ldcg(p.req_g + i), tgt = __ldcg(p.req_t + i);
         const uint32_t e2 = __ldcg(p.req_e2 + i), n = __ldcg(p.req_n + i);
@@ -1198,35 +1217,47 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         }
       } else if (t < t_arr) {
         const uint32_t i = t - t_dep;
+        // round trip 1: the edge; 2: everything keyed by the edge; 3: the
+        // competitors' slots and the head trip's route; 4: their requests;
+        // 5: the winner's three counter updates together; 6: its slot and its
+        // departure-list position together
         const uint32_t e = __ldcg(dep + i);
         const unsigned long long dk = __ldcg(p.dep_key + e);
+        const uint2 rg = __ldg(p.src_in + e);
+        const EdgeMeta em = load_em(p, e);
+        const uint32_t qp = __ldcg(p.q_pos + e);
         const uint32_t j = (uint32_t)dk;
         bool won = (uint32_t)(dk >> 32) == tag;
+        uint32_t rc = 0u, rend = 0u, ld0 = 0u;
         if (won) {
-          const uint32_t n = __ldg(p.esrc + e);
-          won = min_competitor(p, __ldg(p.nin_off + n), __ldg(p.nin_off + n + 1), MANTA_NONE, target_key(e, 0u),
-                               tag) > j;
+          rc = __ldg(p.route_off + j);
+          rend = __ldg(p.route_off + j + 1u);
+          ld0 = ld_for_entry(p, rc, 0u);
+          won = min_competitor(p, rg.x, rg.y, MANTA_NONE, target_key(e, 0u), tag) > j;
         }
-        uint32_t s = MANTA_NONE;
-        bool keep = true;
+        // the results of these two atomics are first used after the list
+        // append below, so the three round trips overlap
+        uint32_t wi = 0u, pend = 2u;
         if (won) {
-          const uint32_t wi = atomicAdd(&ctl->n_depwin, 1u);
-          const uint32_t fc = ldv(&ctl->free_count);
-          s = wi < fc ? __ldcg(p.freel + (fc - 1u - wi)) : ldv(&ctl->n_slots) + (wi - fc);
-          const EdgeMeta em = load_em(p, e);
+          wi = atomicAdd(&ctl->n_depwin, 1u);
+          pend = atomicSub(p.pending + e, 1u);
+        }
+        const uint32_t ia = warp_append(&ctl->n_act[cb ^ 1], won);
+        uint32_t s = MANTA_NONE;
+        if (won) s = wi < fc ? __ldcg(p.freel + (fc - 1u - wi)) : n_slots + (wi - fc);
+        const bool keep = pend > 1u;
+        const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], keep);
+        if (won) {
           Veh w;
-          w.x = 0.0f; w.v = 0.0f; w.id = j; w.rc = __ldg(p.route_off + j); w.rend = __ldg(p.route_off + j + 1u);
-          w.e = e; w.ld = ld_for_entry(p, w.rc, 0u); w.pcell = MANTA_NONE; w.em = em;
+          w.x = 0.0f; w.v = 0.0f; w.id = j; w.rc = rc; w.rend = rend;
+          w.e = e; w.ld = ld0; w.pcell = MANTA_NONE; w.em = em;
           store_veh(p, s, w);
+          act[ia] = s;
           nxt[em.row0] = speed_code(0.0f);
           atomicAdd(p.entry + e, 1u);
           c_dep++;
-          p.q_pos[e] = __ldcg(p.q_pos + e) + 1u;
-          keep = atomicSub(p.pending + e, 1u) > 1u;
+          p.q_pos[e] = qp + 1u;
         }
-        const uint32_t ia = warp_append(&ctl->n_act[cb ^ 1], won);
-        if (won) act[ia] = s;
-        const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], keep);
         if (keep) dep_n[id2] = e;
       } else if (t < t_due) {
         cur[__ldcg(p.arr + (t - t_arr))] = (uint8_t)MANTA_EMPTY;
