@@ -551,8 +551,8 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   const size_t NT = (size_t)std::max<int64_t>(n, 1);
   P.veh = dalloc<Veh>(S, NT, &ok);
   P.act0 = dalloc<uint32_t>(S, NT, &ok); P.act1 = dalloc<uint32_t>(S, NT, &ok);
-  P.freel = dalloc<uint32_t>(S, NT, &ok); P.chg = dalloc<uint32_t>(S, NT, &ok);
-  P.p3a = dalloc<uint32_t>(S, NT, &ok); P.chg_pos = dalloc<uint32_t>(S, NT, &ok);
+  P.freel = dalloc<uint32_t>(S, NT, &ok); P.lcm = dalloc<LcMove>(S, NT, &ok);
+  P.p3a = dalloc<uint32_t>(S, NT, &ok);
   // candidate regions: every warp may list one candidate per entry it visits,
   // 32 entries per grid-stride block
   size_t gmax = 0;

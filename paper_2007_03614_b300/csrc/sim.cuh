@@ -107,6 +107,15 @@ struct Ctl {
   unsigned long long phase_ns[4];   // device time of phases P1..P4 as seen by block 0
 };
 
+// One lane change, written whole by its decision so that it applies in one
+// round trip: slot, active-list position, old and new map cell; new lane
+// word, first leader-scan batch, speed code.
+struct LcMove {
+  uint32_t slot, pos, from, to;
+  uint32_t ld, p3a, code, pad;
+};
+static_assert(sizeof(LcMove) == 32, "two 16-byte loads per move");
+
 struct Params {
   // network, read-only
   const EdgeMeta *em;
@@ -134,9 +143,9 @@ struct Params {
   // vehicle records by slot
   Veh *veh;
   // lists
-  uint32_t *act0, *act1, *freel, *chg, *req, *arr, *dep0, *dep1;
+  uint32_t *act0, *act1, *freel, *req, *arr, *dep0, *dep1;
   uint32_t *p3a;               // by active-list position: first lane-map batch of the leader scan
-  uint32_t *chg_pos;           // active-list position of each lane changer
+  LcMove *lcm;                 // lane changes decided in P1, applied in P2
   Veh *lcq;                    // lane-change candidates of the step by warp region (record copies,
                                // slot in pcell)
   uint32_t *lcq_pos;           // their active-list positions

@@ -777,9 +777,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           const Veh c = load_veh_at(p.lcq + reg0 + j);
           const uint32_t cpos = __ldcg(p.lcq_pos + reg0 + j);
           const int tgt = lc_decide(p, cur, k, c, c_lce);
-          if (tgt >= 0) p.veh[c.pcell].ld = (c.ld & 0xFF00FFFFu) | ((uint32_t)tgt << 16);
           const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
-          if (tgt >= 0) { p.chg[at] = c.pcell; p.chg_pos[at] = cpos; }
+          if (tgt >= 0) {
+            // the whole move, so that P2 applies it in one round trip; the
+            // map byte at the vehicle's front cell is its own speed code
+            const uint32_t stride = stride_of(cells_of(c.em.cnl));
+            const int cell = (int)floorf(c.x);
+            const uint32_t a = c.em.row0 + (uint32_t)ld_lane(c.ld) * stride + (uint32_t)cell;
+            const uint32_t b = c.em.row0 + (uint32_t)tgt * stride + (uint32_t)cell;
+            uint4 *m = reinterpret_cast<uint4 *>(p.lcm + at);
+            m[0] = make_uint4(c.pcell, cpos, a, b);
+            m[1] = make_uint4((c.ld & (kLdEdgeBits | 0x0000FF00u)) | (uint32_t)tgt, first_batch(c.em, tgt, cell),
+                              speed_code(c.v), 0u);
+          }
         }
       }
     }
@@ -805,18 +815,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     const uint32_t nchg = ldv(&ctl->n_chg);
     if (nchg) {
       for (uint32_t i = gspr; i < nchg; i += gsz) {
-        const uint32_t s = __ldcg(p.chg + i);
-        const uint32_t pos = __ldcg(p.chg_pos + i);
-        const Veh w = load_veh(p, s);
-        const EdgeMeta &em = w.em;
-        const uint32_t stride = stride_of(cells_of(em.cnl));
-        const uint32_t cell = (uint32_t)(int)floorf(w.x);
-        const uint32_t lo = (uint32_t)ld_lane(w.ld), ln = (w.ld >> 16) & 0xFFu;
-        const uint32_t a = em.row0 + lo * stride + cell, b = em.row0 + ln * stride + cell;
-        cur[b] = cur[a];
-        cur[a] = (uint8_t)MANTA_EMPTY;
-        p.veh[s].ld = (w.ld & (kLdEdgeBits | 0x0000FF00u)) | ln;
-        p.p3a[pos] = first_batch(em, (int)ln, (int)cell);
+        // (slot, list position, old cell, new cell), (lane word, first scan
+        // batch, speed code); the gap acceptance keeps every new cell free,
+        // so no move's new cell is another's old one
+        const uint4 *m = reinterpret_cast<const uint4 *>(p.lcm + i);
+        const uint4 m0 = __ldcg(m), m1 = __ldcg(m + 1);
+        cur[m0.w] = (uint8_t)m1.z;
+        cur[m0.z] = (uint8_t)MANTA_EMPTY;
+        p.veh[m0.x].ld = m1.x;
+        p.p3a[m0.y] = m1.y;
         c_lc++;
       }
       if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
