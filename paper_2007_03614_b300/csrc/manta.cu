@@ -30,7 +30,10 @@ manta_status fail(manta_status s, const std::string &msg) {
 
 constexpr int32_t kStepsPerLaunch = 2048;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per grid barrier wait
-constexpr uint64_t kMapPad = 64;                    // lane-map padding after the last row
+// lane-map padding after the last row: the first leader-scan batch is fetched
+// whole (kFirstChunks 16-byte chunks) before its row's end is known, and may
+// start at the last row's last chunk
+constexpr uint64_t kMapPad = 16 * kFirstChunks > 64 ? 16 * kFirstChunks : 64;
 
 // Marks the first route entry of every trip in a bitmap.
 __global__ void trip_start_kernel(const uint32_t *roff, uint32_t n, uint32_t *bits) {
@@ -377,7 +380,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   uint32_t *d_nin = dalloc<uint32_t>(S, lanes_total, &ok);
   uint32_t *d_stops = dalloc<uint32_t>(S, stops.size(), &ok);
   float *d_mtab = dalloc<float>(S, mtab.size(), &ok);
-  // 64 padding bytes: a scan batch may be fetched whole past the last row
+  // kMapPad padding bytes: a first scan batch may run past the last row
   P.atlas0 = dalloc<uint8_t>(S, bytes + kMapPad, &ok);
   P.atlas1 = dalloc<uint8_t>(S, bytes + kMapPad, &ok);
   P.permit = dalloc<uint32_t>(S, N, &ok);

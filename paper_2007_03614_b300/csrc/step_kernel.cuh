@@ -21,10 +21,19 @@
 // loads in flight: in P3 every lane runs its own vehicle through a state
 // machine of one round trip per iteration and takes a new vehicle as soon as
 // one is done; the vehicle record and its first row batch come back together;
-// lane-map scans issue four 16-byte loads per round trip; and the next
-// segment's node data comes with the batch that ends the current one.
+// the main phase's walk batches (64 bytes first, then 128) land in a
+// shared-memory slot per lane by asynchronous copies, holding no registers,
+// while the lane-change scans load four 16-byte chunks per round trip into
+// registers; and the next segment's node data comes with the batch that ends
+// the current one.
 #include <stdint.h>
 #include "sim.cuh"
+#ifndef MANTA_WALK_CHUNKS
+#define MANTA_WALK_CHUNKS 8
+#endif
+#ifndef MANTA_FIRST_CHUNKS
+#define MANTA_FIRST_CHUNKS 4
+#endif
 
 // Threads per block of the helper kernels.  The step kernel is a template
 // over its launch shape (threads per block, minimum blocks per SM), which
@@ -34,7 +43,16 @@ constexpr int kBlock = 256;
 enum { kFqX, kFqV, kFqId, kFqRc, kFqRend, kFqE, kFqLd, kFqRow0, kFqCnl, kFqLim, kFqDst, kFqS, kFqI, kFqCell, kFqLb,
        kFqKind, kFqCL, kFqVL, kFqE2, kFqE2cnl, kFqFields };
 constexpr int kP3Words = 352 + kFqFields * 64;
-constexpr int kWarpWords = kP3Words;
+// Row batches of the main phase's leader walk land in a shared-memory slot
+// per lane (asynchronous copies, no registers held): the first batch, fetched
+// with the vehicle record, has kFirstChunks 16-byte chunks; every later walk
+// round trip up to kWalkChunks.  Slots are 16 bytes longer than a batch so
+// that the lanes' 16-byte reads of the same chunk fall in different banks.
+constexpr int kFirstChunks = MANTA_FIRST_CHUNKS;
+constexpr int kWalkChunks = MANTA_WALK_CHUNKS;
+constexpr int kSlotBytes = 16 * kWalkChunks + 16;
+static_assert(kFirstChunks <= kWalkChunks, "the slot holds the first batch");
+constexpr int kWarpWords = kP3Words + 32 * kSlotBytes / 4;
 // dynamic shared memory of a step-kernel block of `threads` threads
 constexpr size_t step_smem_bytes(int threads) { return (size_t)(threads / 32) * kWarpWords * 4; }
 
@@ -228,6 +246,38 @@ __device__ __forceinline__ int check_batch(const Batch &b, int c, int lo, int hi
   const int first = c + 16 * j + 4 * t + bpos;
   byte = (a >> (8 * bpos)) & 0xFFu;          // the speed code, already in registers
   return first > hi ? -1 : first;
+}
+// 16-byte asynchronous copy from global memory (L2 only) into shared memory
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// n 16-byte chunks from g into the slot at shared address slot
+__device__ __forceinline__ void slot_fetch(uint32_t slot, const uint8_t *g, int n) {
+  for (int j = 0; j < n; ++j) cp_async16(slot + 16u * (uint32_t)j, g + 16 * j);
+}
+// First occupied cell in [lo, hi] among the n chunks of a slot whose chunk 0
+// starts at row cell c (lo lies in chunk 0), or -1; the speed code in byte.
+__device__ __forceinline__ int check_slot(const uint8_t *slot, int n, int c, int lo, int hi, uint32_t &byte) {
+  for (int j = 0; j < n; ++j) {
+    const uint4 q = *reinterpret_cast<const uint4 *>(slot + 16 * j);
+    uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    if (j == 0) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int d = lo - (c + 4 * t);
+        w[t] |= d <= 0 ? 0u : (d >= 4 ? 0xFFFFFFFFu : ((1u << (8 * d)) - 1u));
+      }
+    }
+    if ((w[0] & w[1] & w[2] & w[3]) == 0xFFFFFFFFu) continue;
+    const int t = w[0] != 0xFFFFFFFFu ? 0 : (w[1] != 0xFFFFFFFFu ? 1 : (w[2] != 0xFFFFFFFFu ? 2 : 3));
+    const uint32_t a = t == 0 ? w[0] : (t == 1 ? w[1] : (t == 2 ? w[2] : w[3]));
+    const int bpos = (__ffs(occupied_bits(a)) - 1) >> 3;
+    const int first = c + 16 * j + 4 * t + bpos;
+    byte = (a >> (8 * bpos)) & 0xFFu;
+    return first > hi ? -1 : first;
+  }
+  return -1;
 }
 // First occupied cell of row[lo..hi] (inclusive), continuing from a batch
 // already loaded at lo & ~15; -1 if none.  Rows are 16-byte aligned and padded.
@@ -480,20 +530,20 @@ struct Walk {
   EdgeMeta sm;       // record of the segment's edge
   bool own;          // the segment is the vehicle's own edge
 };
-// What one round trip brings: a vehicle record (b.q[0..2]) or a row batch,
-// plus the node data when the batch ends a segment.
+// What one walk round trip brings besides the row batch (which lands in the
+// lane's shared-memory slot): the node data when the batch ends a segment.
 struct Fetch {
-  Batch b;
   uint32_t nt;
   EdgeSig sig;
   EdgeMeta sm2;
   uint32_t nent2;
 };
 
-// Byte offset in a lane-map buffer of the first 64-byte batch a leader scan
-// from `cell` reads on lane `lane` of edge record em (the batch holding cell
-// + 1), or MANTA_NONE when the vehicle is at the last cell of its edge.  The
-// buffers carry 64 padding bytes so the batch may run past the row end.
+// Byte offset in a lane-map buffer of the first batch (kFirstChunks 16-byte
+// chunks) a leader scan from `cell` reads on lane `lane` of edge record em
+// (the batch holding cell + 1), or MANTA_NONE when the vehicle is at the last
+// cell of its edge.  The buffers are padded so the batch may run past the row
+// end.
 __device__ __forceinline__ uint32_t first_batch(const EdgeMeta &em, int lane, int cell) {
   const uint32_t C = cells_of(em.cnl);
   return (uint32_t)cell + 1u < C ? em.row0 + (uint32_t)lane * stride_of(C) + (((uint32_t)cell + 1u) & ~15u) : MANTA_NONE;
@@ -534,20 +584,20 @@ __device__ __forceinline__ bool walk_start(const Params &p, const uint8_t *cur, 
 // returns true when the scan is complete; otherwise the next round trip
 // continues along the row or, when the batch reached the end of the scanned
 // range, fetches the node data only.
-__device__ __forceinline__ bool walk_first(const Params &p, const Veh &w, Walk &wk, const Batch &b, int cell, Scan &s,
-                                           uint32_t &c_scan) {
+__device__ __forceinline__ bool walk_first(const Params &p, const Veh &w, Walk &wk, const uint8_t *slot, int cell,
+                                           Scan &s, uint32_t &c_scan) {
   const int segC = (int)cells_of(wk.sm.cnl);
   const int hi = min(wk.limit, segC - 1);
   const int lo = wk.pos;
   const int c0 = lo & ~15;
   uint32_t byte = 0;
-  const int c = check_batch(b, c0, lo, hi, byte);
+  const int c = check_slot(slot, min(kFirstChunks, ((hi - c0) >> 4) + 1), c0, lo, hi, byte);
   if (c >= 0) {
     s.kind = SC_LEADER; s.cL = c; s.vL = speed_decode(byte);
     c_scan += (uint32_t)(c - cell);
     return true;
   }
-  if (c0 + 64 <= hi) { wk.pos = c0 + 64; return false; }
+  if (c0 + 16 * kFirstChunks <= hi) { wk.pos = c0 + 16 * kFirstChunks; return false; }
   if (segC > wk.limit) { c_scan += (uint32_t)p.H; return true; }
   if (wk.r + 1u >= w.rend) { c_scan += (uint32_t)(segC - 1 - cell); return true; }
   wk.pos = hi + 1;
@@ -556,13 +606,15 @@ __device__ __forceinline__ bool walk_first(const Params &p, const Veh &w, Walk &
 
 // Issues the loads of the walk's next round trip.
 __device__ __forceinline__ void walk_issue(const Params &p, const uint8_t *cur, const Veh &w, const Walk &wk,
-                                           Fetch &f) {
+                                           uint32_t slot, Fetch &f) {
   const int segC = (int)cells_of(wk.sm.cnl);
   const int hi = min(wk.limit, wk.base + segC - 1) - wk.base;   // row-relative
   const int lo = wk.pos - wk.base;
   const int c0 = lo & ~15;
-  if (lo <= hi) load_batch(cur + wk.sm.row0 + (uint32_t)wk.sl * stride_of((uint32_t)segC), c0, hi, f.b);
-  const bool last = lo > hi || c0 + 64 > hi;
+  if (lo <= hi)
+    slot_fetch(slot, cur + wk.sm.row0 + (uint32_t)wk.sl * stride_of((uint32_t)segC) + c0,
+               min(kWalkChunks, ((hi - c0) >> 4) + 1));
+  const bool last = lo > hi || c0 + 16 * kWalkChunks > hi;
   if (last && wk.base + segC <= wk.limit && wk.r + 1u < w.rend) {
     f.nt = __ldg(p.ntype + node_of(wk.sm));
     f.sig = load_sig(p, wk.se);
@@ -574,21 +626,22 @@ __device__ __forceinline__ void walk_issue(const Params &p, const uint8_t *cur, 
 // Consumes the round trip issued by walk_issue: returns true when the scan
 // is complete (result in s), otherwise advances the walk.
 __device__ __forceinline__ bool walk_process(const Params &p, int64_t k, const Veh &w, int cell, Walk &wk,
-                                             const Fetch &f, Scan &s, uint32_t &c_scan, uint32_t &c_rr) {
+                                             const Fetch &f, const uint8_t *slot, Scan &s, uint32_t &c_scan,
+                                             uint32_t &c_rr) {
   const int segC = (int)cells_of(wk.sm.cnl);
   const int hi = min(wk.limit, wk.base + segC - 1) - wk.base;
   const int lo = wk.pos - wk.base;
   const int c0 = lo & ~15;
-  const bool last = lo > hi || c0 + 64 > hi;
+  const bool last = lo > hi || c0 + 16 * kWalkChunks > hi;
   if (lo <= hi) {
     uint32_t byte = 0;
-    const int c = check_batch(f.b, c0, lo, hi, byte);
+    const int c = check_slot(slot, min(kWalkChunks, ((hi - c0) >> 4) + 1), c0, lo, hi, byte);
     if (c >= 0) {
       s.kind = SC_LEADER; s.cL = wk.base + c; s.vL = speed_decode(byte);
       c_scan += (uint32_t)(s.cL - cell);
       return true;
     }
-    if (!last) { wk.pos = wk.base + c0 + 64; return false; }
+    if (!last) { wk.pos = wk.base + c0 + 16 * kWalkChunks; return false; }
   }
   const int B = wk.base + segC;
   if (B > wk.limit) { c_scan += (uint32_t)p.H; return true; }
@@ -872,6 +925,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       uint32_t *const wb = s_wbuf + wid * kWarpWords;
       uint32_t *ps = wb, *pi = wb + 32, *pa = wb + 64;
       uint32_t *fq = wb + 352;   // finish queue: kFqFields fields x 64 entries
+      // the lane's batch slot (shared-window address for the copies, pointer for the reads)
+      const uint8_t *slot_p = reinterpret_cast<const uint8_t *>(wb + kP3Words) + wl * kSlotBytes;
+      const uint32_t slot_s = (uint32_t)__cvta_generic_to_shared(slot_p);
       const uint32_t dyn0 = 32u * nwarps;   // every warp's first chunk is fixed
       uint32_t ch = gtid - (uint32_t)wl, csz = 32u;
       uint32_t cslot = ch + wl < nact ? __ldcg(act + ch + wl) : MANTA_NONE;
@@ -1093,22 +1149,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         if (st == 1) {
           // the record and, in the same round trip, the first batch of its row
           w = load_veh(p, s);
-          if (a3 != MANTA_NONE) {
-            const uint4 *ra = reinterpret_cast<const uint4 *>(cur + a3);
-            f.b.q[0] = __ldcg(ra); f.b.q[1] = __ldcg(ra + 1); f.b.q[2] = __ldcg(ra + 2); f.b.q[3] = __ldcg(ra + 3);
-          }
+          if (a3 != MANTA_NONE) slot_fetch(slot_s, cur + a3, kFirstChunks);
         } else if (st == 2) {
-          walk_issue(p, cur, w, wk, f);
+          walk_issue(p, cur, w, wk, slot_s, f);
         }
+        cp_async_wait_all();
         bool fin = false;
         if (st == 1) {
           lb = __ldg(p.lane_base + w.e);      // needed when the vehicle is done
           cell = (int)floorf(w.x);
           fin = walk_start(p, cur, k, w, cell, wk, sc, c_scan);
           st = 2;
-          if (!fin && a3 != MANTA_NONE) fin = walk_first(p, w, wk, f.b, cell, sc, c_scan);
+          if (!fin && a3 != MANTA_NONE) fin = walk_first(p, w, wk, slot_p, cell, sc, c_scan);
         } else if (st == 2) {
-          fin = walk_process(p, k, w, cell, wk, f, sc, c_scan, c_rr);
+          fin = walk_process(p, k, w, cell, wk, f, slot_p, sc, c_scan, c_rr);
         }
         // completed vehicles join the warp's finish queue; the update itself
         // runs 32 at a time with the whole warp
