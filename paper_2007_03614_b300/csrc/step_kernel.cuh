@@ -776,6 +776,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       // per list entry its threads visit); after the record loops its warps
       // decide them, taking batches of 32 from the block's list
       const uint32_t reg0 = blockIdx.x * (uint32_t)BLOCK * ((nact + gsz - 1u) / gsz);
+      // the first lc_cap candidates of the block stay in shared memory; the
+      // rest go to the block's region of the global list
+      constexpr uint32_t lc_cap = (uint32_t)(BLOCK / 32) * kWarpWords * 4u / 64u;
       uint32_t base = gtid - (uint32_t)lane;
       uint32_t s_nx = base + lane < nact ? __ldcg(act_in + base + lane) : MANTA_NONE;
       for (; base < nact; base += gsz) {
@@ -812,9 +815,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         if (lane == 0 && bal) b = atomicAdd(&s_lcn, (uint32_t)__popc(bal));
         b = __shfl_sync(0xFFFFFFFFu, b, 0);
         if (cand) {
-          const uint32_t at = reg0 + b + (uint32_t)__popc(bal & ((1u << lane) - 1u));
-          p.lcq[at] = w;
-          p.lcq_pos[at] = pos;
+          const uint32_t at = b + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+          if (at < lc_cap) {
+            // the block's (otherwise idle) main-phase scratch: 64 bytes per entry
+            uint4 *e = reinterpret_cast<uint4 *>(s_wbuf) + 4u * at;
+            e[0] = make_uint4(__float_as_uint(w.x), __float_as_uint(w.v), w.id, w.rc);
+            e[1] = make_uint4(w.rend, w.e, w.ld, w.pcell);
+            e[2] = make_uint4(w.em.row0, w.em.cnl, __float_as_uint(w.em.lim), w.em.dst);
+            e[3].x = pos;
+          } else {
+            p.lcq[reg0 + at] = w;
+            p.lcq_pos[reg0 + at] = pos;
+          }
         }
       }
       // lane-change decisions on M_k, a full warp of candidates at a time
@@ -827,8 +839,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         if (b0 >= ncand) break;
         const uint32_t j = b0 + (uint32_t)lane;
         if (j < ncand) {
-          const Veh c = load_veh_at(p.lcq + reg0 + j);
-          const uint32_t cpos = __ldcg(p.lcq_pos + reg0 + j);
+          Veh c;
+          uint32_t cpos;
+          if (j < lc_cap) {
+            const uint4 *e = reinterpret_cast<const uint4 *>(s_wbuf) + 4u * j;
+            const uint4 q0 = e[0], q1 = e[1], q2 = e[2];
+            c.x = __uint_as_float(q0.x); c.v = __uint_as_float(q0.y); c.id = q0.z; c.rc = q0.w;
+            c.rend = q1.x; c.e = q1.y; c.ld = q1.z; c.pcell = q1.w;
+            c.em.row0 = q2.x; c.em.cnl = q2.y; c.em.lim = __uint_as_float(q2.z); c.em.dst = q2.w;
+            cpos = e[3].x;
+          } else {
+            c = load_veh_at(p.lcq + reg0 + j);
+            cpos = __ldcg(p.lcq_pos + reg0 + j);
+          }
           const int tgt = lc_decide(p, cur, k, c, c_lce);
           const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
           if (tgt >= 0) {
