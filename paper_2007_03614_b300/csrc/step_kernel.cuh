@@ -1176,6 +1176,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         } else if (st == 2) {
           walk_issue(p, cur, w, wk, slot_s, f);
         }
+        // while those loads are in flight, the whole warp updates 32 vehicles
+        // of the finish queue (it holds at most 63 here: at most 31 left by
+        // the last update and 32 added since)
+        if (fqn >= 32) {
+          __syncwarp();
+          finish(fqn - 32 + wl);
+          fqn -= 32;
+          __syncwarp();
+        }
         cp_async_wait_all();
         bool fin = false;
         if (st == 1) {
@@ -1205,15 +1214,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           fq[kFqE2 * 64 + at] = sc.e2; fq[kFqE2cnl * 64 + at] = sc.e2cnl;
         }
         fqn += __popc(fb);
-        if (fqn >= 32) {
-          __syncwarp();
-          finish(fqn - 32 + wl);
-          fqn -= 32;
-          __syncwarp();
-        }
       }
       __syncwarp();
       if (wl < fqn) finish(wl);
+      __syncwarp();
+      if (fqn > 32 && wl < fqn - 32) finish(32 + wl);
       __syncwarp();
       const int nb = s_rqn[wid];
       if (nb > 0) flush_requests(p, rqb, nb, 0xFFFFFFFFu, wl, 32);
