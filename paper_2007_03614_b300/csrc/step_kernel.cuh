@@ -344,8 +344,14 @@ __device__ __forceinline__ EdgeSig load_sig(const Params &p, uint32_t e) {
 
 __device__ __forceinline__ bool is_green(const EdgeSig &s, int64_t k) {
   if (s.cyc == 0) return true;
-  int64_t m = (k - (int64_t)s.off) % (int64_t)s.cyc;
-  if (m < 0) m += s.cyc;
+  const int64_t d = k - (int64_t)s.off;
+  int64_t m;
+  if ((uint64_t)d < (1ull << 32)) {
+    m = (int64_t)((uint32_t)d % (uint32_t)s.cyc);   // the usual case, in 32 bits
+  } else {
+    m = d % (int64_t)s.cyc;
+    if (m < 0) m += s.cyc;
+  }
   return m >= s.gs && m < (int64_t)s.gs + s.gl;
 }
 
