@@ -684,7 +684,8 @@ def run_search(args):
     (20x20 grid, 20k trips, 3,600 steps): 5 parameter sets {a, b, T, s0} per
     iteration run batched as 5 copies of the network in one simulation,
     against link speeds of a hidden parameter set; also times the same 5 sets
-    run one after another."""
+    run one after another.  Drivers draw their own speed limit on every edge
+    (Section IV-B) with sigma_s = --sigma-frac x the edge's limit."""
     import torch
 
     from paper_2007_03614_b300 import calibrate, manta, synth
@@ -706,7 +707,7 @@ def run_search(args):
 
     def single(th):
         g = manta.Sim(one.net, stream=stream, stats_window_steps=600, n_stats_windows=W, n_classes=1, v0f=[1.0],
-                      a=[th["a"]], b=[th["b"]], T=[th["T"]], s0=[th["s0"]])
+                      a=[th["a"]], b=[th["b"]], T=[th["T"]], s0=[th["s0"]], speed_sigma_frac=args.sigma_frac)
         g.load_trips(one.trips.route_off, one.trips.route_edges, one.trips.depart_time_s)
         g.step(steps)
         out = calibrate.link_speed_cells(g, W, 0, int(net.n_edges))
@@ -718,7 +719,8 @@ def run_search(args):
     theta0 = {"a": cfg.a[0], "b": cfg.b[0], "T": cfg.T[0], "s0": cfg.s0[0]}
     t0 = time.perf_counter()
     res = calibrate.perturbation_search(net, tr, target, tcnt, theta0, iters=args.calib_iters, sets=5,
-                                        n_steps=steps, window_steps=600, seed=1, stream=stream)
+                                        n_steps=steps, window_steps=600, seed=1, stream=stream,
+                                        speed_sigma_frac=args.sigma_frac)
     t_batched = (time.perf_counter() - t0) / len(res["history"])
     # the same five sets of the first iteration, one simulation each
     t1 = time.perf_counter()
@@ -731,7 +733,7 @@ def run_search(args):
         "value": 1.0 / t_batched, "unit": "iterations/s", "n_gpus": 1, "steps": len(res["history"]),
         "warmup": 0, "ms_per_step": 1000.0 * t_batched, "higher_is_better": True, "data": "synthetic",
         "config": {"workload": "search", "edges": int(net.n_edges), "trips": int(tr.n_trips), "sim_steps": steps,
-                   "sets": 5, "windows": W},
+                   "sets": 5, "windows": W, "speed_sigma_frac": args.sigma_frac},
         "seconds_per_iteration": {"batched_5_copies": t_batched, "sequential_5_runs": t_seq},
         "hidden": hidden, "start": theta0,
         "objective_mph": [h["objective"] * mph for h in res["history"]],
@@ -846,6 +848,8 @@ def main():
                     choices=["metro", "ensemble", "calibrate", "redgreen", "search", "stress"])
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--calib-iters", type=int, default=6, help="gradient steps of --workload calibrate")
+    ap.add_argument("--sigma-frac", type=float, default=0.05,
+                    help="per-driver speed limits of --workload search: sigma_s / speed limit (Section IV-B)")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: 07:30-08:00 trips, 1200-step warm-up launch, then --steps launches")
     ap.add_argument("--profile-peak", action="store_true",

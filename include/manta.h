@@ -85,6 +85,13 @@ typedef struct {
   int32_t idm_textbook;     /* 0: Eq. 1 as printed; 1: s* = s0 + max(0, vT + v dv / 2 sqrt(ab)) */
   int64_t t0_step;          /* absolute step index of the first manta_step (t = t0_step * dt)   */
   uint64_t seed;            /* seed of the counter-based random numbers (Eqs. 2-4)              */
+  float speed_sigma_frac;   /* Section IV-B per-driver speed limits: sigma_s / s, the spread of
+                               observed speeds at speed limit s as a fraction of s (the paper
+                               takes sigma_s from Uber data; this is its synthetic stand-in).
+                               A driver's limit on the edge of route entry r is
+                               s * max(0.25, 1 + 2 sigma_frac z), z the counter-based normal of
+                               (seed, trip id, r, stream 4); v0 = that limit x v0f[class].
+                               0 (the default): every driver uses the edge's limit.  0..1.    */
 } manta_config;
 
 typedef struct {

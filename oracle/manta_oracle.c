@@ -66,6 +66,7 @@ typedef struct {
   int32_t idm_textbook;
   int64_t t0_step;
   uint64_t seed;
+  float speed_sigma_frac;
 } oracle_config;
 
 typedef struct {
@@ -171,6 +172,22 @@ static int is_green(const osim *S, int32_t e, int64_t k) {
 
 /* Incident lane closure: lane l of edge e is closed at step k; from mid-edge
  * (cell C_e / 2) on it holds a stationary obstacle. */
+/* Section IV-B: a driver's own speed limit on the edge of route entry r.  The
+ * paper samples each driver's maximum speed per edge from a normal law around
+ * the edge's limit s with standard deviation 2 sigma_s; here sigma_s is
+ * speed_sigma_frac x s (the paper's sigma_s comes from Uber data), the
+ * normal draw is stream 4 of the trip's numbers keyed by r, and the result is
+ * floored at s / 4.  With speed_sigma_frac = 0 every driver uses s.        */
+static float driver_limit(const osim *S, int32_t e, int64_t id, int64_t r) {
+  const float s = S->lim[e];
+  const float f = S->cfg.speed_sigma_frac;
+  if (!(f > 0.0f)) return s;
+  const float z = rng_n(S->cfg.seed, (uint64_t)id, r, 4);
+  float q = 1.0f + (2.0f * f) * z;
+  if (q < 0.25f) q = 0.25f;
+  return s * q;
+}
+
 static int lane_closed(const osim *S, int32_t e, int32_t l, int64_t k) {
   int64_t g = S->lane_base[e] + l;
   return S->clo_k0[g] <= k && k < S->clo_k1[g];
@@ -220,6 +237,9 @@ OR_API osim *oracle_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge
       set_err(err, errlen, "bad class parameters"); oracle_destroy(S); return NULL;
     }
     if (cfg->s0[c] > s0max) s0max = cfg->s0[c];
+  }
+  if (!(cfg->speed_sigma_frac >= 0.0f) || !(cfg->speed_sigma_frac <= 1.0f)) {
+    set_err(err, errlen, "speed_sigma_frac out of range"); oracle_destroy(S); return NULL;
   }
   const int32_t cmin = L + (int32_t)ceilf(s0max) + 1;
   for (int32_t n = 0; n < N; ++n) {
@@ -636,7 +656,8 @@ OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
       const int32_t cell = (int32_t)floorf(x);
       scan_t sc = leader_scan(S, id);
       const float a = cf->a[p], b = cf->b[p], T = cf->T[p], s0 = cf->s0[p];
-      const float v0 = S->lim[e] * cf->v0f[p];
+      const float lim = driver_limit(S, e, id, V->r);
+      const float v0 = lim * cf->v0f[p];
       float xn, vn;
       int stop_in_place = 0;
       float acc = 0.0f;
@@ -691,7 +712,7 @@ OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
         S->tp_x[ti] = x; S->tp_v[ti] = v;
         S->tp_s[ti] = sc.kind == SC_FREE ? 0.0f : (float)(sc.cL - cell - L);
         S->tp_vL[ti] = sc.kind == SC_FREE ? 0.0f : sc.vL;
-        S->tp_bnd[ti] = t_bnd; S->tp_lim[ti] = S->lim[e]; S->tp_C[ti] = Ce;
+        S->tp_bnd[ti] = t_bnd; S->tp_lim[ti] = lim; S->tp_C[ti] = Ce;
         S->tp_flags[ti] = 1 | (kind << 1) | (t_ball << 3) | (t_clamp << 4) | ((int32_t)S->cls[e] << 9);
         S->tp_sample[ti] = -1;
       }

@@ -38,7 +38,7 @@ class OracleConfig(C.Structure):
                 ("stop_dwell_steps", C.c_int32), ("stop_v_eps", C.c_float),
                 ("stats_window_steps", C.c_int32), ("n_stats_windows", C.c_int32),
                 ("idm_textbook", C.c_int32),
-                ("t0_step", C.c_int64), ("seed", C.c_uint64)]
+                ("t0_step", C.c_int64), ("seed", C.c_uint64), ("speed_sigma_frac", C.c_float)]
 
 
 class OracleStats(C.Structure):
@@ -56,7 +56,8 @@ DEFAULTS = dict(dt=0.5, cell_m=1.0, veh_len_cells=5, horizon_cells=256, n_classe
                 v0f=[1.0] * 8, T=[1.5] * 8, a=[1.0] * 8, b=[2.0] * 8, s0=[2.0] * 8,
                 lc_x0_m=1.0, lc_len_scale_m=1.0, alpha_lo=0.05, alpha_hi=0.40,
                 g_low=3.0, g_high=7.5, g_speed_split=11.176, stop_dwell_steps=4, stop_v_eps=0.1,
-                stats_window_steps=600, n_stats_windows=96, idm_textbook=0, t0_step=0, seed=1)
+                stats_window_steps=600, n_stats_windows=96, idm_textbook=0, t0_step=0, seed=1,
+                speed_sigma_frac=0.0)
 
 
 def make_config(**over) -> OracleConfig:

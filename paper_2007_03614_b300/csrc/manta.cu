@@ -197,6 +197,8 @@ manta_status check_cfg(const manta_config *c) {
   if (c->stats_window_steps < 1 || c->n_stats_windows < 1) return fail(MANTA_E_INVALID, "bad statistics windows");
   if (c->t0_step < 0 || c->t0_step > (int64_t)1 << 40) return fail(MANTA_E_INVALID, "t0_step out of range");
   if (!(c->lc_len_scale_m > 0.0f)) return fail(MANTA_E_INVALID, "lc_len_scale_m must be > 0");
+  if (!(c->speed_sigma_frac >= 0.0f) || !(c->speed_sigma_frac <= 1.0f))
+    return fail(MANTA_E_INVALID, "speed_sigma_frac out of range");
   return MANTA_OK;
 }
 
@@ -229,6 +231,7 @@ void manta_default_config(manta_config *c) {
   c->idm_textbook = 0;
   c->t0_step = 0;
   c->seed = 1;
+  c->speed_sigma_frac = 0.0f;
 }
 
 const char *manta_last_error(void) { return g_err.c_str(); }
@@ -443,7 +446,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   P.alpha_lo = cfg->alpha_lo; P.alpha_hi = cfg->alpha_hi; P.g_low = cfg->g_low; P.g_high = cfg->g_high;
   P.g_split = cfg->g_speed_split; P.stop_eps = cfg->stop_v_eps; P.stop_dwell = cfg->stop_dwell_steps;
   P.win_steps = cfg->stats_window_steps; P.n_win = cfg->n_stats_windows; P.textbook = cfg->idm_textbook;
-  P.t0 = cfg->t0_step; P.seed = cfg->seed;
+  P.t0 = cfg->t0_step; P.seed = cfg->seed; P.sigma_frac = cfg->speed_sigma_frac;
   P.E = (uint32_t)E; P.N = (uint32_t)N; P.n_stop = (uint32_t)stops.size(); P.mtab_n = (uint32_t)mtab.size();
   P.wait_limit_ns = kWaitLimitNs;
   S->k = cfg->t0_step;

@@ -174,6 +174,7 @@ struct Params {
   int32_t stop_dwell, win_steps, n_win, textbook;
   int64_t t0;
   uint64_t seed;
+  float sigma_frac;            // per-driver speed limits (Section IV-B); 0: off
   uint32_t E, N, n_stop, n_trips, mtab_n;
   // launch
   int64_t k0;

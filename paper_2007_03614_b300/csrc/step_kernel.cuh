@@ -131,6 +131,17 @@ __device__ __forceinline__ float irwin_hall(uint64_t seed, uint32_t id, int64_t 
   return __int2float_rn(acc - 100663296) * 5.9604644775390625e-8f;
 }
 
+// A driver's own speed limit on the edge of route entry r (Section IV-B): the
+// edge's limit s perturbed by 2 sigma_s z with sigma_s = sigma_frac x s and z
+// the counter-based normal of (seed, trip id, r, stream 4), floored at s / 4.
+// Drawn once when the vehicle enters the edge and kept in its record.
+__device__ __forceinline__ float driver_limit(const Params &p, float s, uint32_t id, uint32_t r) {
+  if (!(p.sigma_frac > 0.0f)) return s;
+  const float z = irwin_hall(p.seed, id, (int64_t)r, 4);
+  const float q = fmaxf(0.25f, 1.0f + (2.0f * p.sigma_frac) * z);
+  return s * q;
+}
+
 // ---------------------------------------------------------------- records
 __device__ __forceinline__ uint32_t cells_of(uint32_t cnl) { return cnl & 0xFFFFFFu; }
 __device__ __forceinline__ int lanes_of(uint32_t cnl) { return (int)((cnl >> 24) & 0xFu); }
@@ -1283,6 +1294,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           w.e = e2; w.rc = w.rc + 1u;
           w.ld = ld_for_entry(p, w.rc, l2);
           w.em = em2;
+          w.em.lim = driver_limit(p, em2.lim, w.id, w.rc);
           nxt[em2.row0 + l2 * stride_of(cells_of(em2.cnl)) + (uint32_t)(int)floorf(xf)] = speed_code(vf);
           ef = e2;
         } else {
@@ -1346,6 +1358,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           Veh w;
           w.x = 0.0f; w.v = 0.0f; w.id = j; w.rc = rc; w.rend = rend;
           w.e = e; w.ld = ld0; w.pcell = MANTA_NONE; w.em = em;
+          w.em.lim = driver_limit(p, em.lim, j, rc);
           store_veh(p, s, w);
           act[ia] = s;
           nxt[em.row0] = speed_code(0.0f);

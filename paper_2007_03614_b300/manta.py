@@ -30,7 +30,7 @@ class MantaConfig(C.Structure):
                 ("stop_dwell_steps", C.c_int32), ("stop_v_eps", C.c_float),
                 ("stats_window_steps", C.c_int32), ("n_stats_windows", C.c_int32),
                 ("idm_textbook", C.c_int32),
-                ("t0_step", C.c_int64), ("seed", C.c_uint64)]
+                ("t0_step", C.c_int64), ("seed", C.c_uint64), ("speed_sigma_frac", C.c_float)]
 
 
 class MantaStats(C.Structure):

@@ -44,6 +44,20 @@ class Veh:
 
 
 class Naive:
+    def driver_limit(self, v):
+        """Section IV-B: the driver's own limit on its current edge, s (1 + 2 f z)
+        floored at s / 4, z the normal draw of stream 4 keyed by the global
+        route entry; the edge's limit s when f = 0."""
+        s = self.lim[v.e]
+        f = F(self.cfg.get("speed_sigma_frac", 0.0))
+        if not f > F(0.0):
+            return s
+        z = _n(self.cfg["seed"], v.id, self.roff[v.id] + v.r, 4)
+        q = F(1.0) + (F(2.0) * f) * z
+        if q < F(0.25):
+            q = F(0.25)
+        return s * q
+
     def __init__(self, net, tr, cfg):
         self.cfg = cfg
         L = cfg["veh_len_cells"]
@@ -75,6 +89,7 @@ class Naive:
         self.closures = {}                      # (edge, lane) -> (k0, k1)
         self.permit = {n: None for n in range(len(self.ntype))}
         self.rr = {n: 0 for n in range(len(self.ntype))}
+        self.roff = list(map(int, tr.route_off))
         self.routes = [list(map(int, tr.route_edges[tr.route_off[i]:tr.route_off[i + 1]]))
                        for i in range(len(tr.depart_time_s))]
         self.dstep = [math.ceil(float(t) / float(cfg["dt"])) for t in tr.depart_time_s]
@@ -307,7 +322,7 @@ class Naive:
             e = v.e
             p = self.cls[e]
             a, b, T, s0 = F(c["a"][p]), F(c["b"][p]), F(c["T"][p]), F(c["s0"][p])
-            v0 = self.lim[e] * F(c["v0f"][p])
+            v0 = self.driver_limit(v) * F(c["v0f"][p])
             cell = self.cell(v)
             ld = self.leader(v, k)
             r1 = v.v / v0

@@ -48,9 +48,9 @@ def test_config_layout_matches_header(lib):
 #include <stddef.h>
 #include "manta.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(manta_config), offsetof(manta_config, lc_x0_m),
-         offsetof(manta_config, t0_step), offsetof(manta_config, seed), sizeof(manta_stats_t),
-         offsetof(manta_stats_t, route_reads));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(manta_config), offsetof(manta_config, lc_x0_m),
+         offsetof(manta_config, t0_step), offsetof(manta_config, seed), offsetof(manta_config, speed_sigma_frac),
+         sizeof(manta_stats_t), offsetof(manta_stats_t, route_reads));
   return 0;
 }
 '''
@@ -61,8 +61,8 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, c])
         vals = list(map(int, subprocess.check_output([exe]).split()))
     M, S = manta.MantaConfig, manta.MantaStats
-    assert vals == [C.sizeof(M), M.lc_x0_m.offset, M.t0_step.offset, M.seed.offset, C.sizeof(S),
-                    S.route_reads.offset]
+    assert vals == [C.sizeof(M), M.lc_x0_m.offset, M.t0_step.offset, M.seed.offset, M.speed_sigma_frac.offset,
+                    C.sizeof(S), S.route_reads.offset]
 
 
 def test_default_config(lib):
@@ -70,6 +70,7 @@ def test_default_config(lib):
     assert c.dt == 0.5 and c.cell_m == 1.0 and c.veh_len_cells == 5 and c.horizon_cells == 256
     assert abs(c.alpha_lo - 0.05) < 1e-7 and abs(c.alpha_hi - 0.40) < 1e-7 and c.lc_x0_m == 1.0
     assert c.stop_dwell_steps == 4 and c.stats_window_steps == 600 and c.idm_textbook == 0
+    assert c.speed_sigma_frac == 0.0
 
 
 def _create(net, **cfg):
@@ -88,7 +89,8 @@ def _create(net, **cfg):
 @pytest.mark.parametrize("over,frag", [
     (dict(cell_m=2.0), "cell_m"), (dict(dt=0.0), "dt"), (dict(horizon_cells=4), "horizon"),
     (dict(n_classes=0), "n_classes"), (dict(a=[0.0] * 8), "class"), (dict(stop_dwell_steps=0), "stop_dwell"),
-    (dict(t0_step=-1), "t0_step")])
+    (dict(t0_step=-1), "t0_step"), (dict(speed_sigma_frac=-0.1), "speed_sigma_frac"),
+    (dict(speed_sigma_frac=1.5), "speed_sigma_frac"), (dict(speed_sigma_frac=float("nan")), "speed_sigma_frac")])
 def test_create_rejects_bad_config(lib, over, frag):
     rc, msg = _create(nets.line(2), **over)
     assert rc == manta.E_INVALID and frag in msg

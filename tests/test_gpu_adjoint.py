@@ -64,14 +64,15 @@ def test_checkpoint_restore_is_bit_exact():
     g.close()
 
 
-@pytest.fixture(scope="module")
-def taped():
+@pytest.fixture(scope="module", params=[0.0, 0.1], ids=["edge-limits", "per-driver-limits"])
+def taped(request):
     """The same 600-step run (calibration grid, 1500 trips, 1-minute windows)
-    with its event tape, on the oracle and on the GPU."""
+    with its event tape, on the oracle and on the GPU; once with every driver
+    at the edge's speed limit, once with per-driver limits (Section IV-B)."""
     import torch
     net = synth.calib_network()
     tr = synth.calib_trips(net, n_trips=1500)
-    cfg = dict(stats_window_steps=120, n_stats_windows=5)
+    cfg = dict(stats_window_steps=120, n_stats_windows=5, speed_sigma_frac=request.param)
     o = O.OracleSim(net, **cfg)
     nets.load(o, tr)
     ot = o.record_tape(600)

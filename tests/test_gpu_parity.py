@@ -78,6 +78,28 @@ def test_tiny_workload_bit_exact():
     assert st["arrived"] == 1000 and st["on_network"] == 0
 
 
+def test_per_driver_speed_limits_bit_exact():
+    """Section IV-B per-driver speed limits (speed_sigma_frac = 0.1) on the tiny
+    workload: bit for bit equal to the oracle, and a different run from the one
+    with every driver at the edge's limit."""
+    net = synth.tiny_network()
+    tr = synth.tiny_trips(net)
+    o, g = _pair(net, tr, speed_sigma_frac=0.1)
+    g0 = manta.Sim(net)
+    nets.load(g0, tr)
+    for k in range(0, 1800, 50):
+        o.step(50)
+        g.step(50)
+        _compare(o, g, f"step {k + 50}")
+        if k + 50 == 600:         # mid-run, with the network busy
+            g0.step(600)
+            a, b = g0.snapshot(), g.snapshot()
+            assert len(a["id"]) > 100
+            assert not (np.array_equal(a["id"], b["id"]) and np.array_equal(a["x"], b["x"]))
+    _compare_all(o, g, windows=range(3))
+    g0.close()
+
+
 def test_tiny_all_stop_signs_bit_exact():
     """Red-light case of Section IV-C: every node a flashing red (stop + permit)."""
     net = synth.lattice(10, 10, arterial_every=1, len_median_m=100.0, len_sigma=0.0, len_min_m=100.0,
@@ -93,7 +115,7 @@ def test_tiny_all_stop_signs_bit_exact():
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])
-@pytest.mark.parametrize("ci", [0, 1, 2])
+@pytest.mark.parametrize("ci", [0, 1, 2, 3])
 def test_small_mixed_networks_every_step(seed, ci):
     """Random-walk routes on a 3x3 lattice with stop, signal and green nodes:
     every step compared (merges, queues, permits, lane changes)."""

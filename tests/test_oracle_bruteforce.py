@@ -37,7 +37,8 @@ def _scenario(seed, n_trips=20, nx=3, ny=3):
     return net, tr
 
 
-CFGS = [dict(), dict(lc_len_scale_m=100.0), dict(idm_textbook=1, lc_len_scale_m=30.0, s0=[1.0, 3.5, 2.0])]
+CFGS = [dict(), dict(lc_len_scale_m=100.0), dict(idm_textbook=1, lc_len_scale_m=30.0, s0=[1.0, 3.5, 2.0]),
+        dict(speed_sigma_frac=0.15)]
 
 
 def closures_for(net, seed):

@@ -40,6 +40,59 @@ def test_uniform_and_irwin_hall_moments():
     assert O.rng_u(7, 5, 3, 0) != O.rng_u(7, 5, 4, 0)
 
 
+def test_per_driver_speed_limits():
+    """Section IV-B: every driver draws its own maximum speed on each edge it
+    enters, around the edge's limit s with standard deviation 2 sigma_s (here
+    sigma_s = f s).  Over many (driver, edge) pairs the drawn limits have mean
+    s and standard deviation 2 f s; a driver keeps its limit for the whole
+    edge and draws again on the next; with f = 0 every driver has s."""
+    n_edges, s_lim, f = 6, 20.0, 0.1
+    lengths = [300.0 + 37.0 * i for i in range(n_edges)]      # distinct lengths: the cell count names the edge
+    net = nets.network(n_edges + 1, [(i, i + 1, 1, lengths[i], s_lim, 0) for i in range(n_edges)])
+    n_trips = 500
+    tr = nets.trips([list(range(n_edges))] * n_trips, [2.0 * i for i in range(n_trips)])
+    for frac in (0.0, f):
+        o = O.OracleSim(net, speed_sigma_frac=frac)
+        nets.load(o, tr)
+        tape = o.record_tape(2400)
+        o.step(2400)
+        present = (tape["flags"] & 1) != 0
+        t_idx, ids = np.nonzero(present)
+        lim = tape["lim"][t_idx, ids].astype(np.float64)
+        cells = tape["C"][t_idx, ids]
+        if frac == 0.0:
+            assert np.all(lim == s_lim)
+            continue
+        groups = {}
+        for i, c, l in zip(ids.tolist(), cells.tolist(), lim.tolist()):
+            groups.setdefault((i, c), set()).add(l)
+        assert all(len(v) == 1 for v in groups.values())          # constant along the edge
+        per = np.array([next(iter(v)) for v in groups.values()])
+        assert len(per) > 1500
+        z = (per / s_lim - 1.0) / (2.0 * f)
+        assert abs(z.mean()) < 0.1 and abs(z.std() - 1.0) < 0.07
+        assert len(np.unique(per)) > 0.95 * len(per)                # drivers and edges draw apart
+        by_driver = {}
+        for (i, c), v in groups.items():
+            by_driver.setdefault(i, set()).update(v)
+        assert sum(len(v) > 1 for v in by_driver.values()) > 0.9 * len(by_driver)
+
+
+def test_lone_driver_settles_at_its_own_limit():
+    """With no leader the fixed point of Eq. 1 is v = v0: a lone driver on a long
+    free road ends at its own drawn limit (times v0f = 1), not the edge's."""
+    net = nets.line(1, length=8000.0, speed=20.0)
+    tr = nets.trips([[0]], [0.0])
+    o = O.OracleSim(net, speed_sigma_frac=0.1, seed=5)
+    nets.load(o, tr)
+    tape = o.record_tape(700)
+    o.step(700)
+    lim = float(tape["lim"][-1, 0])
+    v = float(o.snapshot()["v"][0])
+    assert lim != 20.0
+    assert abs(v - lim) <= 1e-4 * lim
+
+
 def test_defaults_match_paper_constants():
     rows = {}
     for line in open(os.path.join(HERE, "golden", "paper_constants.txt")):
