@@ -270,23 +270,17 @@ __device__ __forceinline__ void slot_fetch(uint32_t slot, const uint8_t *g, int 
 // First occupied cell in [lo, hi] among the n chunks of a slot whose chunk 0
 // starts at row cell c (lo lies in chunk 0), or -1; the speed code in byte.
 __device__ __forceinline__ int check_slot(const uint8_t *slot, int n, int c, int lo, int hi, uint32_t &byte) {
-  for (int j = 0; j < n; ++j) {
-    const uint4 q = *reinterpret_cast<const uint4 *>(slot + 16 * j);
-    uint32_t w[4] = {q.x, q.y, q.z, q.w};
-    if (j == 0) {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int d = lo - (c + 4 * t);
-        w[t] |= d <= 0 ? 0u : (d >= 4 ? 0xFFFFFFFFu : ((1u << (8 * d)) - 1u));
-      }
-    }
-    if ((w[0] & w[1] & w[2] & w[3]) == 0xFFFFFFFFu) continue;
-    const int t = w[0] != 0xFFFFFFFFu ? 0 : (w[1] != 0xFFFFFFFFu ? 1 : (w[2] != 0xFFFFFFFFu ? 2 : 3));
-    const uint32_t a = t == 0 ? w[0] : (t == 1 ? w[1] : (t == 2 ? w[2] : w[3]));
-    const int bpos = (__ffs(occupied_bits(a)) - 1) >> 3;
-    const int first = c + 16 * j + 4 * t + bpos;
-    byte = (a >> (8 * bpos)) & 0xFFu;
-    return first > hi ? -1 : first;
+  // four chunks per pass, loaded together and tested branch-free
+  const uint4 none = make_uint4(~0u, ~0u, ~0u, ~0u);
+  const uint4 *q = reinterpret_cast<const uint4 *>(slot);
+  for (int j = 0; j < n; j += 4) {
+    Batch b;
+    b.q[0] = q[j];
+    b.q[1] = j + 1 < n ? q[j + 1] : none;
+    b.q[2] = j + 2 < n ? q[j + 2] : none;
+    b.q[3] = j + 3 < n ? q[j + 3] : none;
+    const int r = check_batch(b, c + 16 * j, lo, hi, byte);
+    if (r >= 0) return r;
   }
   return -1;
 }
