@@ -344,14 +344,18 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
       S->conn[j] = m;
     }
   }
-  // in-lanes of every node in (edge id, lane) order; stop-node list
-  std::vector<uint32_t> nin_off(N + 1, 0), nin(lanes_total);
+  // request and stop-line slots numbered node by node: the in-lanes of node n
+  // are slots [nin_off[n], nin_off[n + 1]) in (edge id, lane) order, and lane
+  // l of edge e is slot rslot[e] + l; stop-node list
+  std::vector<uint32_t> nin_off(N + 1, 0), rslot(E);
   for (int32_t e = 0; e < E; ++e) nin_off[edge_dst[e] + 1] += S->lanes[e];
   for (int32_t n = 0; n < N; ++n) nin_off[n + 1] += nin_off[n];
   {
     std::vector<uint32_t> f(nin_off.begin(), nin_off.end() - 1);
-    for (int32_t e = 0; e < E; ++e)
-      for (uint32_t l = 0; l < S->lanes[e]; ++l) nin[f[edge_dst[e]]++] = S->lane_base[e] + l;
+    for (int32_t e = 0; e < E; ++e) {
+      rslot[e] = f[edge_dst[e]];
+      f[edge_dst[e]] += S->lanes[e];
+    }
   }
   std::vector<uint32_t> stops;
   for (int32_t n = 0; n < N; ++n)
@@ -380,7 +384,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   uint2 *d_src_in = dalloc<uint2>(S, E, &ok);
   uint32_t *d_lb = dalloc<uint32_t>(S, E, &ok);
   uint32_t *d_nin_off = dalloc<uint32_t>(S, N + 1, &ok);
-  uint32_t *d_nin = dalloc<uint32_t>(S, lanes_total, &ok);
+  uint32_t *d_rslot = dalloc<uint32_t>(S, E, &ok);
   uint32_t *d_stops = dalloc<uint32_t>(S, stops.size(), &ok);
   float *d_mtab = dalloc<float>(S, mtab.size(), &ok);
   // kMapPad padding bytes: a first scan batch may run past the last row
@@ -405,7 +409,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   if (!ok) { manta_destroy(S); return fail(MANTA_E_OOM, "device allocation failed in manta_create"); }
   bool cp = upload(S, d_em, em) && upload(S, d_es, es) && upload(S, d_nt, ntype) && upload(S, d_esrc, esrc_u) &&
             upload(S, d_src_in, src_in) &&
-            upload(S, d_lb, lane_base_e) && upload(S, d_nin_off, nin_off) && upload(S, d_nin, nin) &&
+            upload(S, d_lb, lane_base_e) && upload(S, d_nin_off, nin_off) && upload(S, d_rslot, rslot) &&
             upload(S, d_stops, stops) && upload(S, d_mtab, mtab);
   cp = cp && cudaMemsetAsync(P.atlas0, 0xFF, bytes + kMapPad, S->stream) == cudaSuccess &&
        cudaMemsetAsync(P.atlas1, 0xFF, bytes + kMapPad, S->stream) == cudaSuccess &&
@@ -437,7 +441,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   }
   P.clo_k0 = d_ck0; P.clo_k1 = d_ck1;
   P.em = d_em; P.es = d_es; P.ntype = d_nt; P.esrc = d_esrc; P.src_in = d_src_in; P.lane_base = d_lb;
-  P.nin_off = d_nin_off; P.nin = d_nin; P.stop_nodes = d_stops; P.mtab = d_mtab;
+  P.nin_off = d_nin_off; P.rslot = d_rslot; P.stop_nodes = d_stops; P.mtab = d_mtab;
   P.dt = cfg->dt; P.L = cfg->veh_len_cells; P.H = cfg->horizon_cells;
   for (int i = 0; i < 8; ++i) {
     P.T[i] = cfg->T[i]; P.a[i] = cfg->a[i]; P.b[i] = cfg->b[i]; P.s0[i] = cfg->s0[i]; P.v0f[i] = cfg->v0f[i];

@@ -122,10 +122,11 @@ struct Params {
   const EdgeSig *es;
   const uint8_t *ntype;
   const uint32_t *esrc;        // tail node of each edge
-  const uint2 *src_in;         // in-lane range [x, y) in nin of each edge's tail node
+  const uint2 *src_in;         // in-lane slot range [x, y) of each edge's tail node
   const uint32_t *lane_base;   // first global lane index of each edge
-  const uint32_t *nin_off;     // in-lanes (global lane ids) of each node, (edge, lane) order
-  const uint32_t *nin;
+  const uint32_t *nin_off;     // each node's in-lane slots [nin_off[n], nin_off[n + 1]), (edge, lane) order
+  const uint32_t *rslot;       // slot of lane 0 of each edge among its head node's in-lanes: the
+                               // request and stop-line slots of lane l are rslot[e] + l
   const uint32_t *stop_nodes;
   const float *mtab;           // Eq. 2 probability by distance in cells
   const long long *clo_k0;     // closure window [k0, k1) of each lane (empty when k0 >= k1)

@@ -485,22 +485,21 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
 __device__ __forceinline__ uint32_t target_key(uint32_t e, uint32_t l) { return (e << 4) | l; }
 
 // Lowest id among the other crossing requests for target lane key `tgt`
-// posted this step (tag) by the in-lanes [o0, o1) of a node, excluding lane
-// `skip`; MANTA_NONE if there is none.  Eight in-lanes per round trip.
+// posted this step (tag) by the in-lanes of a node, whose request slots are
+// [o0, o1) (slots are numbered node by node), excluding slot `skip`;
+// MANTA_NONE if there is none.  Eight in-lanes per round trip.
 __device__ __forceinline__ uint32_t min_competitor(const Params &p, uint32_t o0, uint32_t o1, uint32_t skip,
                                                    uint32_t tgt, uint32_t tag) {
   uint32_t best = MANTA_NONE;
   for (uint32_t o = o0; o < o1; o += 8u) {
-    uint32_t g[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) g[j] = (o + j < o1) ? __ldg(p.nin + o + j) : MANTA_NONE;
     unsigned long long key[8];
     uint32_t tg[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const bool use = g[j] != MANTA_NONE && g[j] != skip;
-      key[j] = use ? __ldcg(p.req_key + g[j]) : 0ull;
-      tg[j] = use ? __ldcg(p.req_tgt + g[j]) : MANTA_NONE;
+      const uint32_t g = o + (uint32_t)j;
+      const bool use = g < o1 && g != skip;
+      key[j] = use ? __ldcg(p.req_key + g) : 0ull;
+      tg[j] = use ? __ldcg(p.req_tgt + g) : MANTA_NONE;
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j)
@@ -887,7 +886,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       const uint32_t r0 = ldv(p.rr + n);
       for (uint32_t t = 0; t < m; ++t) {
         const uint32_t idx = (r0 + t) % m;
-        const uint32_t g = __ldg(p.nin + o + idx);
+        const uint32_t g = o + idx;      // the node's in-lane slots are consecutive
         const uint32_t td = ldv(p.slot_td + g);
         if ((td >> 8) == (uint32_t)(k & 0xFFFFFF) && (td & 0xFFu) >= (uint32_t)p.stop_dwell) {
           p.permit[n] = ldv(p.slot_id + g);
@@ -1199,7 +1198,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         cp_async_wait_all();
         bool fin = false;
         if (st == 1) {
-          lb = __ldg(p.lane_base + w.e);      // needed when the vehicle is done
+          lb = __ldg(p.rslot + w.e);          // request / stop-line slots, needed when the vehicle is done
           cell = (int)floorf(w.x);
           fin = walk_start(p, cur, k, w, cell, wk, sc, c_scan);
           st = 2;
