@@ -154,6 +154,8 @@ struct Params {
   uint32_t *req_dw, *req_g, *req_t, *req_e2, *req_n;
   // departure queues
   uint32_t *pending, *q_pos;
+  uint32_t *dep_info;          // per departure-list entry of the step: edge, head trip or none,
+                               // competitors' slot range (4 words, written in P3, read in P4)
   unsigned long long *dep_key;
   // per-lane request and stop-line slots
   unsigned long long *req_key;

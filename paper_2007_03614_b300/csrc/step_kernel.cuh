@@ -930,14 +930,21 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       // the edge record, and the head's trip id with the entry cells
       const EdgeMeta em = load_em(p, e);
       const uint32_t lb = __ldg(p.lane_base + e);
+      const uint2 rg = __ldg(p.src_in + e);
       const uint32_t qh = __ldg(p.q_off + e) + __ldcg(p.q_pos + e);
       const uint32_t j = __ldg(p.q_trip + qh);
       const int C = (int)cells_of(em.cnl);
       const int need = min(C, L + p.s0c[class_of(em.cnl)]);
-      if (closable(em) && lane_closed(p, lb, k)) continue;
-      uint32_t byte;
-      if (first_up(cur + em.row0, 0, need - 1, byte) >= 0) continue;
-      p.dep_key[e] = ((unsigned long long)tag << 32) | j;
+      bool req = !(closable(em) && lane_closed(p, lb, k));
+      if (req) {
+        uint32_t byte;
+        req = first_up(cur + em.row0, 0, need - 1, byte) < 0;
+      }
+      if (req) p.dep_key[e] = ((unsigned long long)tag << 32) | j;
+      // what P4 needs of this departure in one entry: the edge, the queue
+      // head's trip (none when it does not request entry) and the slot range
+      // of its competitors, the in-lanes of the edge's tail node
+      reinterpret_cast<uint4 *>(p.dep_info)[i] = make_uint4(e, req ? j : MANTA_NONE, rg.x, rg.y);
     }
     // vehicles
     const int64_t kr = k - p.t0;
@@ -1263,10 +1270,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         const uint32_t s = __ldcg(p.req + i);
         const uint32_t gown = __ldcg(p.req_g + i), tgt = __ldcg(p.req_t + i);
         const uint32_t e2 = __ldcg(p.req_e2 + i), n = __ldcg(p.req_n + i);
+        const float rx = __ldcg(p.req_x + i), rv = __ldcg(p.req_v + i);
         const uint32_t o0 = __ldg(p.nin_off + n), o1 = __ldg(p.nin_off + n + 1);
         const unsigned long long dk = __ldcg(p.dep_key + e2);
         const EdgeMeta em2 = load_em(p, e2);
         Veh w = load_veh(p, s);
+        const uint32_t ld2 = ld_for_entry(p, w.rc + 1u, tgt & 15u);   // with the competitors' slots
         const int lane = ld_lane(w.ld);
         const EdgeMeta em = w.em;
         const uint32_t stride = stride_of(cells_of(em.cnl));
@@ -1281,11 +1290,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           if (__ldg(p.ntype + n) == 1 && ldv(p.permit + n) == w.id) p.permit[n] = MANTA_NONE;
           atomicAdd(p.exitc + w.e, 1u);
           atomicAdd(p.entry + e2, 1u);
-          xf = __ldcg(p.req_x + i) - __int2float_rn(C);
-          vf = __ldcg(p.req_v + i);
+          xf = rx - __int2float_rn(C);
+          vf = rv;
           const uint32_t l2 = tgt & 15u;
           w.e = e2; w.rc = w.rc + 1u;
-          w.ld = ld_for_entry(p, w.rc, l2);
+          w.ld = ld2;
           w.em = em2;
           w.em.lim = driver_limit(p, em2.lim, w.id, w.rc);
           nxt[em2.row0 + l2 * stride_of(cells_of(em2.cnl)) + (uint32_t)(int)floorf(xf)] = speed_code(vf);
@@ -1317,23 +1326,21 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         }
       } else if (t < t_arr) {
         const uint32_t i = t - t_dep;
-        // round trip 1: the edge; 2: everything keyed by the edge; 3: the
-        // competitors' slots and the head trip's route; 4: their requests;
-        // 5: the winner's three counter updates together; 6: its slot and its
-        // departure-list position together
-        const uint32_t e = __ldcg(dep + i);
-        const unsigned long long dk = __ldcg(p.dep_key + e);
-        const uint2 rg = __ldg(p.src_in + e);
+        // round trip 1: the entry P3 wrote (edge, head trip, competitors'
+        // slot range); 2: the competitors' requests, the edge record and the
+        // trip's route; 3: the winner's three counter updates together; 4: its
+        // slot and its departure-list position together
+        const uint4 di = __ldcg(reinterpret_cast<const uint4 *>(p.dep_info) + i);
+        const uint32_t e = di.x, j = di.y;
+        bool won = j != MANTA_NONE;
         const EdgeMeta em = load_em(p, e);
         const uint32_t qp = __ldcg(p.q_pos + e);
-        const uint32_t j = (uint32_t)dk;
-        bool won = (uint32_t)(dk >> 32) == tag;
         uint32_t rc = 0u, rend = 0u, ld0 = 0u;
         if (won) {
           rc = __ldg(p.route_off + j);
           rend = __ldg(p.route_off + j + 1u);
           ld0 = ld_for_entry(p, rc, 0u);
-          won = min_competitor(p, rg.x, rg.y, MANTA_NONE, target_key(e, 0u), tag) > j;
+          won = min_competitor(p, di.z, di.w, MANTA_NONE, target_key(e, 0u), tag) > j;
         }
         // the results of these two atomics are first used after the list
         // append below, so the three round trips overlap
