@@ -1264,9 +1264,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     for (uint32_t t = gspr; t < t_end; t += gsz) {
       if (t < t_dep) {
         const uint32_t i = t;
-        // round trip 1: the request; 2: the records it names; 3: the
-        // competitors' slots and the route entry after the crossing; 4: their
-        // requests
+        // round trip 1: the request (with its position and speed); 2: the
+        // records it names and the node's slot range; 3: the competitors'
+        // requests (the node's slots are consecutive) and the route entry
+        // after the crossing
         const uint32_t s = __ldcg(p.req + i);
         const uint32_t gown = __ldcg(p.req_g + i), tgt = __ldcg(p.req_t + i);
         const uint32_t e2 = __ldcg(p.req_e2 + i), n = __ldcg(p.req_n + i);
