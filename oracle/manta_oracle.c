@@ -21,8 +21,10 @@
  *  C. Departure requests: queue heads due by step k whose entry cells on
  *     lane 0 are free in M_k'                        (Section II-D departures; Section II-D case 2 capacity)
  *  D. Leader scan along the route on M_k' (lane-map lookup of neighbouring
- *     cells), IDM acceleration (Eq. 1, delta = 4), ballistic "double
- *     integration" at dt, clamp behind the leader   (Section II-D, Eq. 1)
+ *     cells), IDM acceleration (Eq. 1, delta = 4) with the driver's own
+ *     speed limit on the edge (Section IV-B, off unless speed_sigma_frac > 0),
+ *     ballistic "double integration" at dt, clamp behind the leader
+ *                                                   (Section II-D, Eq. 1)
  *  E. Merge resolution: per target lane the lowest vehicle id among crossing
  *     and departure requests wins                      (Section II-D capacity rule)
  *  F. Apply outcomes: crossings, held vehicles, departures, arrivals
@@ -37,7 +39,8 @@
  * float64 replay; ring-road equilibrium vs the IDM steady-state relation;
  * conservation; no-overlap / per-lane FIFO; hand-traced merge, signal, stop
  * and lane-change cases; a naive list-based implementation on tiny
- * networks; SplitMix64 reference outputs.
+ * networks; SplitMix64 reference outputs; the moments of the per-driver
+ * limits and a lone driver's terminal speed.
  */
 #include <stdint.h>
 #include <stdlib.h>
