@@ -564,16 +564,20 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   P.act0 = dalloc<uint32_t>(S, NT, &ok); P.act1 = dalloc<uint32_t>(S, NT, &ok);
   P.freel = dalloc<uint32_t>(S, NT, &ok); P.lcm = dalloc<LcMove>(S, NT, &ok);
   P.p3a = dalloc<uint32_t>(S, NT, &ok);
-  // candidate regions: every warp may list one candidate per entry it visits,
-  // 32 entries per grid-stride block
-  size_t gmax = 0;
-  for (int v = 0; v < kNumVariants; ++v) gmax = std::max(gmax, (size_t)S->grid[v] * kVariants[v].threads);
-  const size_t NC = NT + gmax;
+  // candidate overflow regions, for every launch shape: at most NT list
+  // entries and NT + E merge-phase items (requests and departures) per step
+  size_t NC = 1;
+  for (int v = 0; v < kNumVariants; ++v) {
+    const uint32_t gsz = (uint32_t)S->grid[v] * (uint32_t)kVariants[v].threads;
+    NC = std::max(NC, (size_t)S->grid[v] * lc_overflow(kVariants[v].threads, gsz / 2u, gsz, (uint32_t)NT,
+                                                       (uint32_t)(NT + (size_t)S->E)));
+  }
   P.lcq = dalloc<Veh>(S, NC, &ok); P.lcq_pos = dalloc<uint32_t>(S, NC, &ok);
   P.req = dalloc<uint32_t>(S, NT, &ok); P.arr = dalloc<uint32_t>(S, NT, &ok);
   P.req_x = dalloc<float>(S, NT, &ok); P.req_v = dalloc<float>(S, NT, &ok); P.req_dw = dalloc<uint32_t>(S, NT, &ok);
   P.req_g = dalloc<uint32_t>(S, NT, &ok); P.req_t = dalloc<uint32_t>(S, NT, &ok);
   P.req_e2 = dalloc<uint32_t>(S, NT, &ok); P.req_n = dalloc<uint32_t>(S, NT, &ok);
+  P.req_pos = dalloc<uint32_t>(S, NT, &ok);
   if (!ok) return fail(MANTA_E_OOM, "device allocation failed in manta_load_trips");
   bool cp = upload(S, d_roff, roff) && upload(S, d_qoff, q_off) && upload(S, d_qtrip, order) &&
             upload(S, d_due, due_step) && upload(S, d_due_e, due_edge) && upload(S, d_out_off, h_out_off) &&
@@ -893,6 +897,8 @@ manta_status manta_snapshot(manta_sim *S, int64_t cap, int64_t *n_out, float *x,
   std::vector<uint32_t> act(len);
   if (cudaMemcpy(act.data(), c.act_sel[S->k & 1] ? P.act1 : P.act0, 4ull * len, cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(MANTA_E_CUDA, "copy of the active list failed");
+  for (uint32_t &a : act)
+    if (a != MANTA_NONE) a &= 0x7FFFFFFFu;   // a requester's mark (set for the kernel's next record pass)
   act.erase(std::remove(act.begin(), act.end(), MANTA_NONE), act.end());
   if ((int64_t)act.size() != live) return fail(MANTA_E_DEVICE, "active list and counters disagree");
   const uint32_t n = (uint32_t)live;

@@ -152,6 +152,7 @@ struct Params {
   uint32_t *lcq_pos;           // their active-list positions
   float *req_x, *req_v;
   uint32_t *req_dw, *req_g, *req_t, *req_e2, *req_n;
+  uint32_t *req_pos;           // active-list position of each requester
   // departure queues
   uint32_t *pending, *q_pos;
   uint32_t *dep_info;          // per departure-list entry of the step: edge, head trip or none,

@@ -42,7 +42,7 @@ constexpr int kBlock = 256;
 // fields of a finish-queue entry
 enum { kFqX, kFqV, kFqId, kFqRc, kFqRend, kFqE, kFqLd, kFqRow0, kFqCnl, kFqLim, kFqDst, kFqS, kFqI, kFqCell, kFqLb,
        kFqKind, kFqCL, kFqVL, kFqE2, kFqE2cnl, kFqFields };
-constexpr int kP3Words = 352 + kFqFields * 64;
+constexpr int kP3Words = 384 + kFqFields * 64;
 // Row batches of the main phase's leader walk land in a shared-memory slot
 // per lane (asynchronous copies, no registers held): the first batch, fetched
 // with the vehicle record, has kFirstChunks 16-byte chunks; every later walk
@@ -53,6 +53,24 @@ constexpr int kWalkChunks = MANTA_WALK_CHUNKS;
 constexpr int kSlotBytes = 16 * kWalkChunks + 16;
 static_assert(kFirstChunks <= kWalkChunks, "the slot holds the first batch");
 constexpr int kWarpWords = kP3Words + 32 * kSlotBytes / 4;
+// lane-change candidates a block of `threads` keeps in its main-phase scratch
+// (64 bytes each), and the entries of its overflow region in the global list
+// when its record pass visits n_rec list entries with a stride of rstride
+// threads (at least half the grid) and it runs its share of n_items
+// merge-phase items (grid of gsz threads)
+__host__ __device__ constexpr uint32_t lc_cap_of(int threads) {
+  return (uint32_t)(threads / 32) * kWarpWords * 4u / 64u;
+}
+__host__ __device__ constexpr uint32_t lc_bound(int threads, uint32_t rstride, uint32_t gsz, uint32_t n_rec,
+                                                uint32_t n_items) {
+  return (uint32_t)threads * ((n_rec + rstride - 1u) / rstride + (n_items + gsz - 1u) / gsz);
+}
+__host__ __device__ constexpr uint32_t lc_overflow(int threads, uint32_t rstride, uint32_t gsz, uint32_t n_rec,
+                                                   uint32_t n_items) {
+  return lc_bound(threads, rstride, gsz, n_rec, n_items) > lc_cap_of(threads)
+             ? lc_bound(threads, rstride, gsz, n_rec, n_items) - lc_cap_of(threads)
+             : 0u;
+}
 // dynamic shared memory of a step-kernel block of `threads` threads
 constexpr size_t step_smem_bytes(int threads) { return (size_t)(threads / 32) * kWarpWords * 4; }
 
@@ -481,6 +499,20 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
   return lt;
 }
 
+// A vehicle joins step kk's lane-change candidates when the step's direction
+// (+1 on even steps, -1 on odd) points at a lane of its edge, and either it
+// moves (a discretionary change needs a slower leader) or a mandatory change
+// is possible (lane not allowed for the next edge, closures here or next).
+__device__ __forceinline__ bool lc_candidate(const Veh &w, int64_t kk) {
+  const int nl = lanes_of(w.em.cnl), ln = ld_lane(w.ld);
+  const int lt = ln + ((kk & 1) ? -1 : 1);
+  return nl >= 2 && lt >= 0 && lt < nl &&
+         (w.v > 0.0f || !((ld_mask(w.ld) >> ln) & 1u) || closable(w.em) || ld_nxclo(w.ld));
+}
+// A list entry of a vehicle that made a crossing request this step: its
+// record is rewritten in P4, which prepares it for the next step itself.
+constexpr uint32_t kReqMark = 0x80000000u;
+
 // Key of lane l of edge e as a request target.
 __device__ __forceinline__ uint32_t target_key(uint32_t e, uint32_t l) { return (e << 4) | l; }
 
@@ -700,6 +732,7 @@ __device__ __forceinline__ void flush_requests(const Params &p, const uint32_t *
     p.req[o] = q[0 * 32 + j]; p.req_x[o] = __uint_as_float(q[1 * 32 + j]); p.req_v[o] = __uint_as_float(q[2 * 32 + j]);
     p.req_dw[o] = q[3 * 32 + j]; p.req_g[o] = q[4 * 32 + j]; p.req_t[o] = q[5 * 32 + j]; p.req_e2[o] = q[6 * 32 + j];
     p.req_n[o] = q[7 * 32 + j];
+    p.req_pos[o] = q[8 * 32 + j];
   }
   __syncwarp(am);
 }
@@ -712,7 +745,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
   __shared__ float s_sab2[8];                       // 2 sqrt(a b) per road class (Eq. 1)
   // per-warp scratch of P3 (dynamic shared memory, kWarpWords words per
   // warp): the work pool (32 slots, list indices, first-batch offsets), 32
-  // staged crossing requests (8 fields, field-major) and the finish queue
+  // staged crossing requests (9 fields, field-major) and the finish queue
   // (kFqFields fields x 64 entries)
   extern __shared__ __align__(16) uint32_t s_wbuf[];
   __shared__ int s_rqn[BLOCK / 32];
@@ -740,6 +773,80 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
   // the launch is replayed from a captured graph
   const int64_t kbase = p.k_from_ctl ? (int64_t)(*(const volatile long long *)&ctl->k_next) : p.k0;
   uint64_t tp = timer ? globaltimer() : 0;
+  // The block's lane-change candidates: the first lc_cap in its (otherwise
+  // idle) main-phase scratch, 64 bytes each; the rest in the block's region of
+  // the global list.  A block lists at most one candidate per list entry its
+  // record pass visits and one per merge-phase item it runs.
+  constexpr uint32_t lc_cap = lc_cap_of(BLOCK);
+  auto lc_region = [&](uint32_t rstride, uint32_t n_rec, uint32_t n_items) {
+    return blockIdx.x * lc_overflow(BLOCK, rstride, gsz, n_rec, n_items);
+  };
+  auto lc_store = [&](uint32_t at, const Veh &w, uint32_t pos, uint32_t reg0) {
+    if (at < lc_cap) {
+      uint4 *e = reinterpret_cast<uint4 *>(s_wbuf) + 4u * at;
+      e[0] = make_uint4(__float_as_uint(w.x), __float_as_uint(w.v), w.id, w.rc);
+      e[1] = make_uint4(w.rend, w.e, w.ld, w.pcell);
+      e[2] = make_uint4(w.em.row0, w.em.cnl, __float_as_uint(w.em.lim), w.em.dst);
+      e[3].x = pos;
+    } else {
+      p.lcq[reg0 + (at - lc_cap)] = w;
+      p.lcq_pos[reg0 + (at - lc_cap)] = pos;
+    }
+  };
+  // The record pass that prepares step kk: over list positions [0, n) of ain,
+  // clear each vehicle's cell of M_{kk-1} in clr (the buffer written during
+  // kk), note the first batch of its leader scan (p3a) and list the block's
+  // lane-change candidates (a record copy with the slot in pcell, and the
+  // list position).  With cmp the live entries are compacted into aout (else
+  // aout is ain).  Entries marked kReqMark belong to the last step's
+  // requesters, whose records P4 rewrote: the mark is removed, and when the
+  // pass runs in that same merge phase (merged) P4 prepares them itself.
+  // The pass runs on warps w0 .. w0 + nw - 1 of the spread numbering (gspr).
+  auto rec = [&](int64_t kk, const uint32_t *ain, uint32_t *aout, uint32_t n, bool cmp, uint8_t *clr,
+                 bool merged, uint32_t reg0, uint32_t w0, uint32_t nw) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = gspr >> 5;
+    if (gw < w0) return;
+    const uint32_t stride = 32u * nw;
+    uint32_t base = 32u * (gw - w0);
+    uint32_t s_nx = base + lane < n ? __ldcg(ain + base + lane) : MANTA_NONE;
+    for (; base < n; base += stride) {
+      const uint32_t i = base + (uint32_t)lane;
+      uint32_t s = s_nx;
+      // the warp's next entries load while it works on these
+      s_nx = base + stride + lane < n ? __ldcg(ain + base + stride + lane) : MANTA_NONE;
+      bool skip = false;
+      if (s != MANTA_NONE && (s & kReqMark) != 0u) {
+        s &= ~kReqMark;
+        if (!cmp) aout[i] = s;
+        skip = merged;
+      }
+      uint32_t pos = i;
+      if (cmp) {
+        const uint32_t at = warp_append(&ctl->n_compact, s != MANTA_NONE);
+        if (s != MANTA_NONE) aout[at] = s;
+        pos = at;
+      }
+      Veh w;
+      bool cand = false;
+      if (s != MANTA_NONE && !skip) {
+        w = load_veh(p, s);
+        if (w.pcell != MANTA_NONE) clr[w.pcell] = (uint8_t)MANTA_EMPTY;
+        p.p3a[pos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
+        cand = lc_candidate(w, kk);
+        if (cand) w.pcell = s;          // the list entry carries the slot in pcell
+      }
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
+      uint32_t b = 0;
+      if (lane == 0 && bal) b = atomicAdd(&s_lcn, (uint32_t)__popc(bal));
+      b = __shfl_sync(0xFFFFFFFFu, b, 0);
+      if (cand) lc_store(b + (uint32_t)__popc(bal & ((1u << lane) - 1u)), w, pos, reg0);
+    }
+  };
+  // the record pass of the current step already ran in the last merge phase,
+  // and the block's candidate list lives in region reg0_next
+  bool rec_ready = false;
+  uint32_t reg0_next = 0u;
   for (int it = 0; it < p.n_steps && alive; ++it) {
     const int64_t k = kbase + it;
     const int cb = (int)(k & 1);
@@ -750,8 +857,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     uint32_t *dep = cb ? p.dep1 : p.dep0;
     uint32_t *dep_n = cb ? p.dep0 : p.dep1;
     uint32_t nact = ldv(&ctl->n_act[cb]);
-    // compact the active list into the other buffer when holes pass a quarter of it
-    const bool compact = holes > 0u && 4u * holes > nact;
+    // compact the active list into the other buffer when holes pass a quarter
+    // of it (only in a step whose record pass runs here)
+    const bool compact = !rec_ready && holes > 0u && 4u * holes > nact;
     const uint32_t *act_in = sel ? p.act1 : p.act0;
     uint32_t *act = compact ? (sel ? p.act0 : p.act1) : (sel ? p.act1 : p.act0);
     // ================================================================ P1
@@ -782,62 +890,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     }
     {
       const int lane = threadIdx.x & 31;
-      // the block lists its candidates in a region of its own (at most one
-      // per list entry its threads visit); after the record loops its warps
-      // decide them, taking batches of 32 from the block's list
-      const uint32_t reg0 = blockIdx.x * (uint32_t)BLOCK * ((nact + gsz - 1u) / gsz);
-      // the first lc_cap candidates of the block stay in shared memory; the
-      // rest go to the block's region of the global list
-      constexpr uint32_t lc_cap = (uint32_t)(BLOCK / 32) * kWarpWords * 4u / 64u;
-      uint32_t base = gtid - (uint32_t)lane;
-      uint32_t s_nx = base + lane < nact ? __ldcg(act_in + base + lane) : MANTA_NONE;
-      for (; base < nact; base += gsz) {
-        const uint32_t i = base + (uint32_t)lane;
-        const uint32_t s = s_nx;
-        // the next block's slots load while this block runs
-        s_nx = base + gsz + lane < nact ? __ldcg(act_in + base + gsz + lane) : MANTA_NONE;
-        uint32_t pos = i;
-        if (compact) {
-          const uint32_t at = warp_append(&ctl->n_compact, s != MANTA_NONE);
-          if (s != MANTA_NONE) act[at] = s;
-          pos = at;
-        }
-        Veh w;
-        bool cand = false;
-        if (s != MANTA_NONE) {
-          w = load_veh(p, s);
-          if (w.pcell != MANTA_NONE) nxt[w.pcell] = (uint8_t)MANTA_EMPTY;
-          p.p3a[pos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
-          // only vehicles that can change lanes this step join the queue: the
-          // step's direction must point at a lane, and either the vehicle moves
-          // (a discretionary change needs a slower leader) or a mandatory
-          // change is possible (lane not allowed, closures here or next)
-          const int nl = lanes_of(w.em.cnl), ln = ld_lane(w.ld);
-          const int lt = ln + ((k & 1) ? -1 : 1);
-          cand = nl >= 2 && lt >= 0 && lt < nl &&
-                 (w.v > 0.0f || !((ld_mask(w.ld) >> ln) & 1u) || closable(w.em) || ld_nxclo(w.ld));
-          if (cand) w.pcell = s;          // the list entry carries the slot in pcell
-        }
-        // candidates join the block's lane-change list (a copy of the record
-        // and the list position)
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
-        uint32_t b = 0;
-        if (lane == 0 && bal) b = atomicAdd(&s_lcn, (uint32_t)__popc(bal));
-        b = __shfl_sync(0xFFFFFFFFu, b, 0);
-        if (cand) {
-          const uint32_t at = b + (uint32_t)__popc(bal & ((1u << lane) - 1u));
-          if (at < lc_cap) {
-            // the block's (otherwise idle) main-phase scratch: 64 bytes per entry
-            uint4 *e = reinterpret_cast<uint4 *>(s_wbuf) + 4u * at;
-            e[0] = make_uint4(__float_as_uint(w.x), __float_as_uint(w.v), w.id, w.rc);
-            e[1] = make_uint4(w.rend, w.e, w.ld, w.pcell);
-            e[2] = make_uint4(w.em.row0, w.em.cnl, __float_as_uint(w.em.lim), w.em.dst);
-            e[3].x = pos;
-          } else {
-            p.lcq[reg0 + at] = w;
-            p.lcq_pos[reg0 + at] = pos;
-          }
-        }
+      uint32_t reg0 = reg0_next;
+      if (!rec_ready) {
+        reg0 = lc_region(gsz, nact, 0u);
+        rec(k, act_in, act, nact, compact, nxt, false, reg0, 0u, gsz / 32u);
       }
       // lane-change decisions on M_k, a full warp of candidates at a time
       __syncthreads();
@@ -859,8 +915,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
             c.em.row0 = q2.x; c.em.cnl = q2.y; c.em.lim = __uint_as_float(q2.z); c.em.dst = q2.w;
             cpos = e[3].x;
           } else {
-            c = load_veh_at(p.lcq + reg0 + j);
-            cpos = __ldcg(p.lcq_pos + reg0 + j);
+            c = load_veh_at(p.lcq + reg0 + (j - lc_cap));
+            cpos = __ldcg(p.lcq_pos + reg0 + (j - lc_cap));
           }
           const int tgt = lc_decide(p, cur, k, c, c_lce);
           const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
@@ -964,7 +1020,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       const uint32_t nwarps = gridDim.x * (BLOCK / 32);
       uint32_t *const wb = s_wbuf + wid * kWarpWords;
       uint32_t *ps = wb, *pi = wb + 32, *pa = wb + 64;
-      uint32_t *fq = wb + 352;   // finish queue: kFqFields fields x 64 entries
+      uint32_t *fq = wb + 384;   // finish queue: kFqFields fields x 64 entries
       // the lane's batch slot (shared-window address for the copies, pointer for the reads)
       const uint8_t *slot_p = reinterpret_cast<const uint8_t *>(wb + kP3Words) + wl * kSlotBytes;
       const uint32_t slot_s = (uint32_t)__cvta_generic_to_shared(slot_p);
@@ -1120,10 +1176,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           const int at = nb + rk;
           rqb[0 * 32 + at] = s; rqb[1 * 32 + at] = __float_as_uint(xn); rqb[2 * 32 + at] = __float_as_uint(vn);
           rqb[3 * 32 + at] = dwn; rqb[4 * 32 + at] = rq_g; rqb[5 * 32 + at] = rq_t; rqb[6 * 32 + at] = rq_e2;
-          rqb[7 * 32 + at] = node_of(em);
+          rqb[7 * 32 + at] = node_of(em); rqb[8 * 32 + at] = i;
           __syncwarp(am);
           if (rk == 0) s_rqn[wid] = nb + cnt;
           __syncwarp(am);
+          // P4 rewrites this record: the next record pass leaves it to P4
+          act[i] = s | kReqMark;
         }
         if (p.tape) {
           const int64_t tk = k - p.tape_k0;
@@ -1260,6 +1318,24 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     const uint32_t due_lo = ldv(&ctl->due_pos), due_hi = ldv(&ctl->due_hi);
     // free slots: constant during this phase (arrivals freed theirs in P3)
     const uint32_t fc = ldv(&ctl->free_count), n_slots = ldv(&ctl->n_slots);
+    // This phase also runs the record pass of step k + 1 (the vehicles that
+    // stayed on their edge in P3; P4's own vehicles are prepared where P4
+    // finalises them), unless this is the launch's last step or k + 1 will
+    // compact its list.  Every block takes the same decision.
+    const uint32_t holes_n = ldv(&ctl->n_holes[cb ^ 1]);
+    const bool ahead = it + 1 < p.n_steps && !(holes_n > 0u && 4u * holes_n > nact);
+    // the pass runs on the warps that have no merge-phase item, when those are
+    // at least half of all warps (items go to warps in gspr order)
+    const uint32_t t_items = nreq + ndep + narr + (due_hi - due_lo);
+    const uint32_t w_items = (t_items + 31u) / 32u, w_all = gsz / 32u;
+    const uint32_t rw0 = 2u * w_items <= w_all ? w_items : 0u;
+    const uint32_t reg0n = ahead ? lc_region(32u * (w_all - rw0), nact, nreq + ndep) : 0u;
+    if (threadIdx.x == 0) { s_lcn = 0u; s_lct = 0u; }   // the block's lane-change list of step k + 1
+    __syncthreads();
+    auto lc_add1 = [&](Veh w, uint32_t pos, uint32_t slot) {
+      w.pcell = slot;
+      lc_store(atomicAdd(&s_lcn, 1u), w, pos, reg0n);
+    };
     const uint32_t t_dep = nreq, t_arr = t_dep + ndep, t_due = t_arr + narr, t_end = t_due + (due_hi - due_lo);
     for (uint32_t t = gspr; t < t_end; t += gsz) {
       if (t < t_dep) {
@@ -1272,6 +1348,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         const uint32_t gown = __ldcg(p.req_g + i), tgt = __ldcg(p.req_t + i);
         const uint32_t e2 = __ldcg(p.req_e2 + i), n = __ldcg(p.req_n + i);
         const float rx = __ldcg(p.req_x + i), rv = __ldcg(p.req_v + i);
+        const uint32_t rpos = __ldcg(p.req_pos + i);
         const uint32_t o0 = __ldg(p.nin_off + n), o1 = __ldg(p.nin_off + n + 1);
         const unsigned long long dk = __ldcg(p.dep_key + e2);
         const EdgeMeta em2 = load_em(p, e2);
@@ -1325,6 +1402,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           atomicAdd(p.ssum + o, (unsigned long long)(vf * 1048576.0f));
           atomicAdd(p.scnt + o, 1u);
         }
+        if (ahead) {
+          // step k + 1's record pass for this vehicle: its M_k cell is in the
+          // buffer written during k + 1
+          cur[w.pcell] = (uint8_t)MANTA_EMPTY;
+          p.p3a[rpos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
+          if (lc_candidate(w, k + 1)) lc_add1(w, rpos, s);
+        }
       } else if (t < t_arr) {
         const uint32_t i = t - t_dep;
         // round trip 1: the entry P3 wrote (edge, head trip, competitors'
@@ -1366,6 +1450,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           atomicAdd(p.entry + e, 1u);
           c_dep++;
           p.q_pos[e] = qp + 1u;
+          if (ahead) {                        // step k + 1's record pass for this vehicle
+            p.p3a[ia] = first_batch(em, 0, 0);
+            if (lc_candidate(w, k + 1)) lc_add1(w, ia, s);
+          }
         }
         if (keep) dep_n[id2] = e;
       } else if (t < t_due) {
@@ -1378,10 +1466,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         if (first) dep_n[id2] = e;
       }
     }
+    // step k + 1's record pass over the vehicles that stayed on their edge
+    if (ahead) rec(k + 1, act, act, nact, false, cur, true, reg0n, rw0, w_all - rw0);
     if (gtid == 0) ctl->n_compact = 0u;
-    if (threadIdx.x == 0) { s_lcn = 0u; s_lct = 0u; }   // the block's lane-change list of the next step
     if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
     if (timer) { const uint64_t t = globaltimer(); ph[3] += t - tp; tp = t; }
+    rec_ready = ahead;
+    reg0_next = reg0n;
   }
   // flush counters
   atomicAdd(&s_cnt[CNT_UPD], (unsigned long long)c_upd);
