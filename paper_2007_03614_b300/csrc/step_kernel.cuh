@@ -2,16 +2,20 @@
 //
 // One cooperative launch runs n_steps steps.  Per step k the grid goes
 // through four phases separated by grid barriers with bounded waits:
-//   P1  clear last step's cells in the spare map buffer; the first lane-map
-//       batch of every vehicle's leader scan; lane-change decisions on M_k
-//       (Section II-D, Eqs. 2-4); stop-sign permits for this step; the
-//       departure-step range of the trips that join queues at k + 1
+//   P1  lane-change decisions on M_k (Section II-D, Eqs. 2-4); stop-sign
+//       permits for this step; the departure-step range of the trips that
+//       join queues at k + 1.  The step's record pass (clear last step's cells
+//       in the spare map buffer, note the first lane-map batch of every
+//       leader scan, list the lane-change candidates) ran in the previous
+//       step's P4 phase, on the warps without merge items; it runs here at a
+//       launch's first step and when the active list is compacted.
 //   P2  lane-change apply in place, M_k -> M_k' (skipped when nobody changes)
 //   P3  leader scan along the route on M_k', IDM (Eq. 1), ballistic update,
 //       clamp; write M_{k+1} for vehicles that stay on their edge; crossing
 //       requests; departure requests; arrivals
 //   P4  merge resolution (lowest id wins per target lane), crossings,
-//       departures, arrivals' cells, departure-queue bookkeeping
+//       departures, arrivals' cells, departure-queue bookkeeping; the record
+//       pass of step k + 1 (P4 prepares the vehicles it finalises itself)
 // Arithmetic is binary32 with the operation order of the definition; the
 // library is compiled with -fmad=false -prec-div=true -prec-sqrt=true so
 // every operation is one correctly rounded IEEE op.
