@@ -172,6 +172,80 @@ def test_free_flow_first_order_convergence_to_ode():
     assert 1.7 < e1 / e2 < 2.3
 
 
+# ------------------------------------------- link-speed statistic (A10) --
+def _link_speed_trace(lengths, x, v, n_steps, t0, W, v0=25.0, a=1.0, dt=0.5):
+    """Float64 trace of a lone vehicle on a line of green edges, written from
+    the definitions alone: Eq. 1 free-road term (delta = 4), the ballistic
+    step, the one-node-per-step clamp (at most C_e + C_next - 1, speed 0 when
+    clamped), the crossing into the next edge, and the link-speed sample of
+    Sections IV-A/B taken once per vehicle-step AFTER the step: the speed the
+    vehicle ends the step with, on the edge it ends the step on, in window
+    (k - t0) // W.  Returns {(window, edge): [speeds]} and the smallest
+    distance of any tentative position from a decision threshold (an edge end
+    or a clamp bound), so the caller can check that the binary32 run takes the
+    same discrete decisions."""
+    C = [max(8, int(round(L_))) for L_ in lengths]
+    e = 0
+    samples = {}
+    margin = float("inf")
+    for k in range(t0, t0 + n_steps):
+        acc = a * (1.0 - (v / v0) ** 4)
+        vt = v + acc * dt
+        assert vt >= 0.0
+        xt = x + v * dt + 0.5 * acc * dt * dt
+        xn, vn = xt, vt
+        if e + 1 < len(C):
+            cap = C[e] + C[e + 1] - 1
+            margin = min(margin, abs(xt - cap), abs(xt - C[e]))
+            if xt > cap:
+                xn, vn = max(x, float(cap)), 0.0
+            if xn >= C[e]:
+                xn -= C[e]
+                e += 1
+        x, v = xn, vn
+        samples.setdefault(((k - t0) // W, e), []).append(v)
+    return samples, margin
+
+
+def test_link_speed_statistic_window_edge_and_sample():
+    """Pins which (window, edge) cell each vehicle-step's speed sample lands
+    in and which speed is sampled: against an independent float64 trace, the
+    per-(window, edge) counts are exact and the fixed-point sums agree within
+    the float32/float64 gap of T1.  A sample taken before the clamp (the first
+    step is clamped from 25 m/s to 0 at the one-node bound), on the edge left
+    in a crossing step, before the step (the old speed), or in a window shifted
+    by one step fails here."""
+    lengths = [300.0, 8.0, 60.0, 45.0, 120.0, 37.0, 250.0, 3000.0]
+    t0, W, n_steps = 13, 40, 260
+    x0, v0_init = 296.5, 25.0
+    net = nets.network(len(lengths) + 1, [(i, i + 1, 1, L_, 25.0, 0) for i, L_ in enumerate(lengths)])
+    tr = nets.trips([list(range(len(lengths)))], [1e7])
+    o = O.OracleSim(net, t0_step=t0, stats_window_steps=W, n_stats_windows=10)
+    nets.load(o, tr)
+    o.place(0, 0, 0, x0, v0_init)
+    o.step(n_steps)
+    expect, margin = _link_speed_trace(lengths, x0, v0_init, n_steps, t0, W)
+    assert margin > 0.05
+    # the trace covers what the pin is about: a clamped first step, several
+    # crossings, crossings inside windows and windows inside edges
+    assert expect[(0, 1)][0] == 0.0
+    edges_seen = {e for (_, e) in expect}
+    assert len(edges_seen) >= 6 and len({w for (w, _) in expect}) >= 6
+    assert any(len({e for (w, e) in expect if w == w0}) > 1 for w0 in range(7))
+    got_cnt, got_sum = {}, {}
+    for w in range(10):
+        ec = o.edge_counters(w)
+        for e in np.nonzero(ec["speed_cnt"])[0]:
+            got_cnt[(w, int(e))] = int(ec["speed_cnt"][e])
+            got_sum[(w, int(e))] = int(ec["speed_sum"][e])
+    assert got_cnt == {key: len(vs) for key, vs in expect.items()}
+    for key, vs in expect.items():
+        fx = sum(int(v * 1048576.0) for v in vs)
+        # T1's bound per sample (2e-5 relative on v) in units of 2^-20 m/s, plus truncation
+        tol = sum(2e-5 * max(1.0, v) * 1048576.0 + 1.0 for v in vs)
+        assert abs(got_sum[key] - fx) <= tol, (key, got_sum[key], fx, tol)
+
+
 # ------------------------------------------------------ T2: ring equilibrium --
 def _ring_sim(n_veh, ring_edges=4, edge_len=100.0, v_init=0.0, laps=400, **cfg):
     total = int(ring_edges * edge_len)
