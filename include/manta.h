@@ -343,11 +343,11 @@ MANTA_API const char *manta_last_error(void);
 MANTA_API manta_status manta_selftest_barrier_timeout(int32_t limit_ms, void *cuda_stream);
 
 /* Runs a whole small simulation without allocating any device memory, for
- * callers that cannot call cudaMalloc: code running while a CUDA graph is
- * being captured (where allocation is not allowed), host applications whose
- * device memory is fully reserved by their own pool allocator, or real-time
- * loops that must not stall on the driver's allocator.  The paper has no
- * counterpart: it only concerns how device memory is obtained.
+ * callers that cannot call cudaMalloc: host applications whose device memory
+ * is wholly reserved by their own pool allocator (a cudaMalloc from a library
+ * would fail, or fragment their pool), or real-time loops that must not
+ * stall on the driver's allocator.  The paper has no counterpart: it only
+ * concerns how device memory is obtained.
  *
  * Arguments are those of manta_create, manta_load_trips (host arrays,
  * copied), the number of steps, and the outputs of manta_stats and
@@ -362,8 +362,13 @@ MANTA_API manta_status manta_selftest_barrier_timeout(int32_t limit_ms, void *cu
  * reuses the same array and resets what must start empty; two calls that
  * overlap on the GPU (other threads, other streams) race on it and must not
  * be issued.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture begins.  The call synchronises cuda_stream before returning. */
+ * address (cudaGetSymbolAddress) and keeps it for the life of the process;
+ * a cudaDeviceReset invalidates it, so do not call this function after one.
+ * cuda_stream must belong to the current device (MANTA_E_INVALID otherwise).
+ *
+ * The call uploads its inputs from pageable host memory, synchronises
+ * cuda_stream several times and returns only when the results are on the
+ * host: issue it outside any stream capture. */
 MANTA_API manta_status manta_run_noalloc(
     int32_t n_nodes, int32_t n_edges, const int32_t *edge_src, const int32_t *edge_dst, const uint8_t *edge_lanes,
     const float *edge_length_m, const float *edge_speed_limit_mps, const uint8_t *edge_class,

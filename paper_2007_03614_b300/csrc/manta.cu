@@ -995,6 +995,15 @@ manta_status manta_run_noalloc(int32_t n_nodes, int32_t n_edges, const int32_t *
   static void *addr[64] = {nullptr};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(MANTA_E_CUDA, "no current CUDA device");
+  // the kernels run on cuda_stream: it must belong to the device whose arena
+  // address is used (the legacy default stream follows the current device)
+  if (cuda_stream) {
+    int sdev = -1;
+    cudaError_t e = cudaStreamGetDevice(static_cast<cudaStream_t>(cuda_stream), &sdev);
+    if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("cudaStreamGetDevice: ") + cudaGetErrorString(e));
+    if (sdev != dev) return fail(MANTA_E_INVALID, "cuda_stream belongs to device " + std::to_string(sdev) +
+                                                      ", not the current device " + std::to_string(dev));
+  }
   void *base = nullptr;
   {
     std::lock_guard<std::mutex> lock(mu);

@@ -1,9 +1,10 @@
 """manta_run_noalloc: a whole small simulation whose device state lives in the
 library's static arena instead of cudaMalloc'd memory, for callers that cannot
-allocate device memory (inside CUDA graph capture, under a host application's
-own pool allocator, or in loops that must not stall on allocation).  Its
-results must equal those of the allocating entry points bit for bit, on two
-calls in a row (the second call reuses the arena the first one left behind).
+allocate device memory (a host application whose device memory is wholly held
+by its own pool allocator, or a loop that must not stall on the driver's
+allocator).  Its results must equal those of the allocating entry points bit
+for bit, on two calls in a row (the second call reuses the arena the first one
+left behind), and after a different workload has dirtied the arena.
 
 Collected last on purpose: a failure here leaves every other test already run.
 """
@@ -50,6 +51,24 @@ def test_no_alloc_matches_allocating_path_twice():
     # a different workload in between must not leak into the next call
     tr2 = synth.tiny_trips(net, n_trips=400, seed=9)
     _same(manta.run_noalloc(net, tr2, 300, seed=5), _allocating(net, tr2, 300, seed=5))
+
+
+def test_no_alloc_dirty_arena_with_per_driver_limits():
+    """Per-driver speed limits (Section IV-B) and a non-default seed, on an
+    arena left dirty by a different, larger workload: still bit for bit the
+    allocating path.  (The entry point takes no lane closures; the closure
+    windows it uploads are empty on every call.)"""
+    import torch
+    assert torch.cuda.is_available()
+    build()
+    net = synth.tiny_network()
+    manta.run_noalloc(net, synth.tiny_trips(net, n_trips=1000, seed=3), 900, seed=11)
+    tr = synth.tiny_trips(net, n_trips=600, seed=21)
+    cfg = dict(speed_sigma_frac=0.05, seed=77)
+    a = manta.run_noalloc(net, tr, 500, **cfg)
+    b = _allocating(net, tr, 500, **cfg)
+    assert b[0]["on_network"] > 0
+    _same(a, b)
 
 
 def test_no_alloc_rejects_workloads_beyond_the_arena():
