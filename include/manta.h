@@ -300,8 +300,17 @@ MANTA_API void manta_checkpoint_destroy(manta_checkpoint *ckpt);
  * binary64 accumulates the replayed speed of every sample.  Asynchronous on
  * the sim's stream.
  *
+ * Both are reproducible bit for bit: the gradient is summed per thread, per
+ * block in a fixed tree and over blocks in block order, and replayed speeds
+ * are summed exactly in 128-bit fixed point before one rounding to binary64,
+ * so no result depends on the order in which GPU threads run.  Each keeps a
+ * small device scratch buffer in the simulation, allocated on its first call
+ * (the adjoint: 320 bytes per 256 trips; the replay: 16 bytes per statistics
+ * cell) and freed by manta_destroy.
+ *
  * Both return MANTA_E_STATE when no tape was recorded or its segment has
- * not been run completely. */
+ * not been run completely, MANTA_E_OOM when the scratch buffer cannot be
+ * allocated. */
 /* One record of the event tape (40 bytes): index (k - k0) * n_trips + trip
  * for step k of the recorded segment [k0, k0 + n_steps).  flags: bit 0 on
  * the network at the start of the step; bits 1-2 kind (0 free road, 1

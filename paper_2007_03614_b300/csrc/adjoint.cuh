@@ -14,6 +14,12 @@
 // Vehicles interact only through the byte lane map, whose content is held
 // fixed, so every vehicle's recurrence is independent: one thread carries a
 // vehicle's adjoint backward through a tape segment.  Arithmetic is binary64.
+//
+// Both sweeps are reproducible bit for bit: no floating-point sum depends on
+// the order in which threads run.  Parameter derivatives are summed per
+// thread, then over each block in a fixed tree, then over the blocks in
+// block order; replayed speeds are summed exactly, as 128-bit fixed-point
+// numbers with 64 fractional bits, whose integer additions commute.
 #pragma once
 #include <stdint.h>
 #include "sim.cuh"
@@ -91,13 +97,27 @@ __device__ __forceinline__ bool replay_step(const IdmTheta &th, double dt, const
   return true;
 }
 
+// Exact accumulation of a binary64 value of magnitude below 2^62 into a
+// 128-bit two's-complement fixed-point sum (acc[0]: 64 fractional bits,
+// acc[1]: integer part): v = floor(v) + a fraction in [0, 1), both exact.
+// The carry out of the low word is known from the value it held before the
+// addition, so the final sum does not depend on the order of the additions.
+__device__ __forceinline__ void fx128_add(unsigned long long *acc, double v) {
+  const double ip = floor(v);
+  const unsigned long long lo = __double2ull_rz((v - ip) * 18446744073709551616.0);   // x 2^64, exact
+  const unsigned long long hi = (unsigned long long)__double2ll_rz(ip);
+  const unsigned long long old = atomicAdd(acc, lo);
+  const unsigned long long carry = old + lo < old ? 1ull : 0ull;
+  if (hi + carry) atomicAdd(acc + 1, hi + carry);
+}
+
 // Forward replay of a tape segment of n_steps steps with parameters th:
 // per trip, the state (x, v) carried in from the previous segment (present
 // flag 1) or taken from the tape where the vehicle enters; the speed of every
-// recorded sample is added to sums[sample].  Used for finite differences on
-// the frozen-event run.
+// recorded sample is added to the fixed-point sum acc[2 * sample].  Used for
+// finite differences on the frozen-event run.
 __global__ void replay_kernel(const TapeRec *tape, int32_t n_steps, uint32_t n_trips, double dt, IdmTheta th,
-                              double *xs, double *vs, uint8_t *present, double *sums) {
+                              double *xs, double *vs, uint8_t *present, unsigned long long *acc) {
   for (uint32_t id = blockIdx.x * blockDim.x + threadIdx.x; id < n_trips; id += gridDim.x * blockDim.x) {
     double x = xs[id], v = vs[id];
     bool prev = present[id] != 0;
@@ -107,21 +127,34 @@ __global__ void replay_kernel(const TapeRec *tape, int32_t n_steps, uint32_t n_t
       if (!prev) { x = (double)r.x; v = (double)r.v; }
       const uint32_t out = (r.flags >> TF_OUT_SHIFT) & 7u;
       prev = replay_step(th, dt, r, x, v);
-      if (r.sample != MANTA_NONE && (out == TO_STAY || out == TO_CROSS)) atomicAdd(sums + r.sample, v);
+      if (r.sample != MANTA_NONE && (out == TO_STAY || out == TO_CROSS)) fx128_add(acc + 2 * (size_t)r.sample, v);
     }
     xs[id] = x; vs[id] = v; present[id] = prev ? 1 : 0;
+  }
+}
+
+// sums[i] += the fixed-point sum acc[2 i], rounded once to binary64
+__global__ void replay_sums_kernel(const unsigned long long *acc, size_t n, double *sums) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long lo = acc[2 * i], hi = acc[2 * i + 1];
+    if (lo | hi) sums[i] += (double)(long long)hi + (double)lo * 5.421010862427522170037e-20;   // 2^-64
   }
 }
 
 // Reverse sweep of a tape segment: lam_x, lam_v hold, per trip, the adjoint
 // of the state after the segment (in) and receive the adjoint of the state
 // entering it (out).  seed[sample] = dLoss / d(sample speed).  Parameter
-// derivatives are added to grad[5 * class + j], j over (v0f, T, a, b, s0).
-__global__ void adjoint_kernel(const TapeRec *tape, int32_t n_steps, uint32_t n_trips, double dt, IdmTheta th,
-                               const double *seed, double *lam_x, double *lam_v, double *grad) {
-  __shared__ double g[40];
-  if (threadIdx.x < 40) g[threadIdx.x] = 0.0;
-  __syncthreads();
+// derivatives of block b go to part[40 b + 5 * class + j], j over (v0f, T,
+// a, b, s0); adjoint_grad_kernel adds the blocks' parts to grad in block
+// order.  Launch with kAdjBlock threads per block.
+constexpr int kAdjBlock = 256;
+__global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(const TapeRec *tape, int32_t n_steps, uint32_t n_trips,
+                                                            double dt, IdmTheta th, const double *seed,
+                                                            double *lam_x, double *lam_v, double *part) {
+  __shared__ double red[kAdjBlock];
+  double g[40];                          // this thread's derivatives, summed in its own order
+#pragma unroll
+  for (int q = 0; q < 40; ++q) g[q] = 0.0;
   for (uint32_t id = blockIdx.x * blockDim.x + threadIdx.x; id < n_trips; id += gridDim.x * blockDim.x) {
     double lx = lam_x[id], lv = lam_v[id];
     for (int32_t t = n_steps - 1; t >= 0; --t) {
@@ -143,8 +176,7 @@ __global__ void adjoint_kernel(const TapeRec *tape, int32_t n_steps, uint32_t n_
       if (kind == TK_STOP || clamp == 1) {
         lx0 += lxp;                       // xp = x, vp = 0
       } else if (clamp == 0) {
-        const double x = (double)r.x, v = (double)r.v;
-        (void)x;
+        const double v = (double)r.v;
         const AccD d = idm_acc(th, c, (double)r.lim, v, kind == TK_INTERACT, (double)r.s, (double)r.vL);
         double ga;                        // adjoint of acc
         lx0 += lxp;
@@ -158,13 +190,36 @@ __global__ void adjoint_kernel(const TapeRec *tape, int32_t n_steps, uint32_t n_
           lv0 += lxp * (-v / d.acc);
         }
         lv0 += ga * d.dv;
-        for (int j = 0; j < 5; ++j) atomicAdd(&g[5 * c + j], ga * d.dth[j]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q == c) {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) g[5 * q + j] += ga * d.dth[j];
+          }
       }
       // clamp == 2: xp = bound, vp = 0: nothing flows back
       lx = lx0; lv = lv0;
     }
     lam_x[id] = lx; lam_v[id] = lv;
   }
-  __syncthreads();
-  if (threadIdx.x < 40 && g[threadIdx.x] != 0.0) atomicAdd(grad + threadIdx.x, g[threadIdx.x]);
+  // the block's sum of each derivative: a fixed binary tree over the threads
+  for (int q = 0; q < 40; ++q) {
+    red[threadIdx.x] = g[q];
+    __syncthreads();
+    for (int h = kAdjBlock / 2; h > 0; h >>= 1) {
+      if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[40 * (size_t)blockIdx.x + q] = red[0];
+    __syncthreads();
+  }
+}
+
+// grad[q] += the blocks' parts, summed in block order (one thread per q < nq)
+__global__ void adjoint_grad_kernel(const double *part, int n_blocks, double *grad, int nq) {
+  const int q = threadIdx.x;
+  if (q >= nq) return;
+  double s = 0.0;
+  for (int b = 0; b < n_blocks; ++b) s += part[40 * (size_t)b + q];
+  grad[q] += s;
 }

@@ -120,6 +120,12 @@ struct manta_sim {
   size_t tape_cap = 0;
   int64_t tape_k0 = 0;
   int32_t tape_len = 0;
+  // scratch of the adjoint (per-block parts of the gradient) and of the
+  // replay (128-bit fixed-point sums per statistics cell), allocated on first use
+  double *adj_part = nullptr;
+  size_t adj_part_cap = 0;
+  unsigned long long *rep_acc = nullptr;
+  size_t rep_acc_cap = 0;
 };
 
 // Launch shapes of the step kernel (threads per block, minimum blocks per
@@ -241,6 +247,8 @@ void manta_destroy(manta_sim *S) {
   cudaStreamSynchronize(S->stream);
   for (void *p : S->allocs) cudaFree(p);
   if (S->tape) cudaFree(S->tape);
+  if (S->adj_part) cudaFree(S->adj_part);
+  if (S->rep_acc) cudaFree(S->rep_acc);
   delete S;
 }
 
@@ -1194,9 +1202,21 @@ manta_status manta_adjoint(manta_sim *S, const double *seed, double *lam_x, doub
   if (st != MANTA_OK) return st;
   if (!seed || !lam_x || !lam_v || !grad) return fail(MANTA_E_INVALID, "NULL argument");
   const uint32_t n = (uint32_t)std::max<int64_t>(S->n_trips, 1);
-  const int blocks = (int)std::min<uint32_t>((n + 255u) / 256u, 4096u);
-  adjoint_kernel<<<blocks, 256, 0, S->stream>>>(S->tape, S->tape_len, (uint32_t)S->n_trips, (double)S->cfg.dt,
-                                                theta_of(S->cfg), seed, lam_x, lam_v, grad);
+  const int blocks = (int)std::min<uint32_t>((n + kAdjBlock - 1u) / kAdjBlock, 4096u);
+  if (S->adj_part_cap < (size_t)blocks * 40) {
+    if (S->adj_part) { cudaStreamSynchronize(S->stream); cudaFree(S->adj_part); }
+    S->adj_part = nullptr;
+    S->adj_part_cap = 0;
+    if (cudaMalloc(&S->adj_part, (size_t)blocks * 40 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      S->adj_part = nullptr;
+      return fail(MANTA_E_OOM, "adjoint scratch allocation failed");
+    }
+    S->adj_part_cap = (size_t)blocks * 40;
+  }
+  adjoint_kernel<<<blocks, kAdjBlock, 0, S->stream>>>(S->tape, S->tape_len, (uint32_t)S->n_trips, (double)S->cfg.dt,
+                                                      theta_of(S->cfg), seed, lam_x, lam_v, S->adj_part);
+  adjoint_grad_kernel<<<1, 64, 0, S->stream>>>(S->adj_part, blocks, grad, 5 * S->cfg.n_classes);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
   return MANTA_OK;
@@ -1215,8 +1235,24 @@ manta_status manta_replay(manta_sim *S, const double *theta, double *x, double *
   }
   const uint32_t n = (uint32_t)std::max<int64_t>(S->n_trips, 1);
   const int blocks = (int)std::min<uint32_t>((n + 255u) / 256u, 4096u);
+  const size_t cells = (size_t)S->cfg.n_stats_windows * (size_t)S->E;
+  if (S->rep_acc_cap < 2 * cells) {
+    if (S->rep_acc) { cudaStreamSynchronize(S->stream); cudaFree(S->rep_acc); }
+    S->rep_acc = nullptr;
+    S->rep_acc_cap = 0;
+    if (cudaMalloc(&S->rep_acc, 2 * cells * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      S->rep_acc = nullptr;
+      return fail(MANTA_E_OOM, "replay scratch allocation failed");
+    }
+    S->rep_acc_cap = 2 * cells;
+  }
+  if (cudaMemsetAsync(S->rep_acc, 0, 2 * cells * sizeof(unsigned long long), S->stream) != cudaSuccess)
+    return fail(MANTA_E_CUDA, "replay scratch reset failed");
   replay_kernel<<<blocks, 256, 0, S->stream>>>(S->tape, S->tape_len, (uint32_t)S->n_trips, (double)S->cfg.dt, th,
-                                               x, v, present, sums);
+                                               x, v, present, S->rep_acc);
+  const int sb = (int)std::min<size_t>((cells + 255) / 256, 4096);
+  replay_sums_kernel<<<sb, 256, 0, S->stream>>>(S->rep_acc, cells, sums);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(MANTA_E_CUDA, std::string("replay launch: ") + cudaGetErrorString(e));
   return MANTA_OK;

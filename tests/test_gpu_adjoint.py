@@ -195,6 +195,39 @@ def test_gpu_adjoint_matches_replay_differences(taped):
             assert abs(fd - adj[c, j]) <= 1e-3 * max(abs(fd), 1e-3 * scale), (c, A.PARAMS[j], fd, adj[c, j])
 
 
+def test_gpu_adjoint_and_replay_are_bit_reproducible(taped):
+    """Two sweeps over the same tape give the same bits: gradient, lam_x and
+    lam_v of the adjoint, and the state and speed sums of a replay with
+    perturbed parameters (no sum depends on the order GPU threads run in)."""
+    import torch
+    net, tr, o, ot, g, gt = taped
+    E = len(net.edge_src)
+    n_cells = 5 * E
+    dev = torch.device("cuda")
+    N = tr.n_trips
+    theta = _theta(o.cfg, 3)
+    rng = np.random.default_rng(5)
+    seed = torch.as_tensor(rng.normal(size=n_cells) * 1e-3, device=dev)
+    th_p = theta * (1.0 + 0.01 * rng.uniform(-1.0, 1.0, theta.shape))
+    runs = []
+    for _ in range(2):
+        lx = torch.full((N,), 0.25, dtype=torch.float64, device=dev)
+        lv = torch.full((N,), -0.5, dtype=torch.float64, device=dev)
+        grad = torch.zeros(15, dtype=torch.float64, device=dev)
+        x = torch.zeros(N, dtype=torch.float64, device=dev)
+        v = torch.zeros(N, dtype=torch.float64, device=dev)
+        pr = torch.zeros(N, dtype=torch.uint8, device=dev)
+        sums = torch.full((n_cells,), 1.0, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        g.adjoint(seed, lx, lv, grad)
+        g.replay(th_p, x, v, pr, sums)
+        torch.cuda.synchronize()
+        runs.append([t.cpu().numpy() for t in (grad, lx, lv, x, v, pr, sums)])
+    assert np.abs(runs[0][0]).max() > 0 and (runs[0][6] != 1.0).sum() > 100
+    for a, b in zip(*runs):
+        assert a.tobytes() == b.tobytes()
+
+
 def test_checkpointed_backward_equals_single_tape():
     import torch
     net = synth.calib_network()
