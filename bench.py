@@ -36,24 +36,58 @@ UNIT = "vehicle-updates/s"
 T0_STEP = 36000                     # 05:00 at dt = 0.5 s
 MORNING_STEPS = 50400               # 05:00-12:00
 
-# Algorithmic bytes of the step kernel: per vehicle update (active-list
-# entries, vehicle record read twice and written once, the map byte written
-# and cleared, the per-edge speed statistic read-modify-write), per lane-map
-# cell examined by a leader scan, per node crossed by a scan (route entry,
-# edge record, signal window, node type), per gap-acceptance evaluation.
-BYTES_PER_UPDATE = 162
+# Algorithmic bytes of one step of the method (the scope table's measurement
+# row): per vehicle update, the state a structure-of-arrays layout must read
+# (x 4, v 4, route cursor 4, edge 4, lane/flags/dwell 2, previous cell 4 = 22 B)
+# and write (18 B), the edge record it needs (12 B), the map byte written and
+# the one cleared (1 + 1); per lane-map cell examined by a leader scan, 1 B;
+# per node a scan crosses, the next route entry (4 B); per gap-acceptance
+# evaluation, the lead and lag cells (8 B); per departure, 16 B.
+BYTES_PER_UPDATE = 54
 BYTES_PER_CELL = 1
-BYTES_PER_ROUTE_READ = 29
-BYTES_PER_LC_EVAL = 64
+BYTES_PER_BOUNDARY = 4
+BYTES_PER_LC_EVAL = 8
+BYTES_PER_DEPARTURE = 16
+# Reported beside it, not in it: the per-edge speed statistic's read-modify-
+# write (sum 8 + count 4, read and written) per vehicle update.
+BYTES_STATS_PER_UPDATE = 24
+# What this implementation's layout moves per unit (48-byte vehicle records
+# read twice and written once, active-list entries, statistics; an edge record,
+# signal window and node type per node crossed; a 64-byte window per
+# gap-acceptance evaluation): context for the DRAM traffic, not the roofline.
+LAYOUT_BYTES = {"per_update": 162, "per_cell": 1, "per_route_read": 29, "per_lc_eval": 64}
 KERNEL_SOURCES = ("paper_2007_03614_b300/csrc/step_kernel.cuh", "paper_2007_03614_b300/csrc/sim.cuh")
 TRAFFIC_PROFILE = "profiles/metro_step_kernel_ncu.md"
 WORKLOAD = ("metro-shaped morning: ~550k directed edges / ~218k nodes, 3.2M trips, "
             "05:00-12:00 departures N(08:00, 75 min), dt = 0.5 s")
+PEAK_HOUR = (7.5 * 3600, 8.5 * 3600)
 
 
 def algorithmic_bytes(d: dict) -> int:
     return (d["vehicle_updates"] * BYTES_PER_UPDATE + d["cells_scanned"] * BYTES_PER_CELL
-            + d["route_reads"] * BYTES_PER_ROUTE_READ + d["lc_evals"] * BYTES_PER_LC_EVAL)
+            + d["route_reads"] * BYTES_PER_BOUNDARY + d["lc_evals"] * BYTES_PER_LC_EVAL
+            + d["departed"] * BYTES_PER_DEPARTURE)
+
+
+def layout_bytes(d: dict) -> int:
+    return (d["vehicle_updates"] * LAYOUT_BYTES["per_update"] + d["cells_scanned"] * LAYOUT_BYTES["per_cell"]
+            + d["route_reads"] * LAYOUT_BYTES["per_route_read"] + d["lc_evals"] * LAYOUT_BYTES["per_lc_eval"])
+
+
+def host_cpu() -> dict:
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except Exception:
+        usable = os.cpu_count()
+    return {"nproc": usable, "cpu_count": os.cpu_count(), "model": model}
 
 
 def kernel_hash() -> str:
@@ -235,76 +269,103 @@ def run_gpu(args):
     sim = manta.Sim(net, stream=stream, t0_step=T0_STEP)
     sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+    keys = ("vehicle_updates", "cells_scanned", "route_reads", "lc_evals", "clamps", "lane_changes", "departed",
+            "arrived")
+
+    def timed_chunk():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
             sim.step(chunk)
+            ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / 1000.0
+
+    warm_times = [timed_chunk() for _ in range(args.warmup)]
     s0 = sim.stats()
     ph0 = sim.phase_times_ms()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    times = []
+    times, per_chunk = [], []
+    prev = s0
     with Clocks(local) as clk:
         for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(1)
-                ev0 = torch.cuda.Event(enable_timing=True)
-                ev1 = torch.cuda.Event(enable_timing=True)
-                ev0.record(stream)
-                sim.step(chunk)
-                ev1.record(stream)
-            ev1.synchronize()
-            times.append(ev0.elapsed_time(ev1) / 1000.0)
+            times.append(timed_chunk())
+            cur = sim.stats()             # outside the events: counters of this chunk
+            per_chunk.append({k: cur[k] - prev[k] for k in keys})
+            prev = cur
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     s1 = sim.stats()
     phase_ms = [round(float(a - b), 2) for a, b in zip(sim.phase_times_ms(), ph0)]
     elapsed = sum(times)
-    d = {k: s1[k] - s0[k] for k in ("vehicle_updates", "cells_scanned", "route_reads", "lc_evals", "clamps",
-                                    "lane_changes", "departed", "arrived")}
+    d = {k: s1[k] - s0[k] for k in keys}
     elapsed, total_updates = aggregate_ranks(elapsed, d["vehicle_updates"], device="cuda")
-    morning = None
-    if T0_STEP + (args.warmup + args.steps) * chunk >= T0_STEP + MORNING_STEPS:
-        morning = None  # filled by the e2e run below, which always simulates the whole morning
     sim.close()
     del flush
-    # ---- end-to-end through the C ABI from host buffers ----
-    e2e = None
+    # ---- end to end through the C ABI from host buffers: always the whole
+    # morning (05:00-12:00), create and load included ----
+    e2e, morning = None, None
+    n_morning = (MORNING_STEPS + chunk - 1) // chunk
     if not args.no_e2e:
         torch.cuda.synchronize()
         h2d = sum(a.nbytes for a in (net.edge_src, net.edge_dst, net.edge_lanes, net.edge_length_m,
                                       net.edge_speed_limit_mps, net.edge_class, net.node_type, net.node_cycle_steps,
                                       net.node_offset_steps, net.edge_green_start, net.edge_green_len,
                                       net.conn_lane_mask, tr.route_off, tr.route_edges, tr.depart_time_s))
-        n_chunks = args.warmup + args.steps
         t0 = time.perf_counter()
         sim2 = manta.Sim(net, stream=stream, t0_step=T0_STEP)
         sim2.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
         t_load = time.perf_counter() - t0
-        upd = 0
-        for _ in range(n_chunks):
-            sim2.step(chunk)
+        left = MORNING_STEPS
+        while left > 0:
+            sim2.step(min(chunk, left))
+            left -= chunk
             st = sim2.stats()                 # device -> host read of the step's result
         upd = st["vehicle_updates"]
         t_e2e = time.perf_counter() - t0
-        morning_steps = n_chunks * chunk
-        e2e = {"value": upd / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d // n_chunks),
+        morning = round(t_e2e - t_load, 3)
+        e2e = {"value": upd / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d // n_morning),
                "d2h_bytes_per_step": 96, "seconds": round(t_e2e, 3), "create_load_s": round(t_load, 3),
-               "sim_steps": morning_steps}
-        if morning_steps >= MORNING_STEPS:
-            morning = round(t_e2e - t_load, 3)
+               "sim_steps": MORNING_STEPS, "bench_steps": n_morning,
+               "window": "05:00-12:00 (the whole morning, whatever --steps/--warmup are)"}
         sim2.close()
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     peak, peak_kind = _peaks()
-    bytes_alg = algorithmic_bytes(d)
     per_launch_s = elapsed / max(1, args.steps)
+    bytes_alg = algorithmic_bytes(d)
     achieved = bytes_alg / max(1, args.steps) / per_launch_s / 1e9
     tpu = measured_traffic_per_update()
     traffic = None if tpu is None else int(tpu * d["vehicle_updates"] / max(1, args.steps))
+    # per simulated hour and over the peak hour (07:30-08:30)
+    first = T0_STEP + args.warmup * chunk
+    hours, peak_chunks = {}, []
+    for i, (t, c) in enumerate(zip(times, per_chunk)):
+        k_lo = first + i * chunk
+        t_s = k_lo * 0.5
+        hours.setdefault(int(t_s // 3600), []).append((t, c))
+        if PEAK_HOUR[0] <= t_s and t_s + chunk * 0.5 <= PEAK_HOUR[1]:
+            peak_chunks.append((t, c))
+
+    def summary(rows):
+        tt = sum(r[0] for r in rows)
+        cc = {k: sum(r[1][k] for r in rows) for k in keys}
+        ab = algorithmic_bytes(cc)
+        u = max(1, cc["vehicle_updates"])
+        return {"seconds": round(tt, 4), "vehicle_updates": cc["vehicle_updates"],
+                "updates_per_s": cc["vehicle_updates"] / tt, "algorithmic_bytes_per_update": round(ab / u, 2),
+                "cells_per_update": round(cc["cells_scanned"] / u, 2),
+                "achieved_gbs": round(ab / tt / 1e9, 1), "frac": round(ab / tt / 1e9 / peak, 4)}
+
+    hourly = {f"{h:02d}:00-{h + 1:02d}:00": summary(r) for h, r in sorted(hours.items())}
+    peak_hour = summary(peak_chunks) if len(peak_chunks) == 4 else None
     out = {
         "metric": METRIC, "value": total_updates / elapsed, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
@@ -312,21 +373,35 @@ def run_gpu(args):
         "data": "synthetic (seeded metro-shaped lattice network and gravity-model trips)",
         "config": {"workload": WORKLOAD,
                    "sim_steps_per_bench_step": chunk, "t0_step": T0_STEP,
-                   "timed_sim_window": [T0_STEP + args.warmup * chunk, T0_STEP + (args.warmup + args.steps) * chunk],
+                   "timed_sim_window": [first, first + args.steps * chunk],
                    "l2": "flushed between timed steps (256 MB write) and working set > L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "gpu_launches": args.steps * ((chunk + 2047) // 2048),
         "morning_wall_s": morning,
+        "morning_wall_note": "05:00-12:00 stepped through the C ABI with a stats read per bench step, create "
+                             "and load excluded (the e2e run)",
+        "morning_device_s": round(sum(warm_times) + elapsed, 3) if args.warmup + args.steps >= n_morning else None,
         "counters": d,
         "phase_ms_timed": phase_ms,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(bytes_alg / max(1, args.steps))},
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": int(bytes_alg / max(1, args.steps)),
+                     "algorithmic_bytes_per_update": round(bytes_alg / max(1, d["vehicle_updates"]), 2),
+                     "formula": f"{BYTES_PER_UPDATE} B/update + {BYTES_PER_CELL} B/cell scanned + "
+                                f"{BYTES_PER_BOUNDARY} B/route read + {BYTES_PER_LC_EVAL} B/gap-acceptance "
+                                f"evaluation + {BYTES_PER_DEPARTURE} B/departure",
+                     "frac_with_link_statistics": round(
+                         (bytes_alg + BYTES_STATS_PER_UPDATE * d["vehicle_updates"]) / max(1, args.steps)
+                         / per_launch_s / 1e9 / peak, 4),
+                     "peak_hour": peak_hour,
+                     "traffic_model": {"bytes_per_launch": int(layout_bytes(d) / max(1, args.steps)),
+                                       "per_unit": LAYOUT_BYTES}},
+        "hourly": hourly,
         "clocks": clk.summary(),
         "e2e": e2e,
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(net, tr, args.cpu_steps)
+        out["cpu_baseline"] = cpu_baseline(net, tr, args.cpu_steps, stream)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
@@ -342,22 +417,57 @@ def _sample(tr, lo_s, hi_s):
     return off, tr.route_edges[idx], tr.depart_time_s[sel]
 
 
-def cpu_baseline(net, tr, n_steps):
-    """The CPU oracle, single-threaded, on a bounded sample of the workload:
-    the metro network from an empty start at 07:30 with the trips departing
-    07:30-07:40, `n_steps` steps."""
-    from oracle import oracle as O
+def peak_sample(net, tr):
+    """The bounded sample the CPU oracle is timed on: a dense peak-hour state
+    on the full metro network -- every trip departing 07:00-07:30 put along
+    its route at 07:30 by the seeded dense-state generator (about the number
+    of vehicles on the network at the peak) -- with the trips departing
+    07:00-08:00 loaded (the unplaced ones depart from their queues)."""
+    from paper_2007_03614_b300 import synth
     lo = 7.5 * 3600
-    off, edges, dep = _sample(tr, lo, lo + 600)
-    s = O.OracleSim(net, t0_step=int(lo / 0.5), n_stats_windows=4)
-    s.load_trips(off, edges, dep)
-    t0 = time.perf_counter()
+    off, edges, dep = _sample(tr, lo - 1800, lo + 1800)
+    sub = synth.Trips(route_off=off, route_edges=edges, depart_time_s=dep)
+    pl = synth.dense_state(net, sub, lo - 1800, lo, seed=7)
+    return int(lo / 0.5), sub, pl
+
+
+def cpu_baseline(net, tr, n_steps, stream=None):
+    """The CPU oracle, single-threaded, on a bounded sample: `n_steps` steps
+    from the dense peak-hour state of peak_sample; the GPU's rate on the
+    identical sample is reported beside it."""
+    from oracle import oracle as O
+    t0, sub, pl = peak_sample(net, tr)
+    s = O.OracleSim(net, t0_step=t0, n_stats_windows=4)
+    s.load_trips(sub.route_off, sub.route_edges, sub.depart_time_s)
+    s.place_many(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
+    t = time.perf_counter()
     s.step(n_steps)
-    dt = time.perf_counter() - t0
+    dt = time.perf_counter() - t
     upd = s.stats()["vehicle_updates"]
-    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"metro network, trips departing 07:30-07:40 ({len(dep)}), {n_steps} steps from an empty "
-                      f"network at 07:30, {upd} vehicle updates in {dt:.1f} s"}
+    s.close()
+    out = {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "host": host_cpu(),
+           "sample": f"dense peak-hour state on the metro network: {pl.n} vehicles placed at 07:30 "
+                     f"(trips departing 07:00-07:30), {sub.n_trips} trips loaded; {n_steps} steps, "
+                     f"{upd} vehicle updates in {dt:.1f} s"}
+    if stream is not None:
+        import torch
+        from paper_2007_03614_b300 import manta
+        g = manta.Sim(net, stream=stream, t0_step=t0, n_stats_windows=4)
+        g.load_trips(sub.route_off, sub.route_edges, sub.depart_time_s)
+        g.place(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        g.step(n_steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        gu = g.stats()["vehicle_updates"]
+        g.close()
+        gt = ev0.elapsed_time(ev1) / 1000.0
+        out["gpu_same_sample"] = {"value": gu / gt, "seconds": gt, "vehicle_updates": gu,
+                                  "same_updates_as_oracle": gu == upd}
+    return out
 
 
 def run_ensemble(args):
@@ -802,34 +912,37 @@ def run_stress(args):
 
 
 def run_reference(args):
+    """The oracle (this paper has no reference code) on the dense peak-hour
+    sample of peak_sample: each bench step is --ref-chunk oracle time steps."""
     rank, world = _dist()
     if rank != 0:
         return
     net, tr = workload()
     from oracle import oracle as O
-    lo = 7.5 * 3600
-    off, edges, dep = _sample(tr, lo, lo + 600)
-    s = O.OracleSim(net, t0_step=int(lo / 0.5), n_stats_windows=4)
-    s.load_trips(off, edges, dep)
+    t0, sub, pl = peak_sample(net, tr)
+    s = O.OracleSim(net, t0_step=t0, n_stats_windows=4)
+    s.load_trips(sub.route_off, sub.route_edges, sub.depart_time_s)
+    s.place_many(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
     per = args.ref_chunk
     for _ in range(args.warmup):
         s.step(per)
     u0 = s.stats()["vehicle_updates"]
-    t0 = time.perf_counter()
+    t = time.perf_counter()
     for _ in range(args.steps):
         s.step(per)
-    dt = time.perf_counter() - t0
+    dt = time.perf_counter() - t
     upd = s.stats()["vehicle_updates"] - u0
     v = upd / dt
-    sample = (f"metro network, trips departing 07:30-07:40 ({len(dep)}), empty start at 07:30; each step = "
-              f"{per} oracle time steps")
+    sample = (f"dense peak-hour state on the metro network ({pl.n} vehicles placed at 07:30, {sub.n_trips} "
+              f"trips loaded); each bench step = {per} oracle time steps")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * dt / max(1, args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sim_steps_per_bench_step": per,
                    "sample": "the oracle on a bounded sample of the workload (see cpu_baseline.sample)"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -840,8 +953,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--chunk", type=int, default=1800)
     ap.add_argument("--impl", default="manta", choices=["manta", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=200)
-    ap.add_argument("--ref-chunk", type=int, default=20)
+    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--ref-chunk", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="metro",

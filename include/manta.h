@@ -185,6 +185,26 @@ MANTA_API manta_status manta_edge_counters(manta_sim *sim, uint32_t *entries, ui
 MANTA_API manta_status manta_snapshot(manta_sim *sim, int64_t cap, int64_t *n_out, float *x, float *v, int32_t *edge,
                             uint8_t *lane, uint32_t *id, uint8_t *dwell, int32_t *route_pos);
 
+/* Test hook: puts n waiting trips directly on the network, as if each had
+ * driven to the stated place, so that a run can start from a dense traffic
+ * state instead of an empty network.  The paper has no counterpart (its runs
+ * start empty, Section II-D); the hook gives the same state as the same
+ * placements in the CPU oracle.  Placement i puts trip trip[i] on route
+ * entry route_pos[i] of its route (0 = its first edge), lane lane[i], front
+ * position x[i] cells from the start of that edge (0 <= x < cells), speed
+ * v[i] >= 0, dwell counter 0; its front cell of the current lane map gets its
+ * speed code.  A placed trip leaves its departure queue (the queue's other
+ * trips keep their order), counts as departed and adds an entry on its edge.
+ * Host arrays [n], copied.  Call once, after manta_load_trips and before the
+ * first step.  Errors: MANTA_E_STATE (no trips, already stepped or placed),
+ * MANTA_E_INVALID (a trip out of range or listed twice, a route position out
+ * of range; or a lane, position or cell not valid -- two placements on one
+ * cell, or a cell already taken -- which leaves the simulation unusable),
+ * MANTA_E_OOM, MANTA_E_CUDA.  The caller keeps the usual invariant of a lane:
+ * front cells at least veh_len_cells apart. */
+MANTA_API manta_status manta_place(manta_sim *sim, int64_t n, const int64_t *trip, const int32_t *route_pos,
+                                   const uint8_t *lane, const float *x, const float *v);
+
 /* Synchronises and copies the current lane map in canonical layout: edges in
  * id order, lanes in order, one byte per cell (0xFF empty, else the speed code
  * round(8 v) saturated at 254).  *n_out = total bytes; MANTA_E_INVALID if cap

@@ -905,6 +905,15 @@ OR_API int oracle_place(osim *S, int64_t id, int32_t route_pos, int32_t lane, fl
   return 0;
 }
 
+/* Test hook: oracle_place for placements 0 .. n-1 in order; returns -1 - i for
+ * the first placement i that fails, else 0.                                */
+OR_API int64_t oracle_place_many(osim *S, int64_t n, const int64_t *id, const int32_t *route_pos, const uint8_t *lane,
+                                 const float *x, const float *v) {
+  for (int64_t i = 0; i < n; ++i)
+    if (oracle_place(S, id[i], route_pos[i], (int32_t)lane[i], x[i], v[i]) != 0) return -1 - i;
+  return 0;
+}
+
 /* Invariants after a step: every lane's front cells at least L apart, map bytes
  * exactly the vehicles' speed codes, conservation. Returns 0 or an error code. */
 OR_API int oracle_check(osim *S, char *msg, int len) {

@@ -103,6 +103,8 @@ def _load():
         lib.oracle_permit.argtypes = [P, C.c_int32]
         lib.oracle_place.restype = C.c_int
         lib.oracle_place.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_float]
+        lib.oracle_place_many.restype = C.c_int64
+        lib.oracle_place_many.argtypes = [P, C.c_int64, P, P, P, P, P]
         lib.oracle_check.restype = C.c_int
         lib.oracle_check.argtypes = [P, C.c_char_p, C.c_int]
         lib.oracle_destroy.argtypes = [P]
@@ -221,6 +223,15 @@ class OracleSim:
         rc = self._lib.oracle_place(self._h, int(trip), int(route_pos), int(lane), float(x), float(v))
         if rc != 0:
             raise OracleError(f"place {rc}")
+
+    def place_many(self, trip, route_pos, lane, x, v):
+        """place() for every placement, in order."""
+        a = [np.ascontiguousarray(trip, np.int64), np.ascontiguousarray(route_pos, np.int32),
+             np.ascontiguousarray(lane, np.uint8), np.ascontiguousarray(x, np.float32),
+             np.ascontiguousarray(v, np.float32)]
+        rc = self._lib.oracle_place_many(self._h, len(a[0]), *[_p(q) for q in a])
+        if rc != 0:
+            raise OracleError(f"place_many: placement {-1 - rc} failed")
 
     def set_lane_closure(self, edge, lane, k0, k1):
         rc = self._lib.oracle_set_lane_closure(self._h, int(edge), int(lane), int(k0), int(k1))

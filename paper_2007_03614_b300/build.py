@@ -36,6 +36,33 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+# Test builds of the same sources: each defines compile-time knobs that move
+# the kernel onto paths the product build only takes at sizes a parity test
+# cannot afford (a lane-change candidate list that overflows shared memory),
+# or selects the non-default leader-walk batch sizes.  Same ABI; results must
+# equal the product build's bit for bit.
+VARIANTS = {
+    "lccap": ["-DMANTA_LC_CAP=4"],
+    "walk4": ["-DMANTA_WALK_CHUNKS=4", "-DMANTA_FIRST_CHUNKS=2"],
+    "walk16": ["-DMANTA_WALK_CHUNKS=16", "-DMANTA_FIRST_CHUNKS=8"],
+}
+
+
+def variant_path(name: str) -> str:
+    return os.path.join(PKG, f"libmanta_{name}.so")
+
+
+def build_variant(name: str, force: bool = False) -> str:
+    """Build the test variant `name` of libmanta.so (product flags plus its
+    defines) and return its path."""
+    out = variant_path(name)
+    deps = [os.path.join(CSRC, d) for d in DEPS] + [os.path.join(INCLUDE, "manta.h"), os.path.abspath(__file__)]
+    if force or _stale(out, deps):
+        subprocess.check_call(["nvcc", *NVCC_FLAGS, *VARIANTS[name], "-I", INCLUDE, "-o", out,
+                               *[os.path.join(CSRC, s) for s in SOURCES]])
+    return out
+
+
 def build(force: bool = False, verbose: bool = False, fast: bool = True) -> str:
     deps = [os.path.join(CSRC, d) for d in DEPS] + [os.path.join(INCLUDE, "manta.h")]
     todo = [(LIB, NVCC_FLAGS)] + ([(LIB_FAST, NVCC_FAST_FLAGS)] if fast else [])

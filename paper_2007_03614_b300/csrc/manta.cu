@@ -85,6 +85,48 @@ __global__ void prime_kernel(Params p, uint32_t hi, int cb) {
   }
 }
 
+// Puts placement i (trip trip[i] at absolute route entry rabs[i], lane, x, v)
+// on the network in vehicle slot i and active-list position i: the vehicle
+// record, its front cell in the current lane map (claimed with a compare-
+// and-swap on the aligned word, so two placements on one cell are caught)
+// and the entry count of its edge.  The lowest failing index goes to *bad.
+__global__ void place_kernel(Params p, const uint32_t *trip, const uint32_t *rabs, const uint8_t *lane,
+                             const float *xs, const float *vs, uint32_t n, int cb, unsigned long long *bad) {
+  uint8_t *cur = cb ? p.atlas1 : p.atlas0;
+  uint32_t *act = p.act0;                      // act_sel is 0 before the first step
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t j = trip[i], r = rabs[i], l = lane[i];
+    const float x = xs[i], v = vs[i];
+    const uint32_t e = p.route[r] & MANTA_EDGE_MASK;
+    const EdgeMeta em = load_em(p, e);
+    const uint32_t C = cells_of(em.cnl);
+    if ((int)l >= lanes_of(em.cnl) || !(x >= 0.0f) || !(x < __uint2float_rn(C))) {
+      atomicMin(bad, (unsigned long long)i);
+      continue;
+    }
+    const uint32_t off = em.row0 + l * stride_of(C) + (uint32_t)(int)floorf(x);
+    unsigned *word = reinterpret_cast<unsigned *>(cur + (off & ~3u));
+    const unsigned sh = 8u * (off & 3u);
+    bool ok = false;
+    unsigned old = *word;
+    for (int tries = 0; tries < 16; ++tries) {      // at most 4 placements share a word
+      if (((old >> sh) & 0xFFu) != MANTA_EMPTY) break;
+      const unsigned nw = (old & ~(0xFFu << sh)) | ((unsigned)speed_code(v) << sh);
+      const unsigned got = atomicCAS(word, old, nw);
+      if (got == old) { ok = true; break; }
+      old = got;
+    }
+    if (!ok) { atomicMin(bad, (unsigned long long)i); continue; }
+    Veh w;
+    w.x = x; w.v = v; w.id = j; w.rc = r; w.rend = p.route_off[j + 1u]; w.e = e;
+    w.ld = ld_for_entry(p, r, l); w.pcell = MANTA_NONE; w.em = em;
+    w.em.lim = driver_limit(p, em.lim, j, r);
+    store_veh(p, i, w);
+    act[i] = i;
+    atomicAdd(p.entry + e, 1u);
+  }
+}
+
 __global__ void barrier_selftest_kernel(Ctl *ctl, uint64_t limit_ns) {
   __shared__ int s_ok;
   if (blockIdx.x == 0) return;   // this block never arrives
@@ -111,6 +153,12 @@ struct manta_sim {
   int64_t k = 0, n_trips = 0;
   uint32_t prime_hi = 0;
   std::vector<uint32_t> route_off_h;
+  // host copies kept from manta_load_trips for manta_place: departure queues
+  // (offsets by first edge, trips in (step, id) order), trips in departure
+  // order, departure steps and first edges
+  std::vector<uint32_t> q_off_h, q_trip_h, dorder_h, first_h;
+  std::vector<int64_t> dstep_h;
+  bool placed = false;
   std::vector<EdgeMeta> em_h;
   std::vector<long long> clo_k0, clo_k1;
   int grid[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // co-resident grid size of every launch shape
@@ -623,6 +671,11 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   P.nclo = d_nclo;
   P.route = d_route; P.route_off = d_roff; P.q_off = d_qoff; P.q_trip = d_qtrip;
   P.due_step = d_due; P.due_edge = d_due_e; P.n_trips = (uint32_t)n;
+  S->q_off_h = std::move(q_off);
+  S->q_trip_h = std::move(order);
+  S->dorder_h = std::move(dorder);
+  S->first_h = std::move(first);
+  S->dstep_h = std::move(dstep);
   S->route_off_h = std::move(roff);
   S->n_trips = n;
   S->prime_hi = prime_hi;
@@ -636,6 +689,118 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   if (cudaStreamSynchronize(S->stream) != cudaSuccess)
     return fail(MANTA_E_CUDA, std::string("manta_load_trips: ") + cudaGetErrorString(cudaGetLastError()));
   S->loaded = true;
+  return MANTA_OK;
+}
+
+manta_status manta_place(manta_sim *S, int64_t n, const int64_t *trip, const int32_t *route_pos, const uint8_t *lane,
+                         const float *x, const float *v) {
+  g_err.clear();
+  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
+  if (!S->loaded) return fail(MANTA_E_STATE, "no trips loaded");
+  if (S->placed || S->k != S->cfg.t0_step) return fail(MANTA_E_STATE, "placement runs once, before the first step");
+  if (S->dead) return fail(MANTA_E_STATE, "simulation stopped after an error");
+  if (n < 0 || n > S->n_trips) return fail(MANTA_E_INVALID, "placement count out of range");
+  if (n > 0 && (!trip || !route_pos || !lane || !x || !v)) return fail(MANTA_E_INVALID, "placement array is NULL");
+  const size_t NT = (size_t)S->n_trips;
+  std::vector<uint8_t> is_placed(NT, 0);
+  std::vector<uint32_t> h_trip((size_t)n), h_rabs((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t j = trip[i];
+    if (j < 0 || j >= S->n_trips || is_placed[(size_t)j])
+      return fail(MANTA_E_INVALID, "placement " + std::to_string(i) + ": trip out of range or placed twice");
+    is_placed[(size_t)j] = 1;
+    const int64_t r = (int64_t)S->route_off_h[(size_t)j] + route_pos[i];
+    if (route_pos[i] < 0 || r >= (int64_t)S->route_off_h[(size_t)j + 1])
+      return fail(MANTA_E_INVALID, "placement " + std::to_string(i) + ": route position out of range");
+    if (!(v[i] >= 0.0f) || !(v[i] < 1.0e4f))
+      return fail(MANTA_E_INVALID, "placement " + std::to_string(i) + ": speed out of range");
+    h_trip[(size_t)i] = (uint32_t)j;
+    h_rabs[(size_t)i] = (uint32_t)r;
+  }
+  // Departure queues: the placed trips of each first edge move to its front,
+  // in placement order, and the queue head starts past them.
+  const int32_t E = S->E;
+  std::vector<uint32_t> qpos(E, 0);
+  for (int64_t i = 0; i < n; ++i) qpos[S->first_h[h_trip[(size_t)i]]]++;
+  {
+    std::vector<uint32_t> at(E), rest(E);
+    for (int32_t e = 0; e < E; ++e) { at[e] = S->q_off_h[e]; rest[e] = S->q_off_h[e] + qpos[e]; }
+    std::vector<uint32_t> q2(S->q_trip_h.size());
+    for (int64_t i = 0; i < n; ++i) {
+      const uint32_t j = h_trip[(size_t)i];
+      q2[at[S->first_h[j]]++] = j;
+    }
+    for (int32_t e = 0; e < E; ++e)
+      for (uint32_t q = S->q_off_h[e]; q < S->q_off_h[e + 1]; ++q)
+        if (!is_placed[S->q_trip_h[q]]) q2[rest[e]++] = S->q_trip_h[q];
+    S->q_trip_h.swap(q2);
+  }
+  // Trips that join departure queues when due: the unplaced ones, in
+  // departure order; the freed tail is never due.
+  std::vector<int32_t> due_step(NT, INT32_MAX);
+  std::vector<uint32_t> due_edge(NT, 0u);
+  uint32_t m = 0, prime_hi = 0;
+  for (size_t i = 0; i < NT; ++i) {
+    const uint32_t j = S->dorder_h[i];
+    if (is_placed[j]) continue;
+    const int64_t d = S->dstep_h[j];
+    due_step[m] = (int32_t)std::max<int64_t>(std::min<int64_t>(d, INT32_MAX), INT32_MIN);
+    due_edge[m] = S->first_h[j];
+    ++m;
+    if (d <= S->k) prime_hi = m;
+  }
+  Params &P = S->P;
+  bool ok = true;
+  uint32_t *d_trip = dalloc<uint32_t>(S, (size_t)n, &ok);
+  uint32_t *d_rabs = dalloc<uint32_t>(S, (size_t)n, &ok);
+  uint8_t *d_lane = dalloc<uint8_t>(S, (size_t)n, &ok);
+  float *d_x = dalloc<float>(S, (size_t)n, &ok);
+  float *d_v = dalloc<float>(S, (size_t)n, &ok);
+  unsigned long long *d_bad = dalloc<unsigned long long>(S, 1, &ok);
+  if (!ok) return fail(MANTA_E_OOM, "device allocation failed in manta_place");
+  const int cb = (int)(S->k & 1);
+  Ctl c0;
+  memset(&c0, 0, sizeof(c0));
+  c0.due_pos = prime_hi;
+  c0.due_hi = prime_hi;
+  c0.k_next = S->k;
+  c0.n_act[cb] = (uint32_t)n;
+  c0.n_slots = (uint32_t)n;
+  c0.cnt[CNT_DEP] = (unsigned long long)n;
+  const bool cp =
+      upload(S, d_trip, h_trip) && upload(S, d_rabs, h_rabs) &&
+      (n == 0 || cudaMemcpyAsync(d_lane, lane, (size_t)n, cudaMemcpyHostToDevice, S->stream) == cudaSuccess) &&
+      (n == 0 || cudaMemcpyAsync(d_x, x, 4 * (size_t)n, cudaMemcpyHostToDevice, S->stream) == cudaSuccess) &&
+      (n == 0 || cudaMemcpyAsync(d_v, v, 4 * (size_t)n, cudaMemcpyHostToDevice, S->stream) == cudaSuccess) &&
+      cudaMemsetAsync(d_bad, 0xFF, sizeof(unsigned long long), S->stream) == cudaSuccess &&
+      upload(S, const_cast<uint32_t *>(P.q_trip), S->q_trip_h) &&
+      upload(S, P.q_pos, qpos) &&
+      upload(S, const_cast<int32_t *>(P.due_step), due_step) &&
+      upload(S, const_cast<uint32_t *>(P.due_edge), due_edge) &&
+      cudaMemsetAsync(P.pending, 0, sizeof(uint32_t) * (size_t)E, S->stream) == cudaSuccess &&
+      cudaMemcpyAsync(P.ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
+  S->placed = true;
+  if (!cp) { S->dead = true; return fail(MANTA_E_CUDA, "upload failed in manta_place"); }
+  if (prime_hi > 0) {
+    const int blocks = (int)std::min<uint32_t>((prime_hi + kBlock - 1) / kBlock, 4096u);
+    prime_kernel<<<blocks, kBlock, 0, S->stream>>>(P, prime_hi, cb);
+  }
+  if (n > 0) {
+    const int blocks = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 4096);
+    place_kernel<<<blocks, kBlock, 0, S->stream>>>(P, d_trip, d_rabs, d_lane, d_x, d_v, (uint32_t)n, cb, d_bad);
+  }
+  unsigned long long bad = ~0ull;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, S->stream) != cudaSuccess ||
+      cudaStreamSynchronize(S->stream) != cudaSuccess) {
+    S->dead = true;
+    return fail(MANTA_E_CUDA, "placement kernels failed in manta_place");
+  }
+  if (bad != ~0ull) {
+    S->dead = true;
+    return fail(MANTA_E_INVALID, "placement " + std::to_string(bad) +
+                                     ": lane, position or cell not valid (the simulation is unusable)");
+  }
   return MANTA_OK;
 }
 

@@ -62,8 +62,16 @@ constexpr int kWarpWords = kP3Words + 32 * kSlotBytes / 4;
 // when its record pass visits n_rec list entries with a stride of rstride
 // threads (at least half the grid) and it runs its share of n_items
 // merge-phase items (grid of gsz threads)
+// (MANTA_LC_CAP, defined only in a test build, lowers the capacity so that
+// the overflow region takes most candidates.)
 __host__ __device__ constexpr uint32_t lc_cap_of(int threads) {
+#ifdef MANTA_LC_CAP
+  return (uint32_t)MANTA_LC_CAP < (uint32_t)(threads / 32) * kWarpWords * 4u / 64u
+             ? (uint32_t)MANTA_LC_CAP
+             : (uint32_t)(threads / 32) * kWarpWords * 4u / 64u;
+#else
   return (uint32_t)(threads / 32) * kWarpWords * 4u / 64u;
+#endif
 }
 __host__ __device__ constexpr uint32_t lc_bound(int threads, uint32_t rstride, uint32_t gsz, uint32_t n_rec,
                                                 uint32_t n_items) {

@@ -52,7 +52,7 @@ EXPORTS = ("manta_default_config", "manta_create", "manta_load_trips", "manta_st
            "manta_set_variant", "manta_get_variant", "manta_autotune", "manta_graph_capture",
            "manta_graph_launch", "manta_graph_destroy", "manta_checkpoint_save", "manta_checkpoint_restore",
            "manta_checkpoint_step", "manta_checkpoint_bytes", "manta_checkpoint_destroy", "manta_tape_start",
-           "manta_tape_stop", "manta_tape_copy", "manta_adjoint", "manta_replay")
+           "manta_tape_stop", "manta_tape_copy", "manta_adjoint", "manta_replay", "manta_place")
 
 _lib = None
 
@@ -63,13 +63,19 @@ class MantaError(RuntimeError):
         self.status = status
 
 
-def load_library():
-    """Load libmanta.so (build it first with paper_2007_03614_b300.build)."""
+_libs = {}
+
+
+def load_library(path=None):
+    """Load libmanta.so (build it first with paper_2007_03614_b300.build), or,
+    with `path`, another build of the same library (a test variant); each
+    path is loaded once."""
     global _lib
-    if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError(f"{LIB_PATH} is missing: run paper_2007_03614_b300.build.build()")
-        lib = C.CDLL(LIB_PATH)
+    path = path or LIB_PATH
+    if path not in _libs:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: run paper_2007_03614_b300.build.build()")
+        lib = C.CDLL(path)
         P = C.c_void_p
         lib.manta_default_config.argtypes = [C.POINTER(MantaConfig)]
         lib.manta_create.restype = C.c_int
@@ -134,13 +140,17 @@ def load_library():
         lib.manta_adjoint.argtypes = [P, P, P, P, P]
         lib.manta_replay.restype = C.c_int
         lib.manta_replay.argtypes = [P, P, P, P, P, P]
-        _lib = lib
-    return _lib
+        lib.manta_place.restype = C.c_int
+        lib.manta_place.argtypes = [P, C.c_int64, P, P, P, P, P]
+        _libs[path] = lib
+    if path == LIB_PATH:
+        _lib = _libs[path]
+    return _libs[path]
 
 
-def _check(rc):
+def _check(rc, lib=None):
     if rc != OK:
-        raise MantaError(rc, _lib.manta_last_error().decode())
+        raise MantaError(rc, (lib or _lib).manta_last_error().decode())
 
 
 def default_config(**over) -> MantaConfig:
@@ -183,8 +193,8 @@ TAPE_DTYPE = np.dtype([("x", np.float32), ("v", np.float32), ("s", np.float32), 
 class Sim:
     """One simulation on the current CUDA device (see include/manta.h)."""
 
-    def __init__(self, net, stream=None, **cfg):
-        lib = load_library()
+    def __init__(self, net, stream=None, library=None, **cfg):
+        lib = load_library(library)
         self._lib = lib
         self.cfg = default_config(**cfg)
         keep = []
@@ -207,7 +217,7 @@ class Sim:
                               _p(arr(net.node_offset_steps, np.int32)), _p(arr(net.edge_green_start, np.int16)),
                               _p(arr(net.edge_green_len, np.int16)), _p(arr(net.conn_lane_mask, np.uint32)),
                               C.byref(self.cfg), _stream_handle(stream), C.byref(h))
-        _check(rc)
+        _check(rc, lib)
         self._h = h
         self.n_trips = 0
 
@@ -222,18 +232,26 @@ class Sim:
         ro = np.ascontiguousarray(route_off, dtype=np.int64)
         re = np.ascontiguousarray(route_edges, dtype=np.int32)
         dt = np.ascontiguousarray(depart_time_s, dtype=np.float32)
-        _check(self._lib.manta_load_trips(self._h, len(dt), _p(ro), _p(re), _p(dt)))
+        _check(self._lib.manta_load_trips(self._h, len(dt), _p(ro), _p(re), _p(dt)), self._lib)
         self.n_trips = len(dt)
 
+    def place(self, trip, route_pos, lane, x, v):
+        """Put waiting trips on the network at (route position, lane, x, v)
+        before the first step (manta_place)."""
+        a = [np.ascontiguousarray(trip, np.int64), np.ascontiguousarray(route_pos, np.int32),
+             np.ascontiguousarray(lane, np.uint8), np.ascontiguousarray(x, np.float32),
+             np.ascontiguousarray(v, np.float32)]
+        _check(self._lib.manta_place(self._h, len(a[0]), *[_p(q) for q in a]), self._lib)
+
     def set_lane_closure(self, edge, lane, k0, k1):
-        _check(self._lib.manta_set_lane_closure(self._h, int(edge), int(lane), int(k0), int(k1)))
+        _check(self._lib.manta_set_lane_closure(self._h, int(edge), int(lane), int(k0), int(k1)), self._lib)
 
     def step(self, n=1):
-        _check(self._lib.manta_step(self._h, int(n)))
+        _check(self._lib.manta_step(self._h, int(n)), self._lib)
 
     def stats(self) -> dict:
         s = MantaStats()
-        _check(self._lib.manta_stats(self._h, C.byref(s)))
+        _check(self._lib.manta_stats(self._h, C.byref(s)), self._lib)
         return s.as_dict()
 
     def edge_counters(self, window=0) -> dict:
@@ -241,7 +259,7 @@ class Sim:
         out = dict(entries=np.zeros(E, np.uint32), exits=np.zeros(E, np.uint32),
                    speed_sum=np.zeros(E, np.uint64), speed_cnt=np.zeros(E, np.uint32))
         _check(self._lib.manta_edge_counters(self._h, _p(out["entries"]), _p(out["exits"]),
-                                             _p(out["speed_sum"]), _p(out["speed_cnt"]), int(window)))
+                                             _p(out["speed_sum"]), _p(out["speed_cnt"]), int(window)), self._lib)
         return out
 
     def snapshot(self) -> dict:
@@ -252,12 +270,12 @@ class Sim:
         cnt = C.c_int64()
         _check(self._lib.manta_snapshot(self._h, n, C.byref(cnt), *[_p(out[k]) for k in
                                                                    ("x", "v", "edge", "lane", "id", "dwell",
-                                                                    "route_pos")]))
+                                                                    "route_pos")]), self._lib)
         return {k: a[:cnt.value] for k, a in out.items()}
 
     def phase_times_ms(self) -> np.ndarray:
         out = np.zeros(4, np.float64)
-        _check(self._lib.manta_phase_times(self._h, _p(out)))
+        _check(self._lib.manta_phase_times(self._h, _p(out)), self._lib)
         return out
 
     @property
@@ -266,7 +284,7 @@ class Sim:
 
     @variant.setter
     def variant(self, v):
-        _check(self._lib.manta_set_variant(self._h, int(v)))
+        _check(self._lib.manta_set_variant(self._h, int(v)), self._lib)
 
     def autotune(self, trial_steps=60, rounds=1):
         """Times every launch shape on the live run (which advances by
@@ -276,27 +294,27 @@ class Sim:
         n = int(self._lib.manta_variant_count())
         ms = np.zeros(n, np.float32)
         ch = C.c_int32()
-        _check(self._lib.manta_autotune(self._h, int(trial_steps), int(rounds), C.byref(ch), _p(ms)))
+        _check(self._lib.manta_autotune(self._h, int(trial_steps), int(rounds), C.byref(ch), _p(ms)), self._lib)
         return ch.value, ms
 
     def checkpoint(self) -> "Checkpoint":
         return Checkpoint(self)
 
     def restore(self, ckpt: "Checkpoint"):
-        _check(self._lib.manta_checkpoint_restore(self._h, ckpt._h))
+        _check(self._lib.manta_checkpoint_restore(self._h, ckpt._h), self._lib)
 
     def tape_start(self, n_steps):
-        _check(self._lib.manta_tape_start(self._h, int(n_steps)))
+        _check(self._lib.manta_tape_start(self._h, int(n_steps)), self._lib)
 
     def tape_stop(self):
-        _check(self._lib.manta_tape_stop(self._h))
+        _check(self._lib.manta_tape_stop(self._h), self._lib)
 
     def tape_copy(self, n_steps) -> dict:
         """The recorded tape as arrays of shape (n_steps, n_trips)."""
         N = max(self.n_trips, 1)
         rec = np.zeros(int(n_steps) * N, dtype=TAPE_DTYPE)
         n = C.c_int64()
-        _check(self._lib.manta_tape_copy(self._h, rec.ctypes.data, rec.size, C.byref(n)))
+        _check(self._lib.manta_tape_copy(self._h, rec.ctypes.data, rec.size, C.byref(n)), self._lib)
         return {k: rec[k].reshape(int(n_steps), N) for k in TAPE_DTYPE.names}
 
     def adjoint(self, seed, lam_x, lam_v, grad):
@@ -305,7 +323,7 @@ class Sim:
         for t in (seed, lam_x, lam_v, grad):
             assert t.is_cuda and t.dtype == _torch().float64 and t.is_contiguous()
         _check(self._lib.manta_adjoint(self._h, seed.data_ptr(), lam_x.data_ptr(), lam_v.data_ptr(),
-                                       grad.data_ptr()))
+                                       grad.data_ptr()), self._lib)
 
     def replay(self, theta, x, v, present, sums):
         """Frozen-event replay of the recorded segment with parameters theta
@@ -315,7 +333,7 @@ class Sim:
             assert t.is_cuda and t.dtype == _torch().float64 and t.is_contiguous()
         assert present.is_cuda and present.dtype == _torch().uint8
         _check(self._lib.manta_replay(self._h, th.ctypes.data, x.data_ptr(), v.data_ptr(), present.data_ptr(),
-                                      sums.data_ptr()))
+                                      sums.data_ptr()), self._lib)
 
     def graph(self, n_steps) -> "Graph":
         return Graph(self, n_steps)
@@ -324,7 +342,7 @@ class Sim:
         nb = int(self._lib.manta_lane_map_bytes(self._h))
         buf = np.zeros(max(nb, 1), np.uint8)
         cnt = C.c_int64()
-        _check(self._lib.manta_lane_map(self._h, _p(buf), buf.size, C.byref(cnt)))
+        _check(self._lib.manta_lane_map(self._h, _p(buf), buf.size, C.byref(cnt)), self._lib)
         return buf[:cnt.value]
 
 
@@ -347,12 +365,12 @@ class Graph:
         self.sim = sim
         self.n_steps = int(n_steps)
         h = C.c_void_p()
-        _check(self._lib.manta_graph_capture(sim._h, self.n_steps, C.byref(h)))
+        _check(self._lib.manta_graph_capture(sim._h, self.n_steps, C.byref(h)), self._lib)
         self._h = h
 
     def launch(self, times=1):
         for _ in range(times):
-            _check(self._lib.manta_graph_launch(self._h))
+            _check(self._lib.manta_graph_launch(self._h), self._lib)
 
     def close(self):
         if self._h:
@@ -372,7 +390,7 @@ class Checkpoint:
     def __init__(self, sim):
         self._lib = sim._lib
         h = C.c_void_p()
-        _check(self._lib.manta_checkpoint_save(sim._h, C.byref(h)))
+        _check(self._lib.manta_checkpoint_save(sim._h, C.byref(h)), self._lib)
         self._h = h
 
     @property

@@ -329,6 +329,68 @@ def incident_closures(net: Network, n=200, k0=int(7.5 * 7200), k1=9 * 7200, seed
     return [(int(e), 0, int(k0), int(k1)) for e in np.sort(pick)]
 
 
+# --------------------------------------------------------------- dense state --
+@dataclass
+class Placement:
+    """Trips put directly on the network (the arguments of ``manta_place``)."""
+    trip: np.ndarray        # int64
+    route_pos: np.ndarray   # int32: entry of the trip's route
+    lane: np.ndarray        # uint8
+    x: np.ndarray           # float32: front position, cells from the start of the edge
+    v: np.ndarray           # float32: speed, m/s
+
+    @property
+    def n(self) -> int:
+        return int(self.trip.shape[0])
+
+
+def dense_state(net: Network, tr: Trips, depart_lo_s, depart_hi_s, *, seed=5, head_frac=0.15,
+                last_edge_frac=0.0, slot_cells=8, min_cells=8) -> Placement:
+    """A busy traffic state to start a run from, instead of an empty network.
+
+    Every trip departing in [depart_lo_s, depart_hi_s) is put somewhere along
+    its own route: a route entry drawn uniformly (or, with probability
+    `last_edge_frac`, its last entry, so it arrives soon), a lane drawn
+    uniformly among that edge's lanes, and a front cell in one of the edge's
+    slots of `slot_cells` cells (cell = slot * slot_cells + 0..3, so fronts in
+    one lane are at least slot_cells - 3 = 5 cells apart).  With probability
+    `head_frac` the slot is the edge's last one, at 50-100% of the speed
+    limit, so many vehicles reach a node in the first steps; otherwise the
+    slot is uniform and the speed uniform in [0, limit).  One vehicle per
+    (edge, lane, slot): of several drawn, the first in a seeded random order
+    stays and the others stay waiting in their departure queues.  An edge has
+    max(min_cells, round(length / 1 m)) cells, the lane map's cell rule of
+    Section II-D with the default vehicle length and jam gap.  Placements are
+    returned in trip order."""
+    rng = np.random.default_rng(seed)
+    cand = np.nonzero((tr.depart_time_s >= depart_lo_s) & (tr.depart_time_s < depart_hi_s))[0].astype(np.int64)
+    n = cand.size
+    ro = tr.route_off
+    rlen = ro[cand + 1] - ro[cand]
+    pos = np.minimum((rng.random(n) * rlen).astype(np.int64), rlen - 1)
+    last = rng.random(n) < last_edge_frac
+    pos[last] = rlen[last] - 1
+    e = tr.route_edges[ro[cand] + pos].astype(np.int64)
+    lanes = net.edge_lanes.astype(np.int64)[e]
+    lane = np.minimum((rng.random(n) * lanes).astype(np.int64), lanes - 1)
+    cells = np.maximum(min_cells, np.floor(net.edge_length_m.astype(np.float64) + 0.5).astype(np.int64))[e]
+    n_slot = (cells - 4) // slot_cells + 1
+    head = rng.random(n) < head_frac
+    slot = np.where(head, n_slot - 1, np.minimum((rng.random(n) * n_slot).astype(np.int64), n_slot - 1))
+    cell = slot * slot_cells + rng.integers(0, 4, n)
+    lim = net.edge_speed_limit_mps.astype(np.float64)[e]
+    v = np.where(head, lim * rng.uniform(0.5, 1.0, n), lim * rng.random(n))
+    x = cell + rng.random(n) * 0.999
+    # one vehicle per (edge, lane, slot)
+    lane0 = np.concatenate([[0], np.cumsum(net.edge_lanes.astype(np.int64))[:-1]])
+    key = (lane0[e] + lane) * (1 << 20) + slot
+    order = rng.permutation(n)
+    _, first = np.unique(key[order], return_index=True)
+    keep = np.sort(order[first])
+    return Placement(trip=cand[keep], route_pos=pos[keep].astype(np.int32), lane=lane[keep].astype(np.uint8),
+                     x=x[keep].astype(np.float32), v=v[keep].astype(np.float32))
+
+
 # ------------------------------------------------------------------ ensemble --
 @dataclass
 class Ensemble:

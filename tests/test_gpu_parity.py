@@ -195,13 +195,6 @@ def test_barrier_wait_runs_out_and_context_survives():
 
 
 # ------------------------------------------------------------------ metro --
-@pytest.fixture(scope="module")
-def metro():
-    net = synth.metro_network()
-    tr = synth.metro_trips(net)
-    return net, tr
-
-
 def _subset(tr, lo_s, hi_s):
     sel = np.nonzero((tr.depart_time_s >= lo_s) & (tr.depart_time_s < hi_s))[0]
     routes = [tr.route_edges[tr.route_off[i]:tr.route_off[i + 1]] for i in sel]
@@ -244,6 +237,78 @@ def test_metro_incident_closures_bit_exact(metro):
     _compare_all(o, g, windows=(0,))
     with pytest.raises(manta.MantaError) as ei:
         g.set_lane_closure(0, 0, 0, 1)
+    assert ei.value.status == manta.E_STATE
+
+
+def test_metro_dense_state_bit_exact(metro):
+    """A dense mid-morning state on the full metro network, at the size the
+    benchmark runs: ~500k vehicles put on the network at 07:30 by the seeded
+    dense-state generator (the same placements on both sides), 300 steps in
+    one 150-step launch and three 50-step launches, bit for bit.  The state is
+    built to reach the kernel's full-size paths: in the first step far more
+    merge-phase items than half the warps (the record pass then shares warps
+    with merge items), more arrivals than a quarter of the active list within
+    150 steps (compaction), and a list long enough for guided chunk tails."""
+    net, tr = metro
+    lo = 7.5 * 3600
+    sub = _subset(tr, lo - 2700, lo + 300)
+    pl = synth.dense_state(net, sub, lo - 2700, lo, head_frac=0.15, last_edge_frac=0.3, seed=5)
+    assert pl.n > 450_000
+    t0 = int(lo / 0.5)
+    o, g = _pair(net, sub, t0_step=t0, n_stats_windows=4)
+    o.place_many(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
+    g.place(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
+    _compare_all(o, g, where="placed")
+    # merge-phase items of the first step, from the oracle's own event tape:
+    # crossing requests (crossed or held), arrivals
+    tape = o.record_tape(1)
+    o.step(1)
+    out = (tape["flags"][0] >> 6) & 7
+    present = (tape["flags"][0] & 1) != 0
+    items = int(np.sum(present & (out >= 1)))
+    assert items > 40_000, items
+    o.stop_tape()
+    o.step(149)
+    g.step(150)
+    _compare_all(o, g, where="dense step 150")
+    st = o.stats()
+    assert st["arrived"] > 0.25 * st["departed"]
+    for k in range(150, 300, 50):
+        o.step(50)
+        g.step(50)
+        _compare(o, g, f"dense step {k + 50}")
+    _compare_all(o, g, windows=(0,), where="dense step 300")
+    assert g.stats()["on_network"] > 300_000
+
+
+def test_place_rejects_bad_placements():
+    """manta_place validates what the host can see (trip, route position,
+    speed) before touching the device, and is refused after the first step."""
+    net = nets.line(3, length=100.0, lanes=2)
+    tr = nets.trips([[0, 1, 2], [1, 2], [0, 1]], [0.0, 0.0, 50.0])
+    g = manta.Sim(net)
+    nets.load(g, tr)
+    for bad in (dict(trip=[5]), dict(trip=[0, 0]), dict(route_pos=[3]), dict(v=[-1.0])):
+        args = dict(trip=[0], route_pos=[1], lane=[0], x=[10.0], v=[5.0])
+        args.update(bad)
+        n = len(args["trip"])
+        for k in ("route_pos", "lane", "x", "v"):
+            args[k] = (args[k] * n)[:n]
+        with pytest.raises(manta.MantaError) as ei:
+            g.place(**args)
+        assert ei.value.status == manta.E_INVALID
+    o = O.OracleSim(net)
+    nets.load(o, tr)
+    g.place([0, 1], [1, 0], [1, 0], [10.5, 40.25], [5.0, 0.0])
+    o.place_many([0, 1], [1, 0], [1, 0], [10.5, 40.25], [5.0, 0.0])
+    _compare_all(o, g)
+    for _ in range(40):
+        o.step(1)
+        g.step(1)
+        _compare(o, g)
+    _compare_all(o, g)
+    with pytest.raises(manta.MantaError) as ei:
+        g.place([2], [0], [0], [1.0], [0.0])
     assert ei.value.status == manta.E_STATE
 
 

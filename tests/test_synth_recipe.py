@@ -62,3 +62,40 @@ def test_metro_trips_recipe(metro):
     # gravity model with decay length 5.4 km: mean route about 11.8 km (the paper reports 11.3 km)
     lengths = np.add.reduceat(net.edge_length_m[edges].astype(np.float64), off[:-1])
     assert 10_500.0 < lengths.mean() < 13_000.0
+
+
+def test_dense_state_recipe(metro):
+    """The dense starting state (synth.dense_state): every placement lies on
+    its own trip's route, within its edge and lane; fronts in one lane are at
+    least L = 5 cells apart; the requested share sits in the last slot of its
+    edge; and the CPU oracle accepts the state and keeps its invariants
+    (conservation, map bytes = speed codes, fronts >= L apart) over 20 steps."""
+    from oracle import oracle as O
+    net = metro
+    tr = synth.metro_trips(net, n_trips=20_000)
+    lo = 7.5 * 3600.0
+    pl = synth.dense_state(net, tr, lo - 3600.0, lo, head_frac=0.2, seed=3)
+    assert pl.n > 2000
+    ro = tr.route_off
+    rlen = ro[pl.trip + 1] - ro[pl.trip]
+    assert np.all((pl.route_pos >= 0) & (pl.route_pos < rlen))
+    e = tr.route_edges[ro[pl.trip] + pl.route_pos].astype(np.int64)
+    assert np.all(pl.lane < net.edge_lanes[e])
+    cells = np.maximum(8, np.floor(net.edge_length_m.astype(np.float64) + 0.5).astype(np.int64))[e]
+    assert np.all((pl.x >= 0.0) & (pl.x < cells)) and np.all(pl.v >= 0.0)
+    assert np.all(pl.v <= net.edge_speed_limit_mps[e])
+    key = e * 16 + pl.lane
+    order = np.lexsort((np.floor(pl.x), key))
+    same = key[order][1:] == key[order][:-1]
+    assert np.all(np.diff(np.floor(pl.x[order]))[same] >= 5)
+    near_end = cells - np.floor(pl.x) <= 11
+    assert near_end.mean() > 0.15
+    o = O.OracleSim(net, t0_step=int(lo / 0.5), n_stats_windows=2)
+    o.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+    o.place_many(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
+    o.check()
+    st = o.stats()
+    assert st["on_network"] == pl.n and st["departed"] == pl.n
+    for _ in range(4):
+        o.step(5)
+        o.check()
