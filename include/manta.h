@@ -167,7 +167,13 @@ MANTA_API manta_status manta_set_lane_closure(manta_sim *sim, int32_t edge, int3
  * MANTA_E_CUDA. */
 MANTA_API manta_status manta_step(manta_sim *sim, int64_t n_steps);
 
-/* Synchronises the stream and returns the scalar counters. */
+/* Synchronises the stream and returns the scalar counters: the step clock,
+ * trips loaded / departed / arrived / on the network / waiting (Section II-D
+ * departures and arrivals), vehicle updates (Section V-B's workload: one per
+ * on-network vehicle and step), lane-map cells examined by leader scans
+ * (the atlas look-ups of Section II-D), clamps, lane changes and
+ * gap-acceptance evaluations (Eqs. 2-4), and route entries read by scans
+ * crossing a node. */
 MANTA_API manta_status manta_stats(manta_sim *sim, manta_stats_t *out);
 
 /* Synchronises and copies per-edge counters: entries and exits since the
@@ -180,8 +186,11 @@ MANTA_API manta_status manta_edge_counters(manta_sim *sim, uint32_t *entries, ui
 
 /* Synchronises and copies the on-network vehicles in ascending id into arrays
  * of capacity `cap`: front position in cells from the start of the edge,
- * speed, edge, lane, id, stop dwell counter, position in the route.  *n_out
- * receives the count; MANTA_E_INVALID if cap is too small.  Pointers may be NULL. */
+ * speed, edge, lane, id, stop dwell counter, position in the route -- the
+ * per-vehicle state the update of Section II-D carries from step to step
+ * (Eq. 1 position and speed; lane; the Section IV-C stop dwell).  A test and
+ * inspection hook.  *n_out receives the count; MANTA_E_INVALID if cap is too
+ * small.  Pointers may be NULL. */
 MANTA_API manta_status manta_snapshot(manta_sim *sim, int64_t cap, int64_t *n_out, float *x, float *v, int32_t *edge,
                             uint8_t *lane, uint32_t *id, uint8_t *dwell, int32_t *route_pos);
 
@@ -370,6 +379,30 @@ MANTA_API const char *manta_last_error(void);
  * block gave up and returned (the expected outcome), MANTA_OK if the wait
  * did not run out.  The context stays usable. */
 MANTA_API manta_status manta_selftest_barrier_timeout(int32_t limit_ms, void *cuda_stream);
+
+/* ---- test hooks for failure detection (no counterpart in the paper) ----
+ * 1 if this build of the library checks the indices of the step kernel's
+ * device writes (compiled with MANTA_CHECK_BOUNDS), else 0.  In a checked
+ * build every write of the step kernel into the lane maps, vehicle records,
+ * per-step lists, per-lane slots and statistics is checked against its
+ * array's capacity; a failing check skips the write, records the first
+ * failing site, and ends the launch at the next grid barrier; the next
+ * synchronising call returns MANTA_E_DEVICE (with the site in the message)
+ * and the simulation stops, while the CUDA context stays usable.  The
+ * product build compiles the checks away. */
+MANTA_API int32_t manta_debug_checks(void);
+/* Lowers the capacity the checked build allows for writes into a lane-map
+ * buffer to `bytes` (the buffers themselves stay as they are), so that a
+ * test can make an index check fail on an access that is in bounds.  No
+ * effect on a build without checks.  Errors: MANTA_E_INVALID. */
+MANTA_API manta_status manta_debug_limit_map(manta_sim *sim, int64_t bytes);
+/* Host-side fault injection on the calling thread: from now on, the nth
+ * device allocation (kind 0) or the nth host-to-device copy (kind 1) that
+ * the library makes fails as the CUDA call would (nth = 0 turns it off).
+ * The call that meets the fault returns MANTA_E_OOM or MANTA_E_CUDA;
+ * manta_destroy then releases everything allocated so far.
+ * Errors: MANTA_E_INVALID for another kind or nth < 0. */
+MANTA_API manta_status manta_debug_fail_nth(int32_t kind, int64_t nth);
 
 /* Runs a whole small simulation without allocating any device memory, for
  * callers that cannot call cudaMalloc: host applications whose device memory

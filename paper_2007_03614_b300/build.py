@@ -39,12 +39,14 @@ def _stale(out, deps):
 # Test builds of the same sources: each defines compile-time knobs that move
 # the kernel onto paths the product build only takes at sizes a parity test
 # cannot afford (a lane-change candidate list that overflows shared memory),
-# or selects the non-default leader-walk batch sizes.  Same ABI; results must
-# equal the product build's bit for bit.
+# select the non-default leader-walk batch sizes, or check every device write
+# index.  Same ABI; results must equal the product build's bit for bit.
 VARIANTS = {
     "lccap": ["-DMANTA_LC_CAP=4"],
     "walk4": ["-DMANTA_WALK_CHUNKS=4", "-DMANTA_FIRST_CHUNKS=2"],
     "walk16": ["-DMANTA_WALK_CHUNKS=16", "-DMANTA_FIRST_CHUNKS=8"],
+    # index checks on every device write of the step kernel (manta_debug_checks)
+    "check": ["-DMANTA_CHECK_BOUNDS"],
 }
 
 

@@ -207,10 +207,31 @@ struct Arena {
 };
 thread_local Arena *t_arena = nullptr;
 
+// Host-side fault injection (manta_debug_fail_nth): on this thread, the nth
+// device allocation or host-to-device copy made by the library from now on
+// fails as the CUDA call would have (0: off).
+thread_local int64_t t_fail_alloc = 0, t_fail_copy = 0;
+bool injected(int64_t &countdown) {
+  if (countdown <= 0) return false;
+  return --countdown == 0;
+}
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  if (injected(t_fail_alloc)) { *p = nullptr; return cudaErrorMemoryAllocation; }
+  return cudaMalloc(p, bytes);
+}
+cudaError_t h2d_async(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  if (injected(t_fail_copy)) return cudaErrorInvalidValue;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+}
+
 template <class T>
 T *dalloc(manta_sim *S, size_t n, bool *ok) {
   void *p = nullptr;
   if (n == 0) n = 1;
+  if (injected(t_fail_alloc)) {
+    *ok = false;
+    return nullptr;
+  }
   if (t_arena) {
     const size_t off = (t_arena->used + 255u) & ~(size_t)255u;
     if (off + n * sizeof(T) > t_arena->cap) {
@@ -233,7 +254,7 @@ T *dalloc(manta_sim *S, size_t n, bool *ok) {
 template <class T>
 bool upload(manta_sim *S, T *dst, const std::vector<T> &src) {
   if (src.empty()) return true;
-  return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
+  return h2d_async(dst, src.data(), src.size() * sizeof(T), S->stream) == cudaSuccess;
 }
 
 manta_status check_cfg(const manta_config *c) {
@@ -510,6 +531,8 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   P.t0 = cfg->t0_step; P.seed = cfg->seed; P.sigma_frac = cfg->speed_sigma_frac;
   P.E = (uint32_t)E; P.N = (uint32_t)N; P.n_stop = (uint32_t)stops.size(); P.mtab_n = (uint32_t)mtab.size();
   P.wait_limit_ns = kWaitLimitNs;
+  P.cap_map = bytes + kMapPad;
+  P.cap_lanes = lanes_total;
   S->k = cfg->t0_step;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -629,6 +652,9 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
                                                        (uint32_t)(NT + (size_t)S->E)));
   }
   P.lcq = dalloc<Veh>(S, NC, &ok); P.lcq_pos = dalloc<uint32_t>(S, NC, &ok);
+  P.cap_slots = (uint32_t)NT;
+  P.cap_list = (uint32_t)NT;
+  P.cap_lcq = (uint32_t)NC;
   P.req = dalloc<uint32_t>(S, NT, &ok); P.arr = dalloc<uint32_t>(S, NT, &ok);
   P.req_x = dalloc<float>(S, NT, &ok); P.req_v = dalloc<float>(S, NT, &ok); P.req_dw = dalloc<uint32_t>(S, NT, &ok);
   P.req_g = dalloc<uint32_t>(S, NT, &ok); P.req_t = dalloc<uint32_t>(S, NT, &ok);
@@ -638,8 +664,7 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   bool cp = upload(S, d_roff, roff) && upload(S, d_qoff, q_off) && upload(S, d_qtrip, order) &&
             upload(S, d_due, due_step) && upload(S, d_due_e, due_edge) && upload(S, d_out_off, h_out_off) &&
             upload(S, d_out_e, h_out_e) && upload(S, d_conn_off, h_conn_off) && upload(S, d_conn, S->conn);
-  cp = cp && (nr == 0 || cudaMemcpyAsync(d_route, route_edges, (size_t)nr * 4, cudaMemcpyHostToDevice, S->stream) ==
-                             cudaSuccess);
+  cp = cp && (nr == 0 || h2d_async(d_route, route_edges, (size_t)nr * 4, S->stream) == cudaSuccess);
   cp = cp && cudaMemsetAsync(d_nclo, 0, nbits * 4, S->stream) == cudaSuccess &&
        cudaMemsetAsync(d_starts, 0, nbits * 4, S->stream) == cudaSuccess &&
        cudaMemsetAsync(d_bad, 0xFF, sizeof(unsigned long long), S->stream) == cudaSuccess;
@@ -666,7 +691,7 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   c0.due_pos = prime_hi;
   c0.due_hi = prime_hi;
   c0.k_next = S->k;
-  cp = cp && cudaMemcpyAsync(P.ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, S->stream) == cudaSuccess;
+  cp = cp && h2d_async(P.ctl, &c0, sizeof(c0), S->stream) == cudaSuccess;
   if (!cp) return fail(MANTA_E_CUDA, "upload failed in manta_load_trips");
   P.nclo = d_nclo;
   P.route = d_route; P.route_off = d_roff; P.q_off = d_qoff; P.q_trip = d_qtrip;
@@ -829,7 +854,10 @@ manta_status sync_and_check(manta_sim *S, Ctl *c) {
   if (cudaMemcpy(c, S->P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(MANTA_E_CUDA, "reading the control block failed");
   if (c->err == 1) { S->dead = true; return fail(MANTA_E_TIMEOUT, "a device grid-barrier wait ran out"); }
-  if (c->err != 0) { S->dead = true; return fail(MANTA_E_DEVICE, "a device index check failed"); }
+  if (c->err != 0) {
+    S->dead = true;
+    return fail(MANTA_E_DEVICE, "a device index check failed (site " + std::to_string(c->err_info) + ")");
+  }
   return MANTA_OK;
 }
 }  // namespace
@@ -1149,6 +1177,31 @@ manta_status manta_selftest_barrier_timeout(int32_t limit_ms, void *cuda_stream)
   return MANTA_OK;
 }
 
+int32_t manta_debug_checks(void) {
+#ifdef MANTA_CHECK_BOUNDS
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+manta_status manta_debug_limit_map(manta_sim *S, int64_t bytes) {
+  g_err.clear();
+  if (!S) return fail(MANTA_E_INVALID, "sim is NULL");
+  if (bytes < 0 || (uint64_t)bytes > S->atlas_bytes + kMapPad) return fail(MANTA_E_INVALID, "bytes out of range");
+  S->P.cap_map = (uint64_t)bytes;
+  return MANTA_OK;
+}
+
+manta_status manta_debug_fail_nth(int32_t kind, int64_t nth) {
+  g_err.clear();
+  if (nth < 0) return fail(MANTA_E_INVALID, "nth < 0");
+  if (kind == 0) t_fail_alloc = nth;
+  else if (kind == 1) t_fail_copy = nth;
+  else return fail(MANTA_E_INVALID, "kind must be 0 (device allocation) or 1 (host-to-device copy)");
+  return MANTA_OK;
+}
+
 manta_status manta_run_noalloc(int32_t n_nodes, int32_t n_edges, const int32_t *edge_src, const int32_t *edge_dst,
                                const uint8_t *edge_lanes, const float *edge_length_m,
                                const float *edge_speed_limit_mps, const uint8_t *edge_class,
@@ -1249,7 +1302,7 @@ manta_status manta_checkpoint_save(manta_sim *S, manta_checkpoint **out) {
   size_t total = 0;
   for (const auto &q : parts) total += (q.second + 255u) & ~(size_t)255u;
   unsigned char *buf = nullptr;
-  if (cudaMalloc(&buf, total) != cudaSuccess) {
+  if (dev_malloc((void **)&buf, total) != cudaSuccess) {
     cudaGetLastError();
     return fail(MANTA_E_OOM, "checkpoint allocation failed");
   }
@@ -1304,7 +1357,7 @@ manta_status manta_tape_start(manta_sim *S, int64_t n_steps) {
     if (S->tape) cudaFree(S->tape);
     S->tape = nullptr;
     S->tape_cap = 0;
-    if (cudaMalloc(&S->tape, need * sizeof(TapeRec)) != cudaSuccess) {
+    if (dev_malloc((void **)&S->tape, need * sizeof(TapeRec)) != cudaSuccess) {
       cudaGetLastError();
       S->tape = nullptr;
       return fail(MANTA_E_OOM, "tape allocation failed");
@@ -1372,7 +1425,7 @@ manta_status manta_adjoint(manta_sim *S, const double *seed, double *lam_x, doub
     if (S->adj_part) { cudaStreamSynchronize(S->stream); cudaFree(S->adj_part); }
     S->adj_part = nullptr;
     S->adj_part_cap = 0;
-    if (cudaMalloc(&S->adj_part, (size_t)blocks * 40 * sizeof(double)) != cudaSuccess) {
+    if (dev_malloc((void **)&S->adj_part, (size_t)blocks * 40 * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       S->adj_part = nullptr;
       return fail(MANTA_E_OOM, "adjoint scratch allocation failed");
@@ -1405,7 +1458,7 @@ manta_status manta_replay(manta_sim *S, const double *theta, double *x, double *
     if (S->rep_acc) { cudaStreamSynchronize(S->stream); cudaFree(S->rep_acc); }
     S->rep_acc = nullptr;
     S->rep_acc_cap = 0;
-    if (cudaMalloc(&S->rep_acc, 2 * cells * sizeof(unsigned long long)) != cudaSuccess) {
+    if (dev_malloc((void **)&S->rep_acc, 2 * cells * sizeof(unsigned long long)) != cudaSuccess) {
       cudaGetLastError();
       S->rep_acc = nullptr;
       return fail(MANTA_E_OOM, "replay scratch allocation failed");

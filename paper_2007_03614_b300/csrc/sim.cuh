@@ -189,4 +189,9 @@ struct Params {
   int64_t tape_k0;
   int32_t tape_len;
   uint64_t wait_limit_ns;
+  // capacities checked by the bounds-checked build (MANTA_CHECK_BOUNDS):
+  // bytes of a lane-map buffer, vehicle slots, entries of the per-step lists,
+  // entries of the lane-change candidate overflow list, per-lane slots
+  uint64_t cap_map;
+  uint32_t cap_slots, cap_list, cap_lcq, cap_lanes;
 };

@@ -109,6 +109,8 @@ __device__ __forceinline__ int ldvi(const int *p) { return *(const volatile int 
 // of each block.  A waiter that passes the wall-clock limit sets the sticky
 // error word and adds kBarrierAbort to the counter, which releases every other
 // waiter at once; all blocks then leave the kernel.
+// The abort mark is one bit, set with an OR, so any number of blocks may set
+// it (arrivals per launch stay far below 2^30).
 constexpr unsigned kBarrierAbort = 1u << 30;
 
 __device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned &target, uint64_t limit_ns, int *s_ok) {
@@ -117,13 +119,21 @@ __device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned &target, uint64_t limi
   if (threadIdx.x == 0) {
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_count) : "memory");
     unsigned c = ld_acquire(&ctl->bar_count);
+#ifdef MANTA_CHECK_BOUNDS
+    // a failed index check ends the launch: every block leaves at this
+    // barrier (or, having passed it already, at the next one)
+    if (ldvi(&ctl->err) != 0) {
+      atomicOr(&ctl->bar_count, kBarrierAbort);
+      c = kBarrierAbort;
+    }
+#endif
     if (c < target) {
       const uint64_t t0 = globaltimer();
       uint32_t spins = 0;
       while ((c = ld_acquire(&ctl->bar_count)) < target) {
         if ((++spins & 63u) == 0u && globaltimer() - t0 > limit_ns) {
           atomicCAS(&ctl->err, 0, 1);
-          atomicAdd(&ctl->bar_count, kBarrierAbort);
+          atomicOr(&ctl->bar_count, kBarrierAbort);
           c = kBarrierAbort;
           break;
         }
@@ -135,6 +145,24 @@ __device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned &target, uint64_t limi
   __syncthreads();
   return *s_ok != 0;
 }
+
+// ------------------------------------------------------------ index checks
+// A build with MANTA_CHECK_BOUNDS checks the index of every write the step
+// kernel makes into the lane maps, vehicle records, lists, per-lane slots and
+// statistics against the capacity of its array (Params cap_*).  A failing
+// check skips the write and records the first failing site in the control
+// block (err = 2, err_info = site); the next grid barrier ends the launch,
+// and the host reports MANTA_E_DEVICE.  Other builds compile every check to
+// `true`.
+#ifdef MANTA_CHECK_BOUNDS
+__device__ __noinline__ bool index_fail(Ctl *ctl, int site) {
+  if (atomicCAS(&ctl->err, 0, 2) == 0) atomicExch(&ctl->err_info, site);
+  return false;
+}
+#define IDX_OK(i, cap, site) ((uint64_t)(i) < (uint64_t)(cap) ? true : index_fail(p.ctl, (site)))
+#else
+#define IDX_OK(i, cap, site) true
+#endif
 
 // ------------------------------------------------------------ random numbers
 // SplitMix64 (Steele, Lea, Flood 2014) of a key from (seed, id, step, stream).
@@ -741,6 +769,7 @@ __device__ __forceinline__ void flush_requests(const Params &p, const uint32_t *
   g0 = __shfl_sync(am, g0, __ffs(am) - 1);
   for (int j = rk; j < n; j += cnt) {
     const uint32_t o = g0 + (uint32_t)j;
+    if (!IDX_OK(o, p.cap_list, 22)) continue;
     p.req[o] = q[0 * 32 + j]; p.req_x[o] = __uint_as_float(q[1 * 32 + j]); p.req_v[o] = __uint_as_float(q[2 * 32 + j]);
     p.req_dw[o] = q[3 * 32 + j]; p.req_g[o] = q[4 * 32 + j]; p.req_t[o] = q[5 * 32 + j]; p.req_e2[o] = q[6 * 32 + j];
     p.req_n[o] = q[7 * 32 + j];
@@ -800,7 +829,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       e[1] = make_uint4(w.rend, w.e, w.ld, w.pcell);
       e[2] = make_uint4(w.em.row0, w.em.cnl, __float_as_uint(w.em.lim), w.em.dst);
       e[3].x = pos;
-    } else {
+    } else if (IDX_OK(reg0 + (at - lc_cap), p.cap_lcq, 5)) {
       p.lcq[reg0 + (at - lc_cap)] = w;
       p.lcq_pos[reg0 + (at - lc_cap)] = pos;
     }
@@ -830,21 +859,21 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       bool skip = false;
       if (s != MANTA_NONE && (s & kReqMark) != 0u) {
         s &= ~kReqMark;
-        if (!cmp) aout[i] = s;
+        if (!cmp && IDX_OK(i, p.cap_list, 1)) aout[i] = s;
         skip = merged;
       }
       uint32_t pos = i;
       if (cmp) {
         const uint32_t at = warp_append(&ctl->n_compact, s != MANTA_NONE);
-        if (s != MANTA_NONE) aout[at] = s;
+        if (s != MANTA_NONE && IDX_OK(at, p.cap_list, 2)) aout[at] = s;
         pos = at;
       }
       Veh w;
       bool cand = false;
       if (s != MANTA_NONE && !skip) {
         w = load_veh(p, s);
-        if (w.pcell != MANTA_NONE) clr[w.pcell] = (uint8_t)MANTA_EMPTY;
-        p.p3a[pos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
+        if (w.pcell != MANTA_NONE && IDX_OK(w.pcell, p.cap_map, 3)) clr[w.pcell] = (uint8_t)MANTA_EMPTY;
+        if (IDX_OK(pos, p.cap_list, 4)) p.p3a[pos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
         cand = lc_candidate(w, kk);
         if (cand) w.pcell = s;          // the list entry carries the slot in pcell
       }
@@ -932,7 +961,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           }
           const int tgt = lc_decide(p, cur, k, c, c_lce);
           const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
-          if (tgt >= 0) {
+          if (tgt >= 0 && IDX_OK(at, p.cap_list, 6)) {
             // the whole move, so that P2 applies it in one round trip; the
             // map byte at the vehicle's front cell is its own speed code
             const uint32_t stride = stride_of(cells_of(c.em.cnl));
@@ -974,10 +1003,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         // so no move's new cell is another's old one
         const uint4 *m = reinterpret_cast<const uint4 *>(p.lcm + i);
         const uint4 m0 = __ldcg(m), m1 = __ldcg(m + 1);
-        cur[m0.w] = (uint8_t)m1.z;
-        cur[m0.z] = (uint8_t)MANTA_EMPTY;
-        p.veh[m0.x].ld = m1.x;
-        p.p3a[m0.y] = m1.y;
+        if (IDX_OK(m0.w, p.cap_map, 7)) cur[m0.w] = (uint8_t)m1.z;
+        if (IDX_OK(m0.z, p.cap_map, 8)) cur[m0.z] = (uint8_t)MANTA_EMPTY;
+        if (IDX_OK(m0.x, p.cap_slots, 9)) p.veh[m0.x].ld = m1.x;
+        if (IDX_OK(m0.y, p.cap_list, 10)) p.p3a[m0.y] = m1.y;
         c_lc++;
       }
       if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
@@ -1008,7 +1037,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         uint32_t byte;
         req = first_up(cur + em.row0, 0, need - 1, byte) < 0;
       }
-      if (req) p.dep_key[e] = ((unsigned long long)tag << 32) | j;
+      if (req && IDX_OK(e, p.E, 11)) p.dep_key[e] = ((unsigned long long)tag << 32) | j;
       // what P4 needs of this departure in one entry: the edge, the queue
       // head's trip (none when it does not request entry) and the slot range
       // of its competitors, the in-lanes of the edge's tail node
@@ -1135,7 +1164,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           const int zone = C - 1 - (p.s0c[cls] + 2);
           if ((int)floorf(xn) >= zone && vn < p.stop_eps) dwn = dwell < 255u ? dwell + 1u : 255u;
         }
-        if (has_next && sc.reached_own && sc.nt_own == 1u) {
+        if (has_next && sc.reached_own && sc.nt_own == 1u && IDX_OK(lb + (uint32_t)lane, p.cap_lanes, 12)) {
           const uint32_t g = lb + (uint32_t)lane;
           p.slot_id[g] = w.id;
           p.slot_td[g] = ((uint32_t)(tag & 0xFFFFFF) << 8) | dwn;
@@ -1145,7 +1174,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         const bool arrive = crossing && !has_next;
         const bool request = crossing && has_next;
         if (arrive) {
-          atomicAdd(p.exitc + w.e, 1u);
+          if (IDX_OK(w.e, p.E, 13)) atomicAdd(p.exitc + w.e, 1u);
           c_arr++;
         }
         uint32_t rq_g = 0, rq_t = 0, rq_e2 = 0;
@@ -1155,25 +1184,31 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           const int l2 = min(lane, lanes_of(cnl2) - 1);
           rq_g = lb + (uint32_t)lane;
           rq_t = target_key(rq_e2, (uint32_t)l2);
-          p.req_tgt[rq_g] = rq_t;
-          p.req_key[rq_g] = ((unsigned long long)tag << 32) | w.id;
+          if (IDX_OK(rq_g, p.cap_lanes, 14)) {
+            p.req_tgt[rq_g] = rq_t;
+            p.req_key[rq_g] = ((unsigned long long)tag << 32) | w.id;
+          }
         } else if (!arrive) {
           w.x = xn; w.v = vn;
           w.ld = (w.ld & kLdEdgeBits) | (uint32_t)lane | (dwn << 8);
           w.pcell = gcell;
-          store_veh_state(p, s, w);
-          nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xn)] = speed_code(vn);
+          if (IDX_OK(s, p.cap_slots, 15)) store_veh_state(p, s, w);
+          const uint32_t o_map = em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xn);
+          if (IDX_OK(o_map, p.cap_map, 16)) nxt[o_map] = speed_code(vn);
           if (win >= 0) {
             const size_t o = (size_t)win * p.E + w.e;
-            atomicAdd(p.ssum + o, (unsigned long long)(vn * 1048576.0f));
-            atomicAdd(p.scnt + o, 1u);
+            if (IDX_OK(o, (uint64_t)p.n_win * p.E, 17)) {
+              atomicAdd(p.ssum + o, (unsigned long long)(vn * 1048576.0f));
+              atomicAdd(p.scnt + o, 1u);
+            }
           }
         }
         if (arrive) {
-          act[i] = MANTA_NONE;
+          if (IDX_OK(i, p.cap_list, 18)) act[i] = MANTA_NONE;
           const uint32_t ia = atomicAdd(&ctl->n_arr, 1u);
-          p.arr[ia] = gcell;
-          p.freel[atomicAdd(&ctl->free_count, 1u)] = s;
+          if (IDX_OK(ia, p.cap_list, 19)) p.arr[ia] = gcell;
+          const uint32_t fi = atomicAdd(&ctl->free_count, 1u);
+          if (IDX_OK(fi, p.cap_list, 20)) p.freel[fi] = s;
           atomicAdd(&ctl->n_holes[cb ^ 1], 1u);
         }
         if (request) {
@@ -1193,7 +1228,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           if (rk == 0) s_rqn[wid] = nb + cnt;
           __syncwarp(am);
           // P4 rewrites this record: the next record pass leaves it to P4
-          act[i] = s | kReqMark;
+          if (IDX_OK(i, p.cap_list, 21)) act[i] = s | kReqMark;
         }
         if (p.tape) {
           const int64_t tk = k - p.tape_k0;
@@ -1378,8 +1413,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         if (win_it) {
           const int C = (int)cells_of(em.cnl);
           if (__ldg(p.ntype + n) == 1 && ldv(p.permit + n) == w.id) p.permit[n] = MANTA_NONE;
-          atomicAdd(p.exitc + w.e, 1u);
-          atomicAdd(p.entry + e2, 1u);
+          if (IDX_OK(w.e, p.E, 23)) atomicAdd(p.exitc + w.e, 1u);
+          if (IDX_OK(e2, p.E, 24)) atomicAdd(p.entry + e2, 1u);
           xf = rx - __int2float_rn(C);
           vf = rv;
           const uint32_t l2 = tgt & 15u;
@@ -1387,14 +1422,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           w.ld = ld2;
           w.em = em2;
           w.em.lim = driver_limit(p, em2.lim, w.id, w.rc);
-          nxt[em2.row0 + l2 * stride_of(cells_of(em2.cnl)) + (uint32_t)(int)floorf(xf)] = speed_code(vf);
+          const uint32_t o_map = em2.row0 + l2 * stride_of(cells_of(em2.cnl)) + (uint32_t)(int)floorf(xf);
+          if (IDX_OK(o_map, p.cap_map, 25)) nxt[o_map] = speed_code(vf);
           ef = e2;
         } else {
           const int C = (int)cells_of(em.cnl);
           xf = fmaxf(w.x, __int2float_rn(C - 1));
           vf = 0.0f;
           w.ld = (w.ld & kLdEdgeBits) | (uint32_t)lane | (__ldcg(p.req_dw + i) << 8);
-          nxt[em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xf)] = speed_code(vf);
+          const uint32_t o_map = em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xf);
+          if (IDX_OK(o_map, p.cap_map, 26)) nxt[o_map] = speed_code(vf);
           ef = w.e;
         }
         if (p.tape) {
@@ -1408,17 +1445,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           }
         }
         w.x = xf; w.v = vf;
-        store_veh(p, s, w);
+        if (IDX_OK(s, p.cap_slots, 27)) store_veh(p, s, w);
         if (win >= 0) {
           const size_t o = (size_t)win * p.E + ef;
-          atomicAdd(p.ssum + o, (unsigned long long)(vf * 1048576.0f));
-          atomicAdd(p.scnt + o, 1u);
+          if (IDX_OK(o, (uint64_t)p.n_win * p.E, 28)) {
+            atomicAdd(p.ssum + o, (unsigned long long)(vf * 1048576.0f));
+            atomicAdd(p.scnt + o, 1u);
+          }
         }
         if (ahead) {
           // step k + 1's record pass for this vehicle: its M_k cell is in the
           // buffer written during k + 1
-          cur[w.pcell] = (uint8_t)MANTA_EMPTY;
-          p.p3a[rpos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
+          if (IDX_OK(w.pcell, p.cap_map, 29)) cur[w.pcell] = (uint8_t)MANTA_EMPTY;
+          if (IDX_OK(rpos, p.cap_list, 30)) p.p3a[rpos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
           if (lc_candidate(w, k + 1)) lc_add1(w, rpos, s);
         }
       } else if (t < t_arr) {
@@ -1456,26 +1495,27 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           w.x = 0.0f; w.v = 0.0f; w.id = j; w.rc = rc; w.rend = rend;
           w.e = e; w.ld = ld0; w.pcell = MANTA_NONE; w.em = em;
           w.em.lim = driver_limit(p, em.lim, j, rc);
-          store_veh(p, s, w);
-          act[ia] = s;
-          nxt[em.row0] = speed_code(0.0f);
+          if (IDX_OK(s, p.cap_slots, 31)) store_veh(p, s, w);
+          if (IDX_OK(ia, p.cap_list, 32)) act[ia] = s;
+          if (IDX_OK(em.row0, p.cap_map, 33)) nxt[em.row0] = speed_code(0.0f);
           atomicAdd(p.entry + e, 1u);
           c_dep++;
           p.q_pos[e] = qp + 1u;
-          if (ahead) {                        // step k + 1's record pass for this vehicle
+          if (ahead && IDX_OK(ia, p.cap_list, 34)) {   // step k + 1's record pass for this vehicle
             p.p3a[ia] = first_batch(em, 0, 0);
             if (lc_candidate(w, k + 1)) lc_add1(w, ia, s);
           }
         }
-        if (keep) dep_n[id2] = e;
+        if (keep && IDX_OK(id2, p.E, 35)) dep_n[id2] = e;
       } else if (t < t_due) {
-        cur[__ldcg(p.arr + (t - t_arr))] = (uint8_t)MANTA_EMPTY;
+        const uint32_t o_map = __ldcg(p.arr + (t - t_arr));
+        if (IDX_OK(o_map, p.cap_map, 36)) cur[o_map] = (uint8_t)MANTA_EMPTY;
       } else {
         const uint32_t i = due_lo + (t - t_due);
         const uint32_t e = __ldg(p.due_edge + i);
         const bool first = atomicAdd(p.pending + e, 1u) == 0u;
         const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], first);
-        if (first) dep_n[id2] = e;
+        if (first && IDX_OK(id2, p.E, 37)) dep_n[id2] = e;
       }
     }
     // step k + 1's record pass over the vehicles that stayed on their edge

@@ -52,7 +52,8 @@ EXPORTS = ("manta_default_config", "manta_create", "manta_load_trips", "manta_st
            "manta_set_variant", "manta_get_variant", "manta_autotune", "manta_graph_capture",
            "manta_graph_launch", "manta_graph_destroy", "manta_checkpoint_save", "manta_checkpoint_restore",
            "manta_checkpoint_step", "manta_checkpoint_bytes", "manta_checkpoint_destroy", "manta_tape_start",
-           "manta_tape_stop", "manta_tape_copy", "manta_adjoint", "manta_replay", "manta_place")
+           "manta_tape_stop", "manta_tape_copy", "manta_adjoint", "manta_replay", "manta_place",
+           "manta_debug_checks", "manta_debug_limit_map", "manta_debug_fail_nth")
 
 _lib = None
 
@@ -142,6 +143,12 @@ def load_library(path=None):
         lib.manta_replay.argtypes = [P, P, P, P, P, P]
         lib.manta_place.restype = C.c_int
         lib.manta_place.argtypes = [P, C.c_int64, P, P, P, P, P]
+        lib.manta_debug_checks.restype = C.c_int32
+        lib.manta_debug_checks.argtypes = []
+        lib.manta_debug_limit_map.restype = C.c_int
+        lib.manta_debug_limit_map.argtypes = [P, C.c_int64]
+        lib.manta_debug_fail_nth.restype = C.c_int
+        lib.manta_debug_fail_nth.argtypes = [C.c_int32, C.c_int64]
         _libs[path] = lib
     if path == LIB_PATH:
         _lib = _libs[path]
@@ -242,6 +249,10 @@ class Sim:
              np.ascontiguousarray(lane, np.uint8), np.ascontiguousarray(x, np.float32),
              np.ascontiguousarray(v, np.float32)]
         _check(self._lib.manta_place(self._h, len(a[0]), *[_p(q) for q in a]), self._lib)
+
+    def debug_limit_map(self, n_bytes):
+        """Test hook of the bounds-checked build (manta_debug_limit_map)."""
+        _check(self._lib.manta_debug_limit_map(self._h, int(n_bytes)), self._lib)
 
     def set_lane_closure(self, edge, lane, k0, k1):
         _check(self._lib.manta_set_lane_closure(self._h, int(edge), int(lane), int(k0), int(k1)), self._lib)
@@ -451,3 +462,15 @@ def run_noalloc(net, trips, n_steps, stream=None, **cfg):
         C.byref(cnt), *[_p(out[k]) for k in ("x", "v", "edge", "lane", "id", "dwell", "route_pos")])
     _check(rc)
     return st.as_dict(), {k: a[:cnt.value] for k, a in out.items()}
+
+
+def debug_checks(library=None) -> bool:
+    """Whether the library build checks device write indices (manta_debug_checks)."""
+    return bool(load_library(library).manta_debug_checks())
+
+
+def debug_fail_nth(kind, nth, library=None):
+    """Host-side fault injection (manta_debug_fail_nth): kind 0 device
+    allocations, 1 host-to-device copies; nth = 0 turns it off."""
+    lib = load_library(library)
+    _check(lib.manta_debug_fail_nth(int(kind), int(nth)), lib)

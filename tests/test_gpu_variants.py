@@ -72,7 +72,8 @@ def test_variant_tiny_workload(variant):
         _compare(o, g, f"{variant} step {k + 100}")
     _compare_all(o, g, windows=range(3))
     if variant == "lccap":
-        assert g.stats()["lc_evals"] > 1000
+        # every gap-acceptance evaluation read its candidate from the overflow region
+        assert g.stats()["lc_evals"] > 300
     g.close()
 
 
