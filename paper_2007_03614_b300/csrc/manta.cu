@@ -513,9 +513,13 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   S->clo_k1.assign(lanes_total ? lanes_total : 1, 0);
   long long *d_ck0 = dalloc<long long>(S, lanes_total, &ok);
   long long *d_ck1 = dalloc<long long>(S, lanes_total, &ok);
-  if (!ok || !upload(S, d_ck0, S->clo_k0) || !upload(S, d_ck1, S->clo_k1)) {
+  if (!ok) {
     manta_destroy(S);
     return fail(MANTA_E_OOM, "device allocation failed in manta_create");
+  }
+  if (!upload(S, d_ck0, S->clo_k0) || !upload(S, d_ck1, S->clo_k1)) {
+    manta_destroy(S);
+    return fail(MANTA_E_CUDA, "upload failed in manta_create");
   }
   P.clo_k0 = d_ck0; P.clo_k1 = d_ck1;
   P.em = d_em; P.es = d_es; P.ntype = d_nt; P.esrc = d_esrc; P.src_in = d_src_in; P.lane_base = d_lb;
