@@ -247,12 +247,12 @@ def run_gpu(args):
                           "phase_ms": [float(x) for x in sim.phase_times_ms()]}))
         return
     if args.profile_peak:
-        # the headline workload from 05:00 to 07:45 in untimed launches of 1800
-        # steps (eleven), then `--steps` launches of `--chunk` steps in the
-        # congested peak: the case for counter captures of the peak state
+        # the headline workload from 05:00 to --profile-at (default 07:45) in
+        # untimed launches of 1800 steps, then `--steps` launches of `--chunk`
+        # steps: the case for counter captures of that traffic state
         sim = manta.Sim(net, stream=stream, t0_step=T0_STEP)
         sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
-        n = int(7.75 * 3600 / 0.5) - T0_STEP
+        n = int(args.profile_at * 3600 / 0.5) - T0_STEP
         while n > 0:
             sim.step(min(1800, n))
             n -= 1800
@@ -966,8 +966,10 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: 07:30-08:00 trips, 1200-step warm-up launch, then --steps launches")
     ap.add_argument("--profile-peak", action="store_true",
-                    help="counter-capture case: the headline workload run to 07:45, then --steps launches "
+                    help="counter-capture case: the headline workload run to --profile-at, then --steps launches "
                          "of --chunk steps")
+    ap.add_argument("--profile-at", type=float, default=7.75,
+                    help="time of day (hours) at which --profile-peak starts its captured launches")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("need --steps >= 1 and --warmup >= 0")

@@ -121,7 +121,7 @@ __global__ void place_kernel(Params p, const uint32_t *trip, const uint32_t *rab
     w.x = x; w.v = v; w.id = j; w.rc = r; w.rend = p.route_off[j + 1u]; w.e = e;
     w.ld = ld_for_entry(p, r, l); w.pcell = MANTA_NONE; w.em = em;
     w.em.lim = driver_limit(p, em.lim, j, r);
-    store_veh(p, i, w);
+    store_veh(p.vs[0], i, w);
     act[i] = i;
     atomicAdd(p.entry + e, 1u);
   }
@@ -643,9 +643,15 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   int32_t *d_due = dalloc<int32_t>(S, due_step.size(), &ok);
   uint32_t *d_due_e = dalloc<uint32_t>(S, due_edge.size(), &ok);
   const size_t NT = (size_t)std::max<int64_t>(n, 1);
-  P.veh = dalloc<Veh>(S, NT, &ok);
+  for (int b = 0; b < 2; ++b) {
+    P.vs[b].xv = dalloc<float2>(S, NT, &ok);
+    P.vs[b].idr = dalloc<uint4>(S, NT, &ok);
+    P.vs[b].ld = dalloc<uint32_t>(S, NT, &ok);
+    P.vs[b].pc = dalloc<uint32_t>(S, NT, &ok);
+    P.vs[b].em = dalloc<uint4>(S, NT, &ok);
+  }
   P.act0 = dalloc<uint32_t>(S, NT, &ok); P.act1 = dalloc<uint32_t>(S, NT, &ok);
-  P.freel = dalloc<uint32_t>(S, NT, &ok); P.lcm = dalloc<LcMove>(S, NT, &ok);
+  P.lcm = dalloc<LcMove>(S, NT, &ok);
   P.p3a = dalloc<uint32_t>(S, NT, &ok);
   // candidate overflow regions, for every launch shape: at most NT list
   // entries and NT + E merge-phase items (requests and departures) per step
@@ -663,7 +669,6 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
   P.req_x = dalloc<float>(S, NT, &ok); P.req_v = dalloc<float>(S, NT, &ok); P.req_dw = dalloc<uint32_t>(S, NT, &ok);
   P.req_g = dalloc<uint32_t>(S, NT, &ok); P.req_t = dalloc<uint32_t>(S, NT, &ok);
   P.req_e2 = dalloc<uint32_t>(S, NT, &ok); P.req_n = dalloc<uint32_t>(S, NT, &ok);
-  P.req_pos = dalloc<uint32_t>(S, NT, &ok);
   if (!ok) return fail(MANTA_E_OOM, "device allocation failed in manta_load_trips");
   bool cp = upload(S, d_roff, roff) && upload(S, d_qoff, q_off) && upload(S, d_qtrip, order) &&
             upload(S, d_due, due_step) && upload(S, d_due_e, due_edge) && upload(S, d_out_off, h_out_off) &&
@@ -794,7 +799,6 @@ manta_status manta_place(manta_sim *S, int64_t n, const int64_t *trip, const int
   c0.due_hi = prime_hi;
   c0.k_next = S->k;
   c0.n_act[cb] = (uint32_t)n;
-  c0.n_slots = (uint32_t)n;
   c0.cnt[CNT_DEP] = (unsigned long long)n;
   const bool cp =
       upload(S, d_trip, h_trip) && upload(S, d_rabs, h_rabs) &&
@@ -1099,28 +1103,34 @@ manta_status manta_snapshot(manta_sim *S, int64_t cap, int64_t *n_out, float *x,
   if (live > cap) return fail(MANTA_E_INVALID, "snapshot capacity too small");
   if (live == 0) return MANTA_OK;
   const Params &P = S->P;
+  const uint32_t sel = c.act_sel[S->k & 1];
   std::vector<uint32_t> act(len);
-  if (cudaMemcpy(act.data(), c.act_sel[S->k & 1] ? P.act1 : P.act0, 4ull * len, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return fail(MANTA_E_CUDA, "copy of the active list failed");
-  for (uint32_t &a : act)
-    if (a != MANTA_NONE) a &= 0x7FFFFFFFu;   // a requester's mark (set for the kernel's next record pass)
-  act.erase(std::remove(act.begin(), act.end(), MANTA_NONE), act.end());
-  if ((int64_t)act.size() != live) return fail(MANTA_E_DEVICE, "active list and counters disagree");
-  const uint32_t n = (uint32_t)live;
-  const size_t NT = (size_t)std::max<int64_t>(S->n_trips, 1);
-  std::vector<Veh> hv(NT);
-  if (cudaMemcpy(hv.data(), P.veh, sizeof(Veh) * NT, cudaMemcpyDeviceToHost) != cudaSuccess)
+  std::vector<float2> hxv(len);
+  std::vector<uint4> hidr(len);
+  std::vector<uint32_t> hld(len);
+  const VehSet &R = P.vs[sel];
+  if (len > 0 &&
+      (cudaMemcpy(act.data(), sel ? P.act1 : P.act0, 4ull * len, cudaMemcpyDeviceToHost) != cudaSuccess ||
+       cudaMemcpy(hxv.data(), R.xv, sizeof(float2) * len, cudaMemcpyDeviceToHost) != cudaSuccess ||
+       cudaMemcpy(hidr.data(), R.idr, sizeof(uint4) * len, cudaMemcpyDeviceToHost) != cudaSuccess ||
+       cudaMemcpy(hld.data(), R.ld, 4ull * len, cudaMemcpyDeviceToHost) != cudaSuccess))
     return fail(MANTA_E_CUDA, "copy of vehicle state failed");
-  std::sort(act.begin(), act.end(), [&](uint32_t a, uint32_t b) { return hv[a].id < hv[b].id; });
-  for (uint32_t i = 0; i < n; ++i) {
-    const Veh &w = hv[act[i]];
-    if (x) x[i] = w.x;
-    if (v) v[i] = w.v;
-    if (edge) edge[i] = (int32_t)w.e;
-    if (lane) lane[i] = (uint8_t)(w.ld & 0xFu);
-    if (id) id[i] = w.id;
-    if (dwell) dwell[i] = (uint8_t)((w.ld >> 8) & 0xFFu);
-    if (route_pos) route_pos[i] = (int32_t)(w.rc - S->route_off_h[w.id]);
+  // live list positions (an entry is its own position, a requester's marked)
+  std::vector<uint32_t> pos;
+  pos.reserve(len);
+  for (uint32_t i = 0; i < len; ++i)
+    if (act[i] != MANTA_NONE) pos.push_back(i);
+  if ((int64_t)pos.size() != live) return fail(MANTA_E_DEVICE, "active list and counters disagree");
+  std::sort(pos.begin(), pos.end(), [&](uint32_t a, uint32_t b) { return hidr[a].x < hidr[b].x; });
+  for (size_t q = 0; q < pos.size(); ++q) {
+    const uint32_t i = pos[q];
+    if (x) x[q] = hxv[i].x;
+    if (v) v[q] = hxv[i].y;
+    if (edge) edge[q] = (int32_t)hidr[i].w;
+    if (lane) lane[q] = (uint8_t)(hld[i] & 0xFu);
+    if (id) id[q] = hidr[i].x;
+    if (dwell) dwell[q] = (uint8_t)((hld[i] >> 8) & 0xFFu);
+    if (route_pos) route_pos[q] = (int32_t)(hidr[i].y - S->route_off_h[hidr[i].x]);
   }
   return MANTA_OK;
 }
@@ -1284,8 +1294,10 @@ std::vector<std::pair<void *, size_t>> mutable_state(const manta_sim *S) {
           {P.req_key, 8 * G}, {P.req_tgt, 4 * G}, {P.slot_td, 4 * G}, {P.slot_id, 4 * G},
           {P.entry, 4 * E}, {P.exitc, 4 * E}, {P.ssum, 8 * E * W}, {P.scnt, 4 * E * W},
           {P.pending, 4 * E}, {P.q_pos, 4 * E}, {P.dep_key, 8 * E}, {P.dep0, 4 * E}, {P.dep1, 4 * E},
-          {P.ctl, sizeof(Ctl)}, {P.veh, sizeof(Veh) * NT}, {P.act0, 4 * NT}, {P.act1, 4 * NT},
-          {P.freel, 4 * NT}};
+          {P.ctl, sizeof(Ctl)}, {P.act0, 4 * NT}, {P.act1, 4 * NT},
+          {P.vs[0].xv, 8 * NT}, {P.vs[0].idr, 16 * NT}, {P.vs[0].ld, 4 * NT}, {P.vs[0].pc, 4 * NT},
+          {P.vs[0].em, 16 * NT}, {P.vs[1].xv, 8 * NT}, {P.vs[1].idr, 16 * NT}, {P.vs[1].ld, 4 * NT},
+          {P.vs[1].pc, 4 * NT}, {P.vs[1].em, 16 * NT}};
 }
 }  // namespace
 

@@ -6,17 +6,21 @@
 //                 padding bytes stay 0xFF.  One byte per 1 m cell: 0xFF empty,
 //                 else the speed code of the vehicle whose front is there.
 //   edge tables   EdgeMeta (16 B) and EdgeSig (8 B) per edge, read-only.
-//   vehicles      48-byte records by slot (Veh): position, speed, id, route
-//                 cursor and end, edge, lane/dwell/target, the cell it left in
-//                 the other map buffer (cleared next step), and a copy of the
-//                 current edge's record.
-//   lists         active slots (a vehicle keeps its list position while on
-//                 the network, arrivals leave holes, departures append, and a
-//                 compaction pass into the other buffer runs when holes pass
-//                 a quarter of the list), free slots, lane changers, crossing
-//                 requesters, arrivals, departure edges (double buffered);
-//                 appended with warp-aggregated atomics (the order of a list
-//                 never changes a result).
+//   vehicles      structure of arrays indexed by active-list position, one
+//                 set per list buffer (VehSet): (x, v); (id, route cursor,
+//                 route end, edge); the lane word (lane, dwell, lane mask
+//                 toward the next edge); the cell it left in the other map
+//                 buffer (cleared next step); a copy of the current edge's
+//                 record.  A warp working on consecutive list positions loads
+//                 each array with one coalesced instruction.
+//   lists         the active list (a vehicle keeps its position while on the
+//                 network; arrivals leave holes, departures append, and a
+//                 compaction pass moves the live vehicles into the other
+//                 buffer's list and arrays when holes pass a quarter of the
+//                 list), lane changers, crossing requesters, arrivals,
+//                 departure edges (double buffered); appended with
+//                 warp-aggregated atomics (the order of a list never changes a
+//                 result).
 //   request slots per lane: key = (step + 1) << 32 | vehicle id and target lane,
 //                 read by competitors; the lowest id wins (no atomics).
 #pragma once
@@ -45,9 +49,10 @@ enum {
   CNT_UPD = 0, CNT_SCAN, CNT_CLAMP, CNT_LC, CNT_LCE, CNT_RR, CNT_DEP, CNT_ARR, CNT_N
 };
 
-// One vehicle, 48 bytes, fetched with three independent 16-byte loads; it
-// carries a copy of its current edge's record so that no phase needs a
-// dependent edge-table load before it can address the lane map.
+// One vehicle in registers (and the 48-byte copy kept for lane-change
+// candidates).  Its state carries a copy of its current edge's record so that
+// no phase needs a dependent edge-table load before it can address the lane
+// map.
 struct __align__(16) Veh {
   float x;         // front position in cells from the start of the edge
   float v;         // speed, m/s
@@ -86,6 +91,15 @@ struct TapeRec {
 enum { TK_FREE = 0, TK_INTERACT = 1, TK_STOP = 2 };
 enum { TO_STAY = 0, TO_CROSS = 1, TO_HELD_KEEP = 2, TO_HELD_LINE = 3, TO_ARRIVE = 4, TO_PENDING = 5 };
 
+// Vehicle state by active-list position (structure of arrays).
+struct VehSet {
+  float2 *xv;      // front position (cells from the start of the edge), speed (m/s)
+  uint4 *idr;      // trip id, route cursor, route end, current edge
+  uint32_t *ld;    // lane word (as Veh::ld)
+  uint32_t *pc;    // its cell in the other map buffer (cleared next step), or none
+  uint4 *em;       // record of its current edge (as EdgeMeta)
+};
+
 struct Ctl {
   unsigned bar_count;
   unsigned bar_gen;
@@ -99,8 +113,7 @@ struct Ctl {
   uint32_t pad[2];
   long long k_next;        // step index the next launch starts from (each launch advances it)
   uint32_t n_dep[2];
-  uint32_t n_req, n_arr, n_chg, n_depwin;
-  uint32_t free_count, n_slots;
+  uint32_t n_req, n_arr, n_chg, pad2;
   uint32_t due_pos, due_hi;   // trips [due_pos, due_hi) of the due list join queues this step
 
   unsigned long long cnt[CNT_N];
@@ -108,7 +121,7 @@ struct Ctl {
 };
 
 // One lane change, written whole by its decision so that it applies in one
-// round trip: slot, active-list position, old and new map cell; new lane
+// round trip: active-list position (twice), old and new map cell; new lane
 // word, first leader-scan batch, speed code.
 struct LcMove {
   uint32_t slot, pos, from, to;
@@ -141,18 +154,17 @@ struct Params {
   const uint32_t *due_edge;
   // lane map
   uint8_t *atlas0, *atlas1;
-  // vehicle records by slot
-  Veh *veh;
-  // lists
-  uint32_t *act0, *act1, *freel, *req, *arr, *dep0, *dep1;
+  // vehicle state by active-list position: vs[0] with act0, vs[1] with act1
+  VehSet vs[2];
+  // lists (an active-list entry is its own position, or none for a hole)
+  uint32_t *act0, *act1, *req, *arr, *dep0, *dep1;
   uint32_t *p3a;               // by active-list position: first lane-map batch of the leader scan
   LcMove *lcm;                 // lane changes decided in P1, applied in P2
-  Veh *lcq;                    // lane-change candidates of the step by warp region (record copies,
-                               // slot in pcell)
+  Veh *lcq;                    // lane-change candidates of the step by block region (record copies,
+                               // list position in pcell)
   uint32_t *lcq_pos;           // their active-list positions
   float *req_x, *req_v;
   uint32_t *req_dw, *req_g, *req_t, *req_e2, *req_n;
-  uint32_t *req_pos;           // active-list position of each requester
   // departure queues
   uint32_t *pending, *q_pos;
   uint32_t *dep_info;          // per departure-list entry of the step: edge, head trip or none,

@@ -233,24 +233,38 @@ __device__ __forceinline__ Veh load_veh_at(const Veh *r) {
   w.em.row0 = q2.x; w.em.cnl = q2.y; w.em.lim = __uint_as_float(q2.z); w.em.dst = q2.w;
   return w;
 }
-__device__ __forceinline__ Veh load_veh(const Params &p, uint32_t s) {
-  const uint4 *a = reinterpret_cast<const uint4 *>(p.veh + s);
-  const uint4 q0 = __ldcg(a), q1 = __ldcg(a + 1), q2 = __ldcg(a + 2);
+// The vehicle at active-list position i of a state set: five independent
+// loads, each coalesced across a warp working on consecutive positions.
+__device__ __forceinline__ Veh load_veh(const VehSet &R, uint32_t i) {
+  const float2 a = __ldcg(R.xv + i);
+  const uint4 b = __ldcg(R.idr + i);
+  const uint32_t l = __ldcg(R.ld + i), c = __ldcg(R.pc + i);
+  const uint4 m = __ldcg(R.em + i);
   Veh w;
-  w.x = __uint_as_float(q0.x); w.v = __uint_as_float(q0.y); w.id = q0.z; w.rc = q0.w;
-  w.rend = q1.x; w.e = q1.y; w.ld = q1.z; w.pcell = q1.w;
-  w.em.row0 = q2.x; w.em.cnl = q2.y; w.em.lim = __uint_as_float(q2.z); w.em.dst = q2.w;
+  w.x = a.x; w.v = a.y; w.id = b.x; w.rc = b.y; w.rend = b.z; w.e = b.w; w.ld = l; w.pcell = c;
+  w.em.row0 = m.x; w.em.cnl = m.y; w.em.lim = __uint_as_float(m.z); w.em.dst = m.w;
   return w;
 }
-// position, speed, lane state (edge unchanged)
-__device__ __forceinline__ void store_veh_state(const Params &p, uint32_t s, const Veh &w) {
-  uint4 *a = reinterpret_cast<uint4 *>(p.veh + s);
-  a[0] = make_uint4(__float_as_uint(w.x), __float_as_uint(w.v), w.id, w.rc);
-  a[1] = make_uint4(w.rend, w.e, w.ld, w.pcell);
+// position, speed, lane word, previous cell (edge and route cursor unchanged)
+__device__ __forceinline__ void store_veh_state(const VehSet &R, uint32_t i, const Veh &w) {
+  R.xv[i] = make_float2(w.x, w.v);
+  R.ld[i] = w.ld;
+  R.pc[i] = w.pcell;
 }
-__device__ __forceinline__ void store_veh(const Params &p, uint32_t s, const Veh &w) {
-  store_veh_state(p, s, w);
-  reinterpret_cast<uint4 *>(p.veh + s)[2] = make_uint4(w.em.row0, w.em.cnl, __float_as_uint(w.em.lim), w.em.dst);
+__device__ __forceinline__ void store_veh(const VehSet &R, uint32_t i, const Veh &w) {
+  store_veh_state(R, i, w);
+  R.idr[i] = make_uint4(w.id, w.rc, w.rend, w.e);
+  R.em[i] = make_uint4(w.em.row0, w.em.cnl, __float_as_uint(w.em.lim), w.em.dst);
+}
+// the state set that goes with list buffer `sel`
+__device__ __forceinline__ VehSet veh_set(const Params &p, uint32_t sel) {
+  VehSet r;
+  r.xv = sel ? p.vs[1].xv : p.vs[0].xv;
+  r.idr = sel ? p.vs[1].idr : p.vs[0].idr;
+  r.ld = sel ? p.vs[1].ld : p.vs[0].ld;
+  r.pc = sel ? p.vs[1].pc : p.vs[0].pc;
+  r.em = sel ? p.vs[1].em : p.vs[0].em;
+  return r;
 }
 
 // lane word of a vehicle record
@@ -773,7 +787,6 @@ __device__ __forceinline__ void flush_requests(const Params &p, const uint32_t *
     p.req[o] = q[0 * 32 + j]; p.req_x[o] = __uint_as_float(q[1 * 32 + j]); p.req_v[o] = __uint_as_float(q[2 * 32 + j]);
     p.req_dw[o] = q[3 * 32 + j]; p.req_g[o] = q[4 * 32 + j]; p.req_t[o] = q[5 * 32 + j]; p.req_e2[o] = q[6 * 32 + j];
     p.req_n[o] = q[7 * 32 + j];
-    p.req_pos[o] = q[8 * 32 + j];
   }
   __syncwarp(am);
 }
@@ -834,17 +847,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       p.lcq_pos[reg0 + (at - lc_cap)] = pos;
     }
   };
-  // The record pass that prepares step kk: over list positions [0, n) of ain,
-  // clear each vehicle's cell of M_{kk-1} in clr (the buffer written during
-  // kk), note the first batch of its leader scan (p3a) and list the block's
-  // lane-change candidates (a record copy with the slot in pcell, and the
-  // list position).  With cmp the live entries are compacted into aout (else
-  // aout is ain).  Entries marked kReqMark belong to the last step's
-  // requesters, whose records P4 rewrote: the mark is removed, and when the
+  // The record pass that prepares step kk: over list positions [0, n) of ain
+  // (vehicle state Rin), clear each vehicle's cell of M_{kk-1} in clr (the
+  // buffer written during kk), note the first batch of its leader scan (p3a)
+  // and list the block's lane-change candidates (a record copy with the list
+  // position in pcell, and the list position).  With cmp the live vehicles
+  // are compacted into aout and their state moved to Rout (else aout is ain
+  // and Rout is Rin).  Entries marked kReqMark belong to the last step's
+  // requesters, whose state P4 rewrote: the mark is removed, and when the
   // pass runs in that same merge phase (merged) P4 prepares them itself.
   // The pass runs on warps w0 .. w0 + nw - 1 of the spread numbering (gspr).
-  auto rec = [&](int64_t kk, const uint32_t *ain, uint32_t *aout, uint32_t n, bool cmp, uint8_t *clr,
-                 bool merged, uint32_t reg0, uint32_t w0, uint32_t nw) {
+  auto rec = [&](int64_t kk, const uint32_t *ain, uint32_t *aout, const VehSet &Rin, const VehSet &Rout, uint32_t n,
+                 bool cmp, uint8_t *clr, bool merged, uint32_t reg0, uint32_t w0, uint32_t nw) {
     const int lane = threadIdx.x & 31;
     const uint32_t gw = gspr >> 5;
     if (gw < w0) return;
@@ -865,17 +879,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       uint32_t pos = i;
       if (cmp) {
         const uint32_t at = warp_append(&ctl->n_compact, s != MANTA_NONE);
-        if (s != MANTA_NONE && IDX_OK(at, p.cap_list, 2)) aout[at] = s;
+        if (s != MANTA_NONE && IDX_OK(at, p.cap_list, 2)) aout[at] = at;
         pos = at;
       }
       Veh w;
       bool cand = false;
       if (s != MANTA_NONE && !skip) {
-        w = load_veh(p, s);
+        w = load_veh(Rin, i);
+        if (cmp && IDX_OK(pos, p.cap_slots, 39)) store_veh(Rout, pos, w);
         if (w.pcell != MANTA_NONE && IDX_OK(w.pcell, p.cap_map, 3)) clr[w.pcell] = (uint8_t)MANTA_EMPTY;
         if (IDX_OK(pos, p.cap_list, 4)) p.p3a[pos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
         cand = lc_candidate(w, kk);
-        if (cand) w.pcell = s;          // the list entry carries the slot in pcell
+        if (cand) w.pcell = pos;        // the candidate carries its list position in pcell
       }
       const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
       uint32_t b = 0;
@@ -903,6 +918,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     const bool compact = !rec_ready && holes > 0u && 4u * holes > nact;
     const uint32_t *act_in = sel ? p.act1 : p.act0;
     uint32_t *act = compact ? (sel ? p.act0 : p.act1) : (sel ? p.act1 : p.act0);
+    const VehSet Rin = veh_set(p, sel);
+    const VehSet R = veh_set(p, compact ? sel ^ 1u : sel);
     // ================================================================ P1
     if (gtid == 0) {
       ctl->next3 = 0u;
@@ -911,10 +928,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       ctl->n_holes[cb ^ 1] = compact ? 0u : holes;
       ctl->act_sel[cb ^ 1] = compact ? (sel ^ 1u) : sel;
       ctl->n_dep[cb ^ 1] = 0u;
-      const uint32_t fc = ctl->free_count, w = ctl->n_depwin;
-      if (w <= fc) ctl->free_count = fc - w;
-      else { ctl->n_slots += w - fc; ctl->free_count = 0u; }
-      ctl->n_depwin = 0u;
     }
     if (blockIdx.x == 0 && threadIdx.x < 32) {
       // trips with departure step <= k + 1 not yet queued: [due_pos, due_hi)
@@ -934,7 +947,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       uint32_t reg0 = reg0_next;
       if (!rec_ready) {
         reg0 = lc_region(gsz, nact, 0u);
-        rec(k, act_in, act, nact, compact, nxt, false, reg0, 0u, gsz / 32u);
+        rec(k, act_in, act, Rin, R, nact, compact, nxt, false, reg0, 0u, gsz / 32u);
       }
       // lane-change decisions on M_k, a full warp of candidates at a time
       __syncthreads();
@@ -998,14 +1011,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     const uint32_t nchg = ldv(&ctl->n_chg);
     if (nchg) {
       for (uint32_t i = gspr; i < nchg; i += gsz) {
-        // (slot, list position, old cell, new cell), (lane word, first scan
+        // (list position twice, old cell, new cell), (lane word, first scan
         // batch, speed code); the gap acceptance keeps every new cell free,
         // so no move's new cell is another's old one
         const uint4 *m = reinterpret_cast<const uint4 *>(p.lcm + i);
         const uint4 m0 = __ldcg(m), m1 = __ldcg(m + 1);
         if (IDX_OK(m0.w, p.cap_map, 7)) cur[m0.w] = (uint8_t)m1.z;
         if (IDX_OK(m0.z, p.cap_map, 8)) cur[m0.z] = (uint8_t)MANTA_EMPTY;
-        if (IDX_OK(m0.x, p.cap_slots, 9)) p.veh[m0.x].ld = m1.x;
+        if (IDX_OK(m0.y, p.cap_slots, 9)) R.ld[m0.y] = m1.x;
         if (IDX_OK(m0.y, p.cap_list, 10)) p.p3a[m0.y] = m1.y;
         c_lc++;
       }
@@ -1192,7 +1205,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           w.x = xn; w.v = vn;
           w.ld = (w.ld & kLdEdgeBits) | (uint32_t)lane | (dwn << 8);
           w.pcell = gcell;
-          if (IDX_OK(s, p.cap_slots, 15)) store_veh_state(p, s, w);
+          if (IDX_OK(s, p.cap_slots, 15)) store_veh_state(R, s, w);
           const uint32_t o_map = em.row0 + (uint32_t)lane * stride + (uint32_t)(int)floorf(xn);
           if (IDX_OK(o_map, p.cap_map, 16)) nxt[o_map] = speed_code(vn);
           if (win >= 0) {
@@ -1207,8 +1220,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           if (IDX_OK(i, p.cap_list, 18)) act[i] = MANTA_NONE;
           const uint32_t ia = atomicAdd(&ctl->n_arr, 1u);
           if (IDX_OK(ia, p.cap_list, 19)) p.arr[ia] = gcell;
-          const uint32_t fi = atomicAdd(&ctl->free_count, 1u);
-          if (IDX_OK(fi, p.cap_list, 20)) p.freel[fi] = s;
           atomicAdd(&ctl->n_holes[cb ^ 1], 1u);
         }
         if (request) {
@@ -1223,7 +1234,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           const int at = nb + rk;
           rqb[0 * 32 + at] = s; rqb[1 * 32 + at] = __float_as_uint(xn); rqb[2 * 32 + at] = __float_as_uint(vn);
           rqb[3 * 32 + at] = dwn; rqb[4 * 32 + at] = rq_g; rqb[5 * 32 + at] = rq_t; rqb[6 * 32 + at] = rq_e2;
-          rqb[7 * 32 + at] = node_of(em); rqb[8 * 32 + at] = i;
+          rqb[7 * 32 + at] = node_of(em);
           __syncwarp(am);
           if (rk == 0) s_rqn[wid] = nb + cnt;
           __syncwarp(am);
@@ -1293,7 +1304,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         Fetch f;
         if (st == 1) {
           // the record and, in the same round trip, the first batch of its row
-          w = load_veh(p, s);
+          w = load_veh(R, s);
           if (a3 != MANTA_NONE) slot_fetch(slot_s, cur + a3, kFirstChunks);
         } else if (st == 2) {
           walk_issue(p, cur, w, wk, slot_s, f);
@@ -1363,8 +1374,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     const uint32_t nreq = ldv(&ctl->n_req);
     const uint32_t narr = ldv(&ctl->n_arr);
     const uint32_t due_lo = ldv(&ctl->due_pos), due_hi = ldv(&ctl->due_hi);
-    // free slots: constant during this phase (arrivals freed theirs in P3)
-    const uint32_t fc = ldv(&ctl->free_count), n_slots = ldv(&ctl->n_slots);
     // This phase also runs the record pass of step k + 1 (the vehicles that
     // stayed on their edge in P3; P4's own vehicles are prepared where P4
     // finalises them), unless this is the launch's last step or k + 1 will
@@ -1395,11 +1404,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         const uint32_t gown = __ldcg(p.req_g + i), tgt = __ldcg(p.req_t + i);
         const uint32_t e2 = __ldcg(p.req_e2 + i), n = __ldcg(p.req_n + i);
         const float rx = __ldcg(p.req_x + i), rv = __ldcg(p.req_v + i);
-        const uint32_t rpos = __ldcg(p.req_pos + i);
+        const uint32_t rpos = s;                // its list position
         const uint32_t o0 = __ldg(p.nin_off + n), o1 = __ldg(p.nin_off + n + 1);
         const unsigned long long dk = __ldcg(p.dep_key + e2);
         const EdgeMeta em2 = load_em(p, e2);
-        Veh w = load_veh(p, s);
+        Veh w = load_veh(R, s);
         const uint32_t ld2 = ld_for_entry(p, w.rc + 1u, tgt & 15u);   // with the competitors' slots
         const int lane = ld_lane(w.ld);
         const EdgeMeta em = w.em;
@@ -1445,7 +1454,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           }
         }
         w.x = xf; w.v = vf;
-        if (IDX_OK(s, p.cap_slots, 27)) store_veh(p, s, w);
+        if (IDX_OK(s, p.cap_slots, 27)) store_veh(R, s, w);
         if (win >= 0) {
           const size_t o = (size_t)win * p.E + ef;
           if (IDX_OK(o, (uint64_t)p.n_win * p.E, 28)) {
@@ -1464,8 +1473,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         const uint32_t i = t - t_dep;
         // round trip 1: the entry P3 wrote (edge, head trip, competitors'
         // slot range); 2: the competitors' requests, the edge record and the
-        // trip's route; 3: the winner's three counter updates together; 4: its
-        // slot and its departure-list position together
+        // trip's route; 3: the winner's counter updates together
         const uint4 di = __ldcg(reinterpret_cast<const uint4 *>(p.dep_info) + i);
         const uint32_t e = di.x, j = di.y;
         bool won = j != MANTA_NONE;
@@ -1478,16 +1486,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           ld0 = ld_for_entry(p, rc, 0u);
           won = min_competitor(p, di.z, di.w, MANTA_NONE, target_key(e, 0u), tag) > j;
         }
-        // the results of these two atomics are first used after the list
-        // append below, so the three round trips overlap
-        uint32_t wi = 0u, pend = 2u;
-        if (won) {
-          wi = atomicAdd(&ctl->n_depwin, 1u);
-          pend = atomicSub(p.pending + e, 1u);
-        }
+        // the result of this atomic is first used after the list append
+        // below, so the two round trips overlap; the new vehicle's state
+        // goes to its list position
+        uint32_t pend = 2u;
+        if (won) pend = atomicSub(p.pending + e, 1u);
         const uint32_t ia = warp_append(&ctl->n_act[cb ^ 1], won);
-        uint32_t s = MANTA_NONE;
-        if (won) s = wi < fc ? __ldcg(p.freel + (fc - 1u - wi)) : n_slots + (wi - fc);
+        const uint32_t s = ia;
         const bool keep = pend > 1u;
         const uint32_t id2 = warp_append(&ctl->n_dep[cb ^ 1], keep);
         if (won) {
@@ -1495,7 +1500,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           w.x = 0.0f; w.v = 0.0f; w.id = j; w.rc = rc; w.rend = rend;
           w.e = e; w.ld = ld0; w.pcell = MANTA_NONE; w.em = em;
           w.em.lim = driver_limit(p, em.lim, j, rc);
-          if (IDX_OK(s, p.cap_slots, 31)) store_veh(p, s, w);
+          if (IDX_OK(s, p.cap_slots, 31)) store_veh(R, s, w);
           if (IDX_OK(ia, p.cap_list, 32)) act[ia] = s;
           if (IDX_OK(em.row0, p.cap_map, 33)) nxt[em.row0] = speed_code(0.0f);
           atomicAdd(p.entry + e, 1u);
@@ -1519,7 +1524,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       }
     }
     // step k + 1's record pass over the vehicles that stayed on their edge
-    if (ahead) rec(k + 1, act, act, nact, false, cur, true, reg0n, rw0, w_all - rw0);
+    if (ahead) rec(k + 1, act, act, R, R, nact, false, cur, true, reg0n, rw0, w_all - rw0);
     if (gtid == 0) ctl->n_compact = 0u;
     if (!grid_sync(ctl, bar_target, p.wait_limit_ns, &s_ok)) { alive = false; break; }
     if (timer) { const uint64_t t = globaltimer(); ph[3] += t - tp; tp = t; }
