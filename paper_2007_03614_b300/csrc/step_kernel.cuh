@@ -797,6 +797,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
   __shared__ int s_ok;
   __shared__ unsigned long long s_cnt[CNT_N];
   __shared__ float s_sab2[8];                       // 2 sqrt(a b) per road class (Eq. 1)
+  // Eq. 1 parameters per road class, read with the lane's own class: from
+  // shared memory, a warp whose lanes hold vehicles of different classes
+  // reads them in one access
+  __shared__ float s_a[8], s_T[8], s_s0[8], s_v0f[8];
+  __shared__ int s_s0c[8];
   // per-warp scratch of P3 (dynamic shared memory, kWarpWords words per
   // warp): the work pool (32 slots, list indices, first-batch offsets), 32
   // staged crossing requests (9 fields, field-major) and the finish queue
@@ -806,7 +811,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
   __shared__ uint32_t s_lcn, s_lct;                 // lane-change candidates of the block; batches taken
   Ctl *ctl = p.ctl;
   if (threadIdx.x < CNT_N) s_cnt[threadIdx.x] = 0ull;
-  if (threadIdx.x < 8) s_sab2[threadIdx.x] = 2.0f * sqrtf(p.a[threadIdx.x] * p.b[threadIdx.x]);
+  if (threadIdx.x < 8) {
+    s_sab2[threadIdx.x] = 2.0f * sqrtf(p.a[threadIdx.x] * p.b[threadIdx.x]);
+    s_a[threadIdx.x] = p.a[threadIdx.x]; s_T[threadIdx.x] = p.T[threadIdx.x]; s_s0[threadIdx.x] = p.s0[threadIdx.x];
+    s_v0f[threadIdx.x] = p.v0f[threadIdx.x]; s_s0c[threadIdx.x] = p.s0c[threadIdx.x];
+  }
   if (threadIdx.x == 0) { s_lcn = 0u; s_lct = 0u; }
   __syncthreads();
   // per-thread counters fit 32 bits over one launch (at most 2048 steps)
@@ -865,11 +874,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     const uint32_t stride = 32u * nw;
     uint32_t base = 32u * (gw - w0);
     uint32_t s_nx = base + lane < n ? __ldcg(ain + base + lane) : MANTA_NONE;
+    Veh w_nx;
+    if (base + lane < n) w_nx = load_veh(Rin, base + lane);
     for (; base < n; base += stride) {
       const uint32_t i = base + (uint32_t)lane;
       uint32_t s = s_nx;
-      // the warp's next entries load while it works on these
-      s_nx = base + stride + lane < n ? __ldcg(ain + base + stride + lane) : MANTA_NONE;
+      Veh w = w_nx;
+      // the warp's next entries and their state load while it works on
+      // these (a hole's state is loaded and ignored)
+      const uint32_t i2 = base + stride + (uint32_t)lane;
+      s_nx = i2 < n ? __ldcg(ain + i2) : MANTA_NONE;
+      if (i2 < n) w_nx = load_veh(Rin, i2);
       bool skip = false;
       if (s != MANTA_NONE && (s & kReqMark) != 0u) {
         s &= ~kReqMark;
@@ -882,10 +897,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         if (s != MANTA_NONE && IDX_OK(at, p.cap_list, 2)) aout[at] = at;
         pos = at;
       }
-      Veh w;
       bool cand = false;
       if (s != MANTA_NONE && !skip) {
-        w = load_veh(Rin, i);
         if (cmp && IDX_OK(pos, p.cap_slots, 39)) store_veh(Rout, pos, w);
         if (w.pcell != MANTA_NONE && IDX_OK(w.pcell, p.cap_map, 3)) clr[w.pcell] = (uint8_t)MANTA_EMPTY;
         if (IDX_OK(pos, p.cap_list, 4)) p.p3a[pos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
@@ -1044,7 +1057,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       const uint32_t qh = __ldg(p.q_off + e) + __ldcg(p.q_pos + e);
       const uint32_t j = __ldg(p.q_trip + qh);
       const int C = (int)cells_of(em.cnl);
-      const int need = min(C, L + p.s0c[class_of(em.cnl)]);
+      const int need = min(C, L + s_s0c[class_of(em.cnl)]);
       bool req = !(closable(em) && lane_closed(p, lb, k));
       if (req) {
         uint32_t byte;
@@ -1119,8 +1132,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         const int cls = class_of(em.cnl);
         const uint32_t stride = stride_of((uint32_t)C);
         const uint32_t gcell = em.row0 + (uint32_t)lane * stride + (uint32_t)cell;
-        const float a = p.a[cls], T = p.T[cls], s0 = p.s0[cls];
-        const float v0 = em.lim * p.v0f[cls];
+        const float a = s_a[cls], T = s_T[cls], s0 = s_s0[cls];
+        const float v0 = em.lim * s_v0f[cls];
         const float r1 = v / v0, r2 = r1 * r1, r4 = r2 * r2;
         const bool has_next = w.rc + 1u < w.rend;
         float xn, vn;
@@ -1174,7 +1187,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         }
         uint32_t dwn = 0;
         if (has_next && sc.reached_own && sc.stop_only) {
-          const int zone = C - 1 - (p.s0c[cls] + 2);
+          const int zone = C - 1 - (s_s0c[cls] + 2);
           if ((int)floorf(xn) >= zone && vn < p.stop_eps) dwn = dwell < 255u ? dwell + 1u : 255u;
         }
         if (has_next && sc.reached_own && sc.nt_own == 1u && IDX_OK(lb + (uint32_t)lane, p.cap_lanes, 12)) {
