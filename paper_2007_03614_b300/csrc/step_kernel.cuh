@@ -44,7 +44,7 @@
 // sets its register budget; every shape computes the same results.
 constexpr int kBlock = 256;
 // fields of a finish-queue entry
-enum { kFqX, kFqV, kFqId, kFqRc, kFqRend, kFqE, kFqLd, kFqRow0, kFqCnl, kFqLim, kFqDst, kFqS, kFqI, kFqCell, kFqLb,
+enum { kFqX, kFqV, kFqId, kFqRc, kFqRend, kFqE, kFqLd, kFqRow0, kFqCnl, kFqLim, kFqDst, kFqS, kFqI, kFqCell,
        kFqKind, kFqCL, kFqVL, kFqE2, kFqE2cnl, kFqFields };
 constexpr int kP3Words = 384 + kFqFields * 64;
 // Row batches of the main phase's leader walk land in a shared-memory slot
@@ -242,6 +242,17 @@ __device__ __forceinline__ Veh load_veh(const VehSet &R, uint32_t i) {
   const uint4 m = __ldcg(R.em + i);
   Veh w;
   w.x = a.x; w.v = a.y; w.id = b.x; w.rc = b.y; w.rend = b.z; w.e = b.w; w.ld = l; w.pcell = c;
+  w.em.row0 = m.x; w.em.cnl = m.y; w.em.lim = __uint_as_float(m.z); w.em.dst = m.w;
+  return w;
+}
+// The main phase's view: everything but the previous cell, which it only writes.
+__device__ __forceinline__ Veh load_veh_main(const VehSet &R, uint32_t i) {
+  const float2 a = __ldcg(R.xv + i);
+  const uint4 b = __ldcg(R.idr + i);
+  const uint32_t l = __ldcg(R.ld + i);
+  const uint4 m = __ldcg(R.em + i);
+  Veh w;
+  w.x = a.x; w.v = a.y; w.id = b.x; w.rc = b.y; w.rend = b.z; w.e = b.w; w.ld = l; w.pcell = MANTA_NONE;
   w.em.row0 = m.x; w.em.cnl = m.y; w.em.lim = __uint_as_float(m.z); w.em.dst = m.w;
   return w;
 }
@@ -1086,7 +1097,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       const unsigned lt_mask = (1u << wl) - 1u;
       const uint32_t nwarps = gridDim.x * (BLOCK / 32);
       uint32_t *const wb = s_wbuf + wid * kWarpWords;
-      uint32_t *ps = wb, *pi = wb + 32, *pa = wb + 64;
+      uint32_t *pi = wb + 32, *pa = wb + 64;
       uint32_t *fq = wb + 384;   // finish queue: kFqFields fields x 64 entries
       // the lane's batch slot (shared-window address for the copies, pointer for the reads)
       const uint8_t *slot_p = reinterpret_cast<const uint8_t *>(wb + kP3Words) + wl * kSlotBytes;
@@ -1106,7 +1117,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       if (wl == 0) s_rqn[wid] = 0;
       int pn = 0, pu = 0;         // pool size and entries taken (warp-uniform)
       int st = 0;                 // 0 idle, 1 record requested, 2 walking
-      uint32_t s = 0, i = 0, lb = 0, a3 = MANTA_NONE;
+      uint32_t s = 0, i = 0, a3 = MANTA_NONE;
       int cell = 0;
       // The update of the vehicle in finish-queue entry j (Eq. 1, ballistic
       // step, clamp, map write, requests, arrivals).
@@ -1117,7 +1128,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         w.e = fq[kFqE * 64 + j]; w.ld = fq[kFqLd * 64 + j]; w.pcell = MANTA_NONE;
         w.em.row0 = fq[kFqRow0 * 64 + j]; w.em.cnl = fq[kFqCnl * 64 + j];
         w.em.lim = __uint_as_float(fq[kFqLim * 64 + j]); w.em.dst = fq[kFqDst * 64 + j];
-        const uint32_t s = fq[kFqS * 64 + j], i = fq[kFqI * 64 + j], lb = fq[kFqLb * 64 + j];
+        const uint32_t s = fq[kFqS * 64 + j], i = fq[kFqI * 64 + j];
         const int cell = (int)fq[kFqCell * 64 + j];
         Scan sc;
         const uint32_t kd = fq[kFqKind * 64 + j];
@@ -1190,8 +1201,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           const int zone = C - 1 - (s_s0c[cls] + 2);
           if ((int)floorf(xn) >= zone && vn < p.stop_eps) dwn = dwell < 255u ? dwell + 1u : 255u;
         }
-        if (has_next && sc.reached_own && sc.nt_own == 1u && IDX_OK(lb + (uint32_t)lane, p.cap_lanes, 12)) {
-          const uint32_t g = lb + (uint32_t)lane;
+        // request and stop-line slots of the vehicle's edge, loaded only where used
+        if (has_next && sc.reached_own && sc.nt_own == 1u &&
+            IDX_OK(__ldg(p.rslot + w.e) + (uint32_t)lane, p.cap_lanes, 12)) {
+          const uint32_t g = __ldg(p.rslot + w.e) + (uint32_t)lane;
           p.slot_id[g] = w.id;
           p.slot_td[g] = ((uint32_t)(tag & 0xFFFFFF) << 8) | dwn;
         }
@@ -1208,7 +1221,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           rq_e2 = sc.e2 != MANTA_NONE ? sc.e2 : (__ldg(p.route + w.rc + 1u) & MANTA_EDGE_MASK);
           const uint32_t cnl2 = sc.e2 != MANTA_NONE ? sc.e2cnl : load_em(p, rq_e2).cnl;
           const int l2 = min(lane, lanes_of(cnl2) - 1);
-          rq_g = lb + (uint32_t)lane;
+          rq_g = __ldg(p.rslot + w.e) + (uint32_t)lane;
           rq_t = target_key(rq_e2, (uint32_t)l2);
           if (IDX_OK(rq_g, p.cap_lanes, 14)) {
             p.req_tgt[rq_g] = rq_t;
@@ -1283,8 +1296,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
             __syncwarp();
             if (valid) {
               const int q = __popc(vb & lt_mask);
-              ps[q] = cslot;
-              pi[q] = ch + (uint32_t)wl;
+              pi[q] = ch + (uint32_t)wl;     // the list position is the vehicle's state index
               pa[q] = caddr;
             }
             pn = __popc(vb);
@@ -1305,8 +1317,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           const int take = min(__popc(need), pn - pu);
           const int rank = __popc(need & lt_mask);
           if (st == 0 && rank < take) {
-            s = ps[pu + rank];
             i = pi[pu + rank];
+            s = i;
             a3 = pa[pu + rank];
             st = 1;
           }
@@ -1317,7 +1329,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         Fetch f;
         if (st == 1) {
           // the record and, in the same round trip, the first batch of its row
-          w = load_veh(R, s);
+          w = load_veh_main(R, s);
           if (a3 != MANTA_NONE) slot_fetch(slot_s, cur + a3, kFirstChunks);
         } else if (st == 2) {
           walk_issue(p, cur, w, wk, slot_s, f);
@@ -1334,7 +1346,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         cp_async_wait_all();
         bool fin = false;
         if (st == 1) {
-          lb = __ldg(p.rslot + w.e);          // request / stop-line slots, needed when the vehicle is done
           cell = (int)floorf(w.x);
           fin = walk_start(p, cur, k, w, cell, wk, sc, c_scan);
           st = 2;
@@ -1353,7 +1364,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           fq[kFqE * 64 + at] = w.e; fq[kFqLd * 64 + at] = w.ld; fq[kFqRow0 * 64 + at] = w.em.row0;
           fq[kFqCnl * 64 + at] = w.em.cnl; fq[kFqLim * 64 + at] = __float_as_uint(w.em.lim);
           fq[kFqDst * 64 + at] = w.em.dst; fq[kFqS * 64 + at] = s; fq[kFqI * 64 + at] = i;
-          fq[kFqCell * 64 + at] = (uint32_t)cell; fq[kFqLb * 64 + at] = lb;
+          fq[kFqCell * 64 + at] = (uint32_t)cell;
           fq[kFqKind * 64 + at] = (uint32_t)sc.kind | ((uint32_t)sc.reached_own << 2) | ((uint32_t)sc.stop_only << 3) |
                                   (sc.nt_own << 4);
           fq[kFqCL * 64 + at] = (uint32_t)sc.cL; fq[kFqVL * 64 + at] = __float_as_uint(sc.vL);
