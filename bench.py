@@ -911,6 +911,52 @@ def run_stress(args):
         "hourly": hourly, "clocks": clk.summary(), "gpu_launches": len(times)}))
 
 
+def run_eq2(args):
+    """Sensitivity of the morning to Eq. 2's length scale: the paper prints
+    Eq. 2 without a unit for x (x0 = 1); the default reading takes metres,
+    so lambda = 1 m and mandatory changes happen only a few metres before
+    the node.  The metro-shaped morning (05:00-12:00) runs once per lambda
+    in `--lambdas` on the same trips; reported per run: lane changes,
+    gap-acceptance evaluations, clamps, arrivals, vehicles left at 12:00,
+    hourly link speeds and device time."""
+    import torch
+
+    from paper_2007_03614_b300 import manta
+    from paper_2007_03614_b300.build import build
+    rank, world = _dist()
+    if rank != 0:
+        return
+    build()
+    manta.load_library()
+    torch.cuda.set_device(0)
+    net, tr = workload()
+    stream = torch.cuda.Stream()
+    runs = {}
+    for lam in args.lambdas:
+        sim = manta.Sim(net, stream=stream, t0_step=T0_STEP, stats_window_steps=7200, n_stats_windows=7,
+                        lc_len_scale_m=float(lam))
+        sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        left = MORNING_STEPS
+        while left > 0:
+            sim.step(min(1800, left))
+            left -= 1800
+        ev1.record(stream)
+        ev1.synchronize()
+        st = sim.stats()
+        runs[str(lam)] = {"lc_len_scale_m": float(lam), "wall_s": ev0.elapsed_time(ev1) / 1000.0,
+                          "updates_per_s": st["vehicle_updates"] / (ev0.elapsed_time(ev1) / 1000.0),
+                          "stats": st, "hourly": hourly_speeds(sim, 7)}
+        sim.close()
+    print(json.dumps({
+        "metric": "Eq. 2 length-scale sensitivity (metro-shaped morning 05:00-12:00)",
+        "value": None, "unit": None, "n_gpus": 1, "steps": 1, "warmup": 0, "data": "synthetic",
+        "config": {"workload": "eq2", "lambdas_m": [float(x) for x in args.lambdas], "sim_steps": MORNING_STEPS},
+        "runs": runs}))
+
+
 def run_reference(args):
     """The oracle (this paper has no reference code) on the dense peak-hour
     sample of peak_sample: each bench step is --ref-chunk oracle time steps."""
@@ -958,7 +1004,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="metro",
-                    choices=["metro", "ensemble", "calibrate", "redgreen", "search", "stress"])
+                    choices=["metro", "ensemble", "calibrate", "redgreen", "search", "stress", "eq2"])
+    ap.add_argument("--lambdas", type=float, nargs="+", default=[1.0, 10.0, 100.0],
+                    help="Eq. 2 length scales (m) of --workload eq2")
     ap.add_argument("--scenarios", type=int, default=64)
     ap.add_argument("--calib-iters", type=int, default=6, help="gradient steps of --workload calibrate")
     ap.add_argument("--sigma-frac", type=float, default=0.05,
@@ -985,6 +1033,8 @@ def main():
         run_search(args)
     elif args.workload == "stress":
         run_stress(args)
+    elif args.workload == "eq2":
+        run_eq2(args)
     else:
         run_gpu(args)
 
