@@ -470,6 +470,53 @@ def cpu_baseline(net, tr, n_steps, stream=None):
     return out
 
 
+def _oracle_scenario(job):
+    """One ensemble scenario on the CPU oracle for n_steps steps from 07:00
+    (a worker of the ensemble's CPU baseline)."""
+    net, tr, t0, n_steps = job
+    from oracle import oracle as O
+    s = O.OracleSim(net, t0_step=t0, n_stats_windows=16)
+    s.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+    t = time.perf_counter()
+    s.step(n_steps)
+    dt = time.perf_counter() - t
+    upd = s.stats()["vehicle_updates"]
+    s.close()
+    return upd, dt
+
+
+def _warm_worker(_):
+    from oracle import oracle as O
+    O.build()
+    return 0
+
+
+def ensemble_cpu_baseline(sc, t0, n_steps):
+    """The oracle on every scenario of the ensemble for n_steps steps, (a) one
+    process running them one after another, (b) one process per usable host
+    core (independent scenarios, spawn-started pool): scenario-steps/s and
+    vehicle-updates/s of each."""
+    import multiprocessing as mp
+    jobs = [(net, tr, t0, n_steps) for net, tr in sc]
+    out = {"sample": f"{len(sc)} scenarios x {n_steps} steps from 07:00", "host": host_cpu()}
+    t = time.perf_counter()
+    res = [_oracle_scenario(j) for j in jobs]
+    one = time.perf_counter() - t
+    upd = sum(r[0] for r in res)
+    out["one_process"] = {"seconds": one, "scenario_steps_per_s": len(sc) * n_steps / one,
+                          "vehicle_updates_per_s": upd / one, "cores": 1}
+    nproc = out["host"]["nproc"] or 1
+    with mp.get_context("spawn").Pool(nproc) as pool:
+        pool.map(_warm_worker, range(nproc))        # process start and imports, untimed
+        t = time.perf_counter()
+        res = pool.map(_oracle_scenario, jobs, chunksize=1)
+        many = time.perf_counter() - t
+    out["per_core_processes"] = {"seconds": many, "scenario_steps_per_s": len(sc) * n_steps / many,
+                                 "vehicle_updates_per_s": sum(r[0] for r in res) / many, "cores": nproc}
+    out["vehicle_updates"] = upd
+    return out
+
+
 def run_ensemble(args):
     """64 uneven what-if scenarios, one simulated hour each (07:00-08:00), run
     (a) batched: one simulation of the disjoint union.  On a first instance
@@ -559,6 +606,8 @@ def run_ensemble(args):
         "sequential": {"seconds": seq, "scenarios_per_s": n / seq, "vehicle_updates": seq_upd,
                        "vehicle_updates_per_s": seq_upd / seq, "shape": list(shapes[0])},
         "batched_over_sequential": seq / tb,
+        "batched_scenario_steps_per_s": n * steps / tb,
+        "cpu_baseline": None if args.no_cpu_baseline else ensemble_cpu_baseline(sc, t0, args.ens_cpu_steps),
         "gpu_launches": args.steps * ((steps + 2047) // 2048)}))
 
 
@@ -1008,6 +1057,8 @@ def main():
     ap.add_argument("--lambdas", type=float, nargs="+", default=[1.0, 10.0, 100.0],
                     help="Eq. 2 length scales (m) of --workload eq2")
     ap.add_argument("--scenarios", type=int, default=64)
+    ap.add_argument("--ens-cpu-steps", type=int, default=300,
+                    help="steps per scenario of the ensemble's CPU oracle baseline")
     ap.add_argument("--calib-iters", type=int, default=6, help="gradient steps of --workload calibrate")
     ap.add_argument("--sigma-frac", type=float, default=0.05,
                     help="per-driver speed limits of --workload search: sigma_s / speed limit (Section IV-B)")
