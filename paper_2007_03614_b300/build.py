@@ -43,7 +43,7 @@ def _stale(out, deps):
 # index.  Same ABI; results must equal the product build's bit for bit.
 VARIANTS = {
     "lccap": ["-DMANTA_LC_CAP=4"],
-    "walk4": ["-DMANTA_WALK_CHUNKS=4", "-DMANTA_FIRST_CHUNKS=2"],
+    "walk8": ["-DMANTA_WALK_CHUNKS=8", "-DMANTA_FIRST_CHUNKS=4"],
     "walk16": ["-DMANTA_WALK_CHUNKS=16", "-DMANTA_FIRST_CHUNKS=8"],
     # index checks on every device write of the step kernel (manta_debug_checks)
     "check": ["-DMANTA_CHECK_BOUNDS"],

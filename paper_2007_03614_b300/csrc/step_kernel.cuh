@@ -25,18 +25,22 @@
 // loads in flight: in P3 every lane runs its own vehicle through a state
 // machine of one round trip per iteration and takes a new vehicle as soon as
 // one is done; the vehicle record and its first row batch come back together;
-// the main phase's walk batches (64 bytes first, then 128) land in a
+// the main phase's walk batches (32 bytes first, then 64) land in a
 // shared-memory slot per lane by asynchronous copies, holding no registers,
 // while the lane-change scans load four 16-byte chunks per round trip into
 // registers; and the next segment's node data comes with the batch that ends
 // the current one.
 #include <stdint.h>
 #include "sim.cuh"
+// 16-byte chunks per walk round trip and in the first batch (fetched with
+// the vehicle's state).  32 and 64 bytes suit the congested states that
+// dominate a morning (about 10 cells scanned per update) and cost nothing in
+// free flow; test builds select other sizes.
 #ifndef MANTA_WALK_CHUNKS
-#define MANTA_WALK_CHUNKS 8
+#define MANTA_WALK_CHUNKS 4
 #endif
 #ifndef MANTA_FIRST_CHUNKS
-#define MANTA_FIRST_CHUNKS 4
+#define MANTA_FIRST_CHUNKS 2
 #endif
 
 // Threads per block of the helper kernels.  The step kernel is a template

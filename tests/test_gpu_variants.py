@@ -4,8 +4,8 @@
   nearly every candidate goes through the block's overflow region of the
   global candidate list (the product build overflows only when a block lists
   more than ~2,100 candidates in one step).
-- walk4 / walk16: leader-walk batches of 32 / 64 bytes and of 128 / 256 bytes
-  (first batch / later batches) instead of 64 / 128.
+- walk8 / walk16: leader-walk batches of 64 / 128 bytes and of 128 / 256 bytes
+  (first batch / later batches) instead of 32 / 64.
 
 Each is compared every step on mixed small networks (lane changes, merges,
 stop signs, signals, closures) and at checkpoints on the tiny workload and on
@@ -22,7 +22,7 @@ from test_gpu_parity import _compare, _compare_all, _subset
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ("lccap", "walk4", "walk16")
+VARIANTS = ("lccap", "walk8", "walk16")
 
 
 @pytest.fixture(scope="module", autouse=True)
