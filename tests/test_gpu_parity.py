@@ -243,8 +243,8 @@ def test_metro_incident_closures_bit_exact(metro):
 def test_metro_dense_state_bit_exact(metro):
     """A dense mid-morning state on the full metro network, at the size the
     benchmark runs: ~500k vehicles put on the network at 07:30 by the seeded
-    dense-state generator (the same placements on both sides), 300 steps in
-    one 150-step launch and three 50-step launches, bit for bit.  The state is
+    dense-state generator (the same placements on both sides), 600 steps in
+    one 150-step launch, three 50-step launches and one of 300, bit for bit.  The state is
     built to reach the kernel's full-size paths: in the first step far more
     merge-phase items than half the warps (the record pass then shares warps
     with merge items), more arrivals than a quarter of the active list within
@@ -279,6 +279,68 @@ def test_metro_dense_state_bit_exact(metro):
         _compare(o, g, f"dense step {k + 50}")
     _compare_all(o, g, windows=(0,), where="dense step 300")
     assert g.stats()["on_network"] > 300_000
+    o.step(300)
+    g.step(300)
+    _compare_all(o, g, windows=(0, 1), where="dense step 600")
+
+
+def test_metro_first_trips_window_bit_exact(metro):
+    """05:00, the start of the morning: the trips departing 05:00-05:10 on the
+    empty metro network, 600 steps in launches of 200, bit for bit."""
+    net, tr = metro
+    sub = _subset(tr, 5 * 3600, 5 * 3600 + 600)
+    assert sub.n_trips > 1000
+    o, g = _pair(net, sub, t0_step=36000, n_stats_windows=2)
+    for k in range(0, 600, 200):
+        o.step(200)
+        g.step(200)
+        _compare(o, g, f"05:00 window step {k + 200}")
+    _compare_all(o, g, windows=(0,))
+    assert g.stats()["on_network"] > 500
+
+
+def test_metro_late_morning_dense_state_bit_exact(metro):
+    """11:00: the trips departing 09:30-11:00 put along their routes (the
+    dense-state generator, ~280k vehicles), 600 steps in launches of 300,
+    bit for bit."""
+    net, tr = metro
+    lo = 11 * 3600
+    sub = _subset(tr, lo - 5400, lo + 300)
+    pl = synth.dense_state(net, sub, lo - 5400, lo, head_frac=0.1, seed=11)
+    assert pl.n > 200_000
+    o, g = _pair(net, sub, t0_step=int(lo / 0.5), n_stats_windows=2)
+    o.place_many(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
+    g.place(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
+    for k in range(0, 600, 300):
+        o.step(300)
+        g.step(300)
+        _compare(o, g, f"11:00 dense step {k + 300}")
+    _compare_all(o, g, windows=(0, 1), where="11:00 dense step 600")
+
+
+def test_stress_dense_state_with_incidents_bit_exact():
+    """The stress configuration (~1.6M edges) at 08:00 with its incident lane
+    closures active: the trips departing 07:45-08:00 put along their routes,
+    none in a closed lane, 200 steps, bit for bit."""
+    net = synth.stress_network()
+    tr = synth.stress_trips(net)
+    clo = synth.incident_closures(net)
+    lo = 8 * 3600
+    sub = _subset(tr, lo - 900, lo + 300)
+    pl = synth.dense_state(net, sub, lo - 900, lo, head_frac=0.15, seed=13)
+    closed = {(e, l) for (e, l, _, _) in clo}
+    e = sub.route_edges[sub.route_off[pl.trip] + pl.route_pos]
+    keep = np.array([(int(a), int(b)) not in closed for a, b in zip(e, pl.lane)])
+    assert keep.sum() > 200_000
+    o, g = _pair(net, sub, closures=clo, t0_step=int(lo / 0.5), n_stats_windows=2)
+    args = [a[keep] for a in (pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)]
+    o.place_many(*args)
+    g.place(*args)
+    for k in range(0, 200, 100):
+        o.step(100)
+        g.step(100)
+        _compare(o, g, f"stress dense step {k + 100}")
+    _compare_all(o, g, windows=(0,), where="stress dense step 200")
 
 
 def test_place_rejects_bad_placements():
