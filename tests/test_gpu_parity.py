@@ -372,6 +372,19 @@ def test_place_rejects_bad_placements():
     with pytest.raises(manta.MantaError) as ei:
         g.place([2], [0], [0], [1.0], [0.0])
     assert ei.value.status == manta.E_STATE
+    # what only the device sees: a lane the edge lacks, a position past its
+    # end, two placements on one cell; each leaves that simulation unusable
+    for bad in (([0], [1], [2], [10.0], [5.0]), ([0], [1], [0], [100.0], [5.0]),
+                ([0, 1], [1, 0], [0, 0], [10.5, 10.25], [5.0, 0.0])):
+        g2 = manta.Sim(net)
+        nets.load(g2, tr)
+        with pytest.raises(manta.MantaError) as ei:
+            g2.place(*bad)
+        assert ei.value.status == manta.E_INVALID
+        with pytest.raises(manta.MantaError) as ei:
+            g2.step(1)
+        assert ei.value.status == manta.E_STATE
+        g2.close()
 
 
 def test_metro_full_morning_properties(metro):
