@@ -122,6 +122,7 @@ __global__ void place_kernel(Params p, const uint32_t *trip, const uint32_t *rab
     w.ld = ld_for_entry(p, r, l); w.pcell = MANTA_NONE; w.em = em;
     w.em.lim = driver_limit(p, em.lim, j, r);
     store_veh(p.vs[0], i, w);
+    p.vs[0].nx[i] = r + 1u < w.rend ? p.route[r + 1u] : 0u;
     act[i] = i;
     atomicAdd(p.entry + e, 1u);
   }
@@ -475,8 +476,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   P.slot_id = dalloc<uint32_t>(S, lanes_total, &ok);
   P.entry = dalloc<uint32_t>(S, E, &ok);
   P.exitc = dalloc<uint32_t>(S, E, &ok);
-  P.ssum = dalloc<unsigned long long>(S, (size_t)E * cfg->n_stats_windows, &ok);
-  P.scnt = dalloc<uint32_t>(S, (size_t)E * cfg->n_stats_windows, &ok);
+  P.lstat = dalloc<LinkStat>(S, (size_t)E * cfg->n_stats_windows, &ok);
   P.pending = dalloc<uint32_t>(S, E, &ok);
   P.q_pos = dalloc<uint32_t>(S, E, &ok);
   P.dep_key = dalloc<unsigned long long>(S, E, &ok);
@@ -497,8 +497,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
        cudaMemsetAsync(P.slot_td, 0, sizeof(uint32_t) * std::max<uint32_t>(lanes_total, 1), S->stream) == cudaSuccess &&
        cudaMemsetAsync(P.entry, 0, sizeof(uint32_t) * E, S->stream) == cudaSuccess &&
        cudaMemsetAsync(P.exitc, 0, sizeof(uint32_t) * E, S->stream) == cudaSuccess &&
-       cudaMemsetAsync(P.ssum, 0, sizeof(unsigned long long) * (size_t)E * cfg->n_stats_windows, S->stream) == cudaSuccess &&
-       cudaMemsetAsync(P.scnt, 0, sizeof(uint32_t) * (size_t)E * cfg->n_stats_windows, S->stream) == cudaSuccess &&
+       cudaMemsetAsync(P.lstat, 0, sizeof(LinkStat) * (size_t)E * cfg->n_stats_windows, S->stream) == cudaSuccess &&
        cudaMemsetAsync(P.pending, 0, sizeof(uint32_t) * E, S->stream) == cudaSuccess &&
        cudaMemsetAsync(P.q_pos, 0, sizeof(uint32_t) * E, S->stream) == cudaSuccess &&
        cudaMemsetAsync(P.dep_key, 0, sizeof(unsigned long long) * E, S->stream) == cudaSuccess &&
@@ -649,6 +648,7 @@ manta_status manta_load_trips(manta_sim *S, int64_t n, const int64_t *route_off,
     P.vs[b].ld = dalloc<uint32_t>(S, NT, &ok);
     P.vs[b].pc = dalloc<uint32_t>(S, NT, &ok);
     P.vs[b].em = dalloc<uint4>(S, NT, &ok);
+    P.vs[b].nx = dalloc<uint32_t>(S, NT, &ok);
   }
   P.act0 = dalloc<uint32_t>(S, NT, &ok); P.act1 = dalloc<uint32_t>(S, NT, &ok);
   P.lcm = dalloc<LcMove>(S, NT, &ok);
@@ -1082,8 +1082,15 @@ manta_status manta_edge_counters(manta_sim *S, uint32_t *entries, uint32_t *exit
   bool ok = true;
   if (entries) ok = ok && cudaMemcpy(entries, S->P.entry, 4 * E, cudaMemcpyDeviceToHost) == cudaSuccess;
   if (exits) ok = ok && cudaMemcpy(exits, S->P.exitc, 4 * E, cudaMemcpyDeviceToHost) == cudaSuccess;
-  if (speed_sum_fx) ok = ok && cudaMemcpy(speed_sum_fx, S->P.ssum + (size_t)window * E, 8 * E, cudaMemcpyDeviceToHost) == cudaSuccess;
-  if (speed_cnt) ok = ok && cudaMemcpy(speed_cnt, S->P.scnt + (size_t)window * E, 4 * E, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (speed_sum_fx || speed_cnt) {
+    std::vector<LinkStat> ls(E);
+    ok = ok && cudaMemcpy(ls.data(), S->P.lstat + (size_t)window * E, sizeof(LinkStat) * E, cudaMemcpyDeviceToHost) ==
+                   cudaSuccess;
+    for (size_t e = 0; ok && e < E; ++e) {
+      if (speed_sum_fx) speed_sum_fx[e] = ls[e].sum;
+      if (speed_cnt) speed_cnt[e] = ls[e].cnt;
+    }
+  }
   if (!ok) return fail(MANTA_E_CUDA, "copy of edge counters failed");
   return st;
 }
@@ -1292,12 +1299,12 @@ std::vector<std::pair<void *, size_t>> mutable_state(const manta_sim *S) {
   const size_t map = (size_t)S->atlas_bytes + kMapPad;
   return {{P.atlas0, map}, {P.atlas1, map}, {P.permit, 4 * N}, {P.rr, 4 * N},
           {P.req_key, 8 * G}, {P.req_tgt, 4 * G}, {P.slot_td, 4 * G}, {P.slot_id, 4 * G},
-          {P.entry, 4 * E}, {P.exitc, 4 * E}, {P.ssum, 8 * E * W}, {P.scnt, 4 * E * W},
+          {P.entry, 4 * E}, {P.exitc, 4 * E}, {P.lstat, sizeof(LinkStat) * E * W},
           {P.pending, 4 * E}, {P.q_pos, 4 * E}, {P.dep_key, 8 * E}, {P.dep0, 4 * E}, {P.dep1, 4 * E},
           {P.ctl, sizeof(Ctl)}, {P.act0, 4 * NT}, {P.act1, 4 * NT},
           {P.vs[0].xv, 8 * NT}, {P.vs[0].idr, 16 * NT}, {P.vs[0].ld, 4 * NT}, {P.vs[0].pc, 4 * NT},
           {P.vs[0].em, 16 * NT}, {P.vs[1].xv, 8 * NT}, {P.vs[1].idr, 16 * NT}, {P.vs[1].ld, 4 * NT},
-          {P.vs[1].pc, 4 * NT}, {P.vs[1].em, 16 * NT}};
+          {P.vs[1].pc, 4 * NT}, {P.vs[1].em, 16 * NT}, {P.vs[0].nx, 4 * NT}, {P.vs[1].nx, 4 * NT}};
 }
 }  // namespace
 

@@ -11,8 +11,9 @@
 //                 route end, edge); the lane word (lane, dwell, lane mask
 //                 toward the next edge); the cell it left in the other map
 //                 buffer (cleared next step); a copy of the current edge's
-//                 record.  A warp working on consecutive list positions loads
-//                 each array with one coalesced instruction.
+//                 record; the next route entry.  A warp working on consecutive
+//                 list positions loads each array with one coalesced
+//                 instruction.
 //   lists         the active list (a vehicle keeps its position while on the
 //                 network; arrivals leave holes, departures append, and a
 //                 compaction pass moves the live vehicles into the other
@@ -98,6 +99,15 @@ struct VehSet {
   uint32_t *ld;    // lane word (as Veh::ld)
   uint32_t *pc;    // its cell in the other map buffer (cleared next step), or none
   uint4 *em;       // record of its current edge (as EdgeMeta)
+  uint32_t *nx;    // the route entry after its current one (route[rc + 1]), or 0 on its last edge
+};
+
+// Link-speed statistic of one (window, edge): the sum of end-of-step speeds
+// in 2^-20 m/s units and the number of vehicle-steps, in one 16-byte record
+// so that a vehicle-step's two reductions touch one 32-byte sector.
+struct __align__(16) LinkStat {
+  unsigned long long sum;
+  uint32_t cnt, pad;
 };
 
 struct Ctl {
@@ -178,8 +188,7 @@ struct Params {
   uint32_t *permit, *rr;
   // statistics
   uint32_t *entry, *exitc;
-  unsigned long long *ssum;
-  uint32_t *scnt;
+  LinkStat *lstat;             // by window * E + edge
   Ctl *ctl;
   // model constants
   float dt;

@@ -279,6 +279,7 @@ __device__ __forceinline__ VehSet veh_set(const Params &p, uint32_t sel) {
   r.ld = sel ? p.vs[1].ld : p.vs[0].ld;
   r.pc = sel ? p.vs[1].pc : p.vs[0].pc;
   r.em = sel ? p.vs[1].em : p.vs[0].em;
+  r.nx = sel ? p.vs[1].nx : p.vs[0].nx;
   return r;
 }
 
@@ -669,7 +670,7 @@ __device__ __forceinline__ bool walk_start(const Params &p, const uint8_t *cur, 
   s.kind = SC_FREE; s.cL = 0; s.vL = 0.0f; s.reached_own = false; s.stop_only = false;
   s.nt_own = 0u; s.e2 = MANTA_NONE; s.e2cnl = 0u;
   wk.limit = cell + p.H; wk.base = 0; wk.pos = cell + 1; wk.sl = ld_lane(w.ld);
-  wk.r = w.rc; wk.se = w.e; wk.sm = w.em; wk.own = true; wk.nent = 0u;
+  wk.r = w.rc; wk.se = w.e; wk.sm = w.em; wk.own = true;   // wk.nent: the next route entry, from the state
   const int C = (int)cells_of(w.em.cnl);
   if (closable(w.em)) {
     const int half = C / 2;
@@ -687,7 +688,6 @@ __device__ __forceinline__ bool walk_start(const Params &p, const uint8_t *cur, 
       return true;
     }
   }
-  if (C <= wk.limit && w.rc + 1u < w.rend) wk.nent = __ldg(p.route + w.rc + 1u);
   return false;
 }
 
@@ -890,16 +890,24 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     uint32_t base = 32u * (gw - w0);
     uint32_t s_nx = base + lane < n ? __ldcg(ain + base + lane) : MANTA_NONE;
     Veh w_nx;
-    if (base + lane < n) w_nx = load_veh(Rin, base + lane);
+    uint32_t r_nx = 0u;   // the next route entry, moved by a compaction
+    if (base + lane < n) {
+      w_nx = load_veh(Rin, base + lane);
+      if (cmp) r_nx = __ldcg(Rin.nx + base + lane);
+    }
     for (; base < n; base += stride) {
       const uint32_t i = base + (uint32_t)lane;
       uint32_t s = s_nx;
       Veh w = w_nx;
+      const uint32_t rn = r_nx;
       // the warp's next entries and their state load while it works on
       // these (a hole's state is loaded and ignored)
       const uint32_t i2 = base + stride + (uint32_t)lane;
       s_nx = i2 < n ? __ldcg(ain + i2) : MANTA_NONE;
-      if (i2 < n) w_nx = load_veh(Rin, i2);
+      if (i2 < n) {
+        w_nx = load_veh(Rin, i2);
+        if (cmp) r_nx = __ldcg(Rin.nx + i2);
+      }
       bool skip = false;
       if (s != MANTA_NONE && (s & kReqMark) != 0u) {
         s &= ~kReqMark;
@@ -914,7 +922,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       }
       bool cand = false;
       if (s != MANTA_NONE && !skip) {
-        if (cmp && IDX_OK(pos, p.cap_slots, 39)) store_veh(Rout, pos, w);
+        if (cmp && IDX_OK(pos, p.cap_slots, 39)) {
+          store_veh(Rout, pos, w);
+          Rout.nx[pos] = rn;
+        }
         if (w.pcell != MANTA_NONE && IDX_OK(w.pcell, p.cap_map, 3)) clr[w.pcell] = (uint8_t)MANTA_EMPTY;
         if (IDX_OK(pos, p.cap_list, 4)) p.p3a[pos] = first_batch(w.em, ld_lane(w.ld), (int)floorf(w.x));
         cand = lc_candidate(w, kk);
@@ -1241,8 +1252,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           if (win >= 0) {
             const size_t o = (size_t)win * p.E + w.e;
             if (IDX_OK(o, (uint64_t)p.n_win * p.E, 17)) {
-              atomicAdd(p.ssum + o, (unsigned long long)(vn * 1048576.0f));
-              atomicAdd(p.scnt + o, 1u);
+              atomicAdd(&p.lstat[o].sum, (unsigned long long)(vn * 1048576.0f));
+              atomicAdd(&p.lstat[o].cnt, 1u);
             }
           }
         }
@@ -1334,6 +1345,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         if (st == 1) {
           // the record and, in the same round trip, the first batch of its row
           w = load_veh_main(R, s);
+          wk.nent = __ldcg(R.nx + s);
           if (a3 != MANTA_NONE) slot_fetch(slot_s, cur + a3, kFirstChunks);
         } else if (st == 2) {
           walk_issue(p, cur, w, wk, slot_s, f);
@@ -1438,6 +1450,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         const EdgeMeta em2 = load_em(p, e2);
         Veh w = load_veh(R, s);
         const uint32_t ld2 = ld_for_entry(p, w.rc + 1u, tgt & 15u);   // with the competitors' slots
+        const uint32_t nx2 = w.rc + 2u < w.rend ? __ldg(p.route + w.rc + 2u) : 0u;
         const int lane = ld_lane(w.ld);
         const EdgeMeta em = w.em;
         const uint32_t stride = stride_of(cells_of(em.cnl));
@@ -1482,12 +1495,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           }
         }
         w.x = xf; w.v = vf;
-        if (IDX_OK(s, p.cap_slots, 27)) store_veh(R, s, w);
+        if (IDX_OK(s, p.cap_slots, 27)) {
+          store_veh(R, s, w);
+          if (win_it) R.nx[s] = nx2;
+        }
         if (win >= 0) {
           const size_t o = (size_t)win * p.E + ef;
           if (IDX_OK(o, (uint64_t)p.n_win * p.E, 28)) {
-            atomicAdd(p.ssum + o, (unsigned long long)(vf * 1048576.0f));
-            atomicAdd(p.scnt + o, 1u);
+            atomicAdd(&p.lstat[o].sum, (unsigned long long)(vf * 1048576.0f));
+            atomicAdd(&p.lstat[o].cnt, 1u);
           }
         }
         if (ahead) {
@@ -1507,11 +1523,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
         bool won = j != MANTA_NONE;
         const EdgeMeta em = load_em(p, e);
         const uint32_t qp = __ldcg(p.q_pos + e);
-        uint32_t rc = 0u, rend = 0u, ld0 = 0u;
+        uint32_t rc = 0u, rend = 0u, ld0 = 0u, nx0 = 0u;
         if (won) {
           rc = __ldg(p.route_off + j);
           rend = __ldg(p.route_off + j + 1u);
           ld0 = ld_for_entry(p, rc, 0u);
+          nx0 = rc + 1u < rend ? __ldg(p.route + rc + 1u) : 0u;
           won = min_competitor(p, di.z, di.w, MANTA_NONE, target_key(e, 0u), tag) > j;
         }
         // the result of this atomic is first used after the list append
@@ -1528,7 +1545,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
           w.x = 0.0f; w.v = 0.0f; w.id = j; w.rc = rc; w.rend = rend;
           w.e = e; w.ld = ld0; w.pcell = MANTA_NONE; w.em = em;
           w.em.lim = driver_limit(p, em.lim, j, rc);
-          if (IDX_OK(s, p.cap_slots, 31)) store_veh(R, s, w);
+          if (IDX_OK(s, p.cap_slots, 31)) {
+            store_veh(R, s, w);
+            R.nx[s] = nx0;
+          }
           if (IDX_OK(ia, p.cap_list, 32)) act[ia] = s;
           if (IDX_OK(em.row0, p.cap_map, 33)) nxt[em.row0] = speed_code(0.0f);
           atomicAdd(p.entry + e, 1u);
