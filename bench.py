@@ -40,7 +40,9 @@ MORNING_STEPS = 50400               # 05:00-12:00
 # row): per vehicle update, the state a structure-of-arrays layout must read
 # (x 4, v 4, route cursor 4, edge 4, lane/flags/dwell 2, previous cell 4 = 22 B)
 # and write (18 B), the edge record it needs (12 B), the map byte written and
-# the one cleared (1 + 1); per lane-map cell examined by a leader scan, 1 B;
+# the one cleared (1 + 1); per lane-map cell read by a scan, 1 B: the leader
+# scans (cells_scanned) and the lane-change rule's scans (lc_cells_scanned:
+# own-lane leader, target-lane lead, lateral-overlap window, lead and lag);
 # per node a scan crosses, the next route entry (4 B); per gap-acceptance
 # evaluation, the lead and lag cells (8 B); per departure, 16 B.
 BYTES_PER_UPDATE = 54
@@ -63,8 +65,12 @@ WORKLOAD = ("metro-shaped morning: ~550k directed edges / ~218k nodes, 3.2M trip
 PEAK_HOUR = (7.5 * 3600, 8.5 * 3600)
 
 
-def algorithmic_bytes(d: dict) -> int:
+def algorithmic_bytes(d: dict, lc_scans: bool = True) -> int:
+    """The algorithmic bytes of the counters in d; lc_scans=False leaves out
+    the lane-change scans' cells (the figure reported before they were
+    counted)."""
     return (d["vehicle_updates"] * BYTES_PER_UPDATE + d["cells_scanned"] * BYTES_PER_CELL
+            + (d["lc_cells_scanned"] * BYTES_PER_CELL if lc_scans else 0)
             + d["route_reads"] * BYTES_PER_BOUNDARY + d["lc_evals"] * BYTES_PER_LC_EVAL
             + d["departed"] * BYTES_PER_DEPARTURE)
 
@@ -269,8 +275,8 @@ def run_gpu(args):
     sim = manta.Sim(net, stream=stream, t0_step=T0_STEP)
     sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    keys = ("vehicle_updates", "cells_scanned", "route_reads", "lc_evals", "clamps", "lane_changes", "departed",
-            "arrived")
+    keys = ("vehicle_updates", "cells_scanned", "lc_cells_scanned", "route_reads", "lc_evals", "clamps",
+            "lane_changes", "departed", "arrived")
 
     def timed_chunk():
         with torch.cuda.stream(stream):
@@ -362,6 +368,7 @@ def run_gpu(args):
         return {"seconds": round(tt, 4), "vehicle_updates": cc["vehicle_updates"],
                 "updates_per_s": cc["vehicle_updates"] / tt, "algorithmic_bytes_per_update": round(ab / u, 2),
                 "cells_per_update": round(cc["cells_scanned"] / u, 2),
+                "lc_cells_per_update": round(cc["lc_cells_scanned"] / u, 2),
                 "achieved_gbs": round(ab / tt / 1e9, 1), "frac": round(ab / tt / 1e9 / peak, 4)}
 
     hourly = {f"{h:02d}:00-{h + 1:02d}:00": summary(r) for h, r in sorted(hours.items())}
@@ -387,9 +394,11 @@ def run_gpu(args):
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": int(bytes_alg / max(1, args.steps)),
                      "algorithmic_bytes_per_update": round(bytes_alg / max(1, d["vehicle_updates"]), 2),
-                     "formula": f"{BYTES_PER_UPDATE} B/update + {BYTES_PER_CELL} B/cell scanned + "
-                                f"{BYTES_PER_BOUNDARY} B/route read + {BYTES_PER_LC_EVAL} B/gap-acceptance "
-                                f"evaluation + {BYTES_PER_DEPARTURE} B/departure",
+                     "formula": f"{BYTES_PER_UPDATE} B/update + {BYTES_PER_CELL} B/cell read by a leader "
+                                f"scan or a lane-change scan + {BYTES_PER_BOUNDARY} B/route read + "
+                                f"{BYTES_PER_LC_EVAL} B/gap-acceptance evaluation + {BYTES_PER_DEPARTURE} B/departure",
+                     "frac_without_lane_change_scans": round(
+                         algorithmic_bytes(d, lc_scans=False) / max(1, args.steps) / per_launch_s / 1e9 / peak, 4),
                      "frac_with_link_statistics": round(
                          (bytes_alg + BYTES_STATS_PER_UPDATE * d["vehicle_updates"]) / max(1, args.steps)
                          / per_launch_s / 1e9 / peak, 4),

@@ -103,6 +103,11 @@ typedef struct {
   uint64_t lane_changes;    /* lane changes applied                                    */
   uint64_t lc_evals;        /* gap-acceptance evaluations (Eqs. 3-4)                   */
   uint64_t route_reads;     /* route entries read by leader scans crossing a node       */
+  uint64_t lc_cells_scanned; /* lane-map cells read by the lane-change scans (Section II-D:
+                                own-lane leader and target-lane lead for a discretionary
+                                change, then the lateral-overlap window, the lead and the
+                                lag of the gap acceptance, Eqs. 3-4), each scan counted from
+                                its first cell to its hit or its end                         */
 } manta_stats_t;
 
 /* Fills *cfg with the defaults listed above. */

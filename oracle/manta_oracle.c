@@ -75,6 +75,7 @@ typedef struct {
 typedef struct {
   int64_t step, loaded, departed, arrived, on_network, waiting;
   uint64_t vehicle_updates, cells_scanned, clamps, lane_changes, lc_evals, route_reads;
+  uint64_t lc_cells_scanned;   /* lane-map cells read by the lane-change scans (step 3) */
 } oracle_stats_t;
 
 typedef struct {
@@ -411,19 +412,27 @@ OR_API int oracle_load_trips(osim *S, int64_t n, const int64_t *route_off, const
 }
 
 /* --------------------------------------------------------- lane change -- */
-/* first occupied cell of lane row `rw` in [lo, hi] scanning upward (-1 if none) */
-static int32_t first_up(const uint8_t *rw, int32_t lo, int32_t hi) {
-  for (int32_t c = lo; c <= hi; ++c) if (rw[c] != EMPTY) return c;
+/* first occupied cell of lane row `rw` in [lo, hi] scanning upward (-1 if
+ * none); every cell read is added to *cnt when cnt is not NULL */
+static int32_t first_up(const uint8_t *rw, int32_t lo, int32_t hi, uint64_t *cnt) {
+  for (int32_t c = lo; c <= hi; ++c) {
+    if (cnt) ++*cnt;
+    if (rw[c] != EMPTY) return c;
+  }
   return -1;
 }
-static int32_t first_down(const uint8_t *rw, int32_t hi, int32_t lo) {
-  for (int32_t c = hi; c >= lo; --c) if (rw[c] != EMPTY) return c;
+static int32_t first_down(const uint8_t *rw, int32_t hi, int32_t lo, uint64_t *cnt) {
+  for (int32_t c = hi; c >= lo; --c) {
+    if (cnt) ++*cnt;
+    if (rw[c] != EMPTY) return c;
+  }
   return -1;
 }
 
 /* Returns the target lane or -1.  Mandatory vs discretionary per Section
  * II-D; probability of attempting a mandatory change per Eq. 2; critical
- * lead/lag gaps per Eqs. 3 and 4.                                         */
+ * lead/lag gaps per Eqs. 3 and 4.  Every lane-map cell its scans read is
+ * counted in lc_cells_scanned.                                            */
 static int32_t lc_decide(osim *S, int64_t id) {
   const oracle_config *cf = &S->cfg;
   veh_t *V = &S->V[id];
@@ -465,6 +474,7 @@ static int32_t lc_decide(osim *S, int64_t id) {
     return -1;
   }
   const float v = V->v;
+  uint64_t *lcc = &S->st.lc_cells_scanned;   /* cells read by the scans below */
   uint8_t *tr = row(S, S->map_cur, e, lt);
   if (mandatory) {
     /* Eq. 2 probability at the distance to the end of the edge (or to the obstacle) */
@@ -472,14 +482,16 @@ static int32_t lc_decide(osim *S, int64_t id) {
     float u1 = rng_u(cf->seed, (uint64_t)id, k, 0);
     if (!(u1 < S->mtab[dist])) return -1;
   } else {
-    /* discretionary: a slower leader ahead in the own lane and more room ahead in the target lane */
+    /* discretionary: a slower leader ahead in the own lane and more room
+     * ahead in the target lane (a stopped vehicle has no slower leader) */
+    if (!(v > 0.0f)) return -1;
     uint8_t *orw = row(S, S->map_cur, e, l);
     int32_t hi = cell + H < Ce - 1 ? cell + H : Ce - 1;
-    int32_t co = first_up(orw, cell + 1, hi);
+    int32_t co = first_up(orw, cell + 1, hi, lcc);
     if (co < 0) return -1;
     if (!(speed_decode(orw[co]) < v)) return -1;
     int32_t own_gap = co - L - cell;
-    int32_t ca = first_up(tr, cell + L, hi);
+    int32_t ca = first_up(tr, cell + L, hi, lcc);
     if (ca >= 0 && !(ca - L - cell > own_gap)) return -1;
   }
   S->st.lc_evals++;
@@ -487,11 +499,11 @@ static int32_t lc_decide(osim *S, int64_t id) {
   {
     int32_t lo = cell - L + 1 < 0 ? 0 : cell - L + 1;
     int32_t hi = cell + L - 1 > Ce - 1 ? Ce - 1 : cell + L - 1;
-    if (first_up(tr, lo, hi) >= 0) return -1;            /* lateral overlap */
+    if (first_up(tr, lo, hi, lcc) >= 0) return -1;       /* lateral overlap */
   }
   int32_t hi = cell + H < Ce - 1 ? cell + H : Ce - 1;
-  int32_t ca = first_up(tr, cell + L, hi);
-  int32_t cb = first_down(tr, cell - L, cell - H < 0 ? 0 : cell - H);
+  int32_t ca = first_up(tr, cell + L, hi, lcc);
+  int32_t cb = first_down(tr, cell - L, cell - H < 0 ? 0 : cell - H, lcc);
   const float g = v < cf->g_speed_split ? cf->g_low : cf->g_high;
   const float alpha = cf->alpha_lo + (cf->alpha_hi - cf->alpha_lo) * rng_u(cf->seed, (uint64_t)id, 0, 3);
   if (ca >= 0) {
@@ -646,7 +658,7 @@ OR_API int oracle_step(osim *S, int64_t n_steps, char *err, int errlen) {
       int32_t need = L + (int32_t)ceilf(cf->s0[S->cls[e]]);
       if (need > S->C[e]) need = S->C[e];
       uint8_t *rw = row(S, S->map_cur, e, 0);
-      if (first_up(rw, 0, need - 1) >= 0) continue;
+      if (first_up(rw, 0, need - 1, NULL) >= 0) continue;
       dep[e] = j;
     }
     /* D: leader scan, IDM (Eq. 1), ballistic integration, clamp */

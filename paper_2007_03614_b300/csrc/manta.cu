@@ -1066,6 +1066,7 @@ manta_status manta_stats(manta_sim *S, manta_stats_t *out) {
   out->lane_changes = c.cnt[CNT_LC];
   out->lc_evals = c.cnt[CNT_LCE];
   out->route_reads = c.cnt[CNT_RR];
+  out->lc_cells_scanned = c.cnt[CNT_LCS];
   return MANTA_OK;
 }
 

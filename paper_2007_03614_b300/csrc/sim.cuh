@@ -47,7 +47,7 @@ struct EdgeSig {   // signal window of this in-edge at its head node
 };
 
 enum {
-  CNT_UPD = 0, CNT_SCAN, CNT_CLAMP, CNT_LC, CNT_LCE, CNT_RR, CNT_DEP, CNT_ARR, CNT_N
+  CNT_UPD = 0, CNT_SCAN, CNT_CLAMP, CNT_LC, CNT_LCE, CNT_RR, CNT_DEP, CNT_ARR, CNT_LCS, CNT_N
 };
 
 // One vehicle in registers (and the 48-byte copy kept for lane-change

@@ -464,7 +464,14 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t *counter, bool pred) {
 // Target lane or -1 (Section II-D: mandatory vs discretionary; Eq. 2; Eqs. 3-4).
 // The route entry (lane mask toward the next edge), the Eq. 2 probability and
 // the first chunks of the own and target lane rows are fetched together.
-__device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const Veh &w, uint32_t &c_lce) {
+// *lcs (the thread's counter in shared memory, so that no register holds it)
+// receives the lane-map cells the rule's scans read, counted as separate scans
+// in the rule's order (own-lane leader and target-lane lead of a discretionary
+// change; the lateral-overlap window, the lead and the lag of the gap
+// acceptance), each from its first cell to its hit or its end, although the
+// scans here share their loads.
+__device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const Veh &w, uint32_t &c_lce,
+                         uint32_t *lcs) {
   const EdgeMeta &em = w.em;
   const int nl = lanes_of(em.cnl);
   const int lane = ld_lane(w.ld);
@@ -537,17 +544,24 @@ __device__ int lc_decide(const Params &p, const uint8_t *cur, int64_t k, const V
     if (!own_scan) return -1;
     uint32_t bco;
     const int co = scan_from(orow, cell + 1, hi, bo, bco);
-    if (co < 0) return -1;
-    if (!(speed_decode(bco) < v)) return -1;
+    if (co < 0) { *lcs += (uint32_t)(hi - cell); return -1; }         // own lane, cell + 1 .. hi
+    if (!(speed_decode(bco) < v)) { *lcs += (uint32_t)(co - cell); return -1; }
     const int own_gap = co - L - cell;
     c1 = scan_from(trow, lo_t, hi, bt, bc1);
     if (c1 >= 0 && c1 <= cell + L - 1) ca = first_up(trow, cell + L, hi, bca);
     else { ca = c1; bca = bc1; }
+    // the own lane (co - cell = own_gap + L cells) and the target lead, cell + L .. hi
+    *lcs += (uint32_t)(own_gap + L + max(0, (ca >= 0 ? ca : hi) - (cell + L) + 1));
     if (ca >= 0 && !(ca - L - cell > own_gap)) return -1;
   }
   c_lce++;
-  if (c1 >= 0 && c1 <= cell + L - 1) return -1;     // lateral overlap
+  const bool overlap = c1 >= 0 && c1 <= cell + L - 1;
+  // the lateral-overlap window lo_t .. min(cell + L - 1, C - 1)
+  *lcs += (uint32_t)max(0, (overlap ? c1 : min(cell + L - 1, C - 1)) - lo_t + 1);
+  if (overlap) return -1;
+  *lcs += (uint32_t)max(0, (ca >= 0 ? ca : hi) - (cell + L) + 1);       // lead, cell + L .. hi
   const int cb = first_down(trow, cell - L, max(0, cell - H), bcb);
+  *lcs += (uint32_t)max(0, (cell - L) - (cb >= 0 ? cb : max(0, cell - H)) + 1);  // lag, cell - L down
   const float g = v < p.g_split ? p.g_low : p.g_high;
   const float alpha = p.alpha_lo + (p.alpha_hi - p.alpha_lo) * uni(p.seed, w.id, 0, 3);
   if (ca >= 0) {
@@ -823,6 +837,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
   // (kFqFields fields x 64 entries)
   extern __shared__ __align__(16) uint32_t s_wbuf[];
   __shared__ int s_rqn[BLOCK / 32];
+  __shared__ uint32_t s_lcs[BLOCK];                 // per thread: cells read by lane-change scans
   __shared__ uint32_t s_lcn, s_lct;                 // lane-change candidates of the block; batches taken
   Ctl *ctl = p.ctl;
   if (threadIdx.x < CNT_N) s_cnt[threadIdx.x] = 0ull;
@@ -832,6 +847,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
     s_v0f[threadIdx.x] = p.v0f[threadIdx.x]; s_s0c[threadIdx.x] = p.s0c[threadIdx.x];
   }
   if (threadIdx.x == 0) { s_lcn = 0u; s_lct = 0u; }
+  s_lcs[threadIdx.x] = 0u;
   __syncthreads();
   // per-thread counters fit 32 bits over one launch (at most 2048 steps)
   uint32_t c_upd = 0, c_scan = 0, c_clamp = 0, c_lc = 0, c_lce = 0, c_rr = 0, c_dep = 0, c_arr = 0;
@@ -1011,7 +1027,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
             c = load_veh_at(p.lcq + reg0 + (j - lc_cap));
             cpos = __ldcg(p.lcq_pos + reg0 + (j - lc_cap));
           }
-          const int tgt = lc_decide(p, cur, k, c, c_lce);
+          const int tgt = lc_decide(p, cur, k, c, c_lce, &s_lcs[threadIdx.x]);
           const uint32_t at = warp_append(&ctl->n_chg, tgt >= 0);
           if (tgt >= 0 && IDX_OK(at, p.cap_list, 6)) {
             // the whole move, so that P2 applies it in one round trip; the
@@ -1588,6 +1604,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
   atomicAdd(&s_cnt[CNT_RR], (unsigned long long)c_rr);
   atomicAdd(&s_cnt[CNT_DEP], (unsigned long long)c_dep);
   atomicAdd(&s_cnt[CNT_ARR], (unsigned long long)c_arr);
+  atomicAdd(&s_cnt[CNT_LCS], (unsigned long long)s_lcs[threadIdx.x]);
   __syncthreads();
   if (threadIdx.x < CNT_N && s_cnt[threadIdx.x]) atomicAdd(&ctl->cnt[threadIdx.x], s_cnt[threadIdx.x]);
   if (timer) {

@@ -38,7 +38,8 @@ class MantaStats(C.Structure):
                 ("arrived", C.c_int64), ("on_network", C.c_int64), ("waiting", C.c_int64),
                 ("vehicle_updates", C.c_uint64), ("cells_scanned", C.c_uint64),
                 ("clamps", C.c_uint64), ("lane_changes", C.c_uint64),
-                ("lc_evals", C.c_uint64), ("route_reads", C.c_uint64)]
+                ("lc_evals", C.c_uint64), ("route_reads", C.c_uint64),
+                ("lc_cells_scanned", C.c_uint64)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

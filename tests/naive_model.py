@@ -101,7 +101,7 @@ class Naive:
         self.departed_flag = [False] * len(self.routes)
         self.k = cfg["t0_step"]
         self.st = dict(departed=0, arrived=0, vehicle_updates=0, cells_scanned=0, clamps=0,
-                       lane_changes=0, lc_evals=0, route_reads=0)
+                       lane_changes=0, lc_evals=0, route_reads=0, lc_cells_scanned=0)
         self.entry = [0] * self.E
         self.exit = [0] * self.E
 
@@ -131,6 +131,23 @@ class Naive:
         return r[v.r + 1] if v.r + 1 < len(r) else None
 
     # ----------------------------------------------------------- lane change --
+    def _scan_up(self, occ, lo, hi):
+        """First occupied cell in [lo, hi] of a lane whose occupied front cells
+        are `occ` (None if none); the cells an upward scan reads to find it
+        are added to lc_cells_scanned."""
+        hits = [c for c in occ if lo <= c <= hi]
+        hit = min(hits) if hits else None
+        self.st["lc_cells_scanned"] += (hit - lo + 1) if hit is not None else max(0, hi - lo + 1)
+        return hit
+
+    def _scan_down(self, occ, hi, lo):
+        """Last occupied cell in [lo, hi] (None if none), counted as a
+        downward scan from hi."""
+        hits = [c for c in occ if lo <= c <= hi]
+        hit = max(hits) if hits else None
+        self.st["lc_cells_scanned"] += (hi - hit + 1) if hit is not None else max(0, hi - lo + 1)
+        return hit
+
     def lc_decide(self, v, k):
         c = self.cfg
         L, H = c["veh_len_cells"], c["horizon_cells"]
@@ -180,22 +197,26 @@ class Naive:
             if not (_u(c["seed"], v.id, k, 0) < F(m)):
                 return None
         else:
-            ahead = [self.cell(w) for w in self.in_lane(e, l) if cell < self.cell(w) <= hi]
-            if not ahead:
+            if not (v.v > 0):
+                return None            # a stopped vehicle has no slower leader
+            co = self._scan_up([self.cell(w) for w in self.in_lane(e, l)], cell + 1, hi)
+            if co is None:
                 return None
-            co = min(ahead)
             lv = [w for w in self.in_lane(e, l) if self.cell(w) == co][0]
             if not (F(_code(lv.v)) * F(0.125) < v.v):
                 return None
             own_gap = co - L - cell
-            ta = [self.cell(w) for w in target if cell + L <= self.cell(w) <= hi]
-            if ta and not (min(ta) - L - cell > own_gap):
+            ta = self._scan_up([self.cell(w) for w in target], cell + L, hi)
+            if ta is not None and not (ta - L - cell > own_gap):
                 return None
         self.st["lc_evals"] += 1
-        if any(abs(self.cell(w) - cell) <= L - 1 for w in target):
-            return None
-        lead = [w for w in target if cell + L <= self.cell(w) <= hi]
-        lag = [w for w in target if max(0, cell - H) <= self.cell(w) <= cell - L]
+        tcells = [self.cell(w) for w in target]
+        if self._scan_up(tcells, max(0, cell - L + 1), min(cell + L - 1, self.C[e] - 1)) is not None:
+            return None                # lateral overlap
+        ca = self._scan_up(tcells, cell + L, hi)
+        cb = self._scan_down(tcells, cell - L, max(0, cell - H))
+        lead = [w for w in target if self.cell(w) == ca] if ca is not None else []
+        lag = [w for w in target if self.cell(w) == cb] if cb is not None else []
         g = F(c["g_low"]) if v.v < F(c["g_speed_split"]) else F(c["g_high"])
         alpha = F(c["alpha_lo"]) + (F(c["alpha_hi"]) - F(c["alpha_lo"])) * _u(c["seed"], v.id, 0, 3)
         if lead:

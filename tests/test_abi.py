@@ -48,9 +48,9 @@ def test_config_layout_matches_header(lib):
 #include <stddef.h>
 #include "manta.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(manta_config), offsetof(manta_config, lc_x0_m),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(manta_config), offsetof(manta_config, lc_x0_m),
          offsetof(manta_config, t0_step), offsetof(manta_config, seed), offsetof(manta_config, speed_sigma_frac),
-         sizeof(manta_stats_t), offsetof(manta_stats_t, route_reads));
+         sizeof(manta_stats_t), offsetof(manta_stats_t, route_reads), offsetof(manta_stats_t, lc_cells_scanned));
   return 0;
 }
 '''
@@ -62,7 +62,7 @@ int main(void) {
         vals = list(map(int, subprocess.check_output([exe]).split()))
     M, S = manta.MantaConfig, manta.MantaStats
     assert vals == [C.sizeof(M), M.lc_x0_m.offset, M.t0_step.offset, M.seed.offset, M.speed_sigma_frac.offset,
-                    C.sizeof(S), S.route_reads.offset]
+                    C.sizeof(S), S.route_reads.offset, S.lc_cells_scanned.offset]
 
 
 def test_default_config(lib):

@@ -78,6 +78,7 @@ def test_oracle_equals_naive(seed, ci):
     st = s.stats()
     for key, val in nv.st.items():
         assert st[key] == val, (key, st[key], val)
+    assert st["lc_evals"] == 0 or st["lc_cells_scanned"] > 0
     ec = s.edge_counters(0)
     assert list(ec["entries"]) == nv.entry and list(ec["exits"]) == nv.exit
     for e in range(net.n_edges):
