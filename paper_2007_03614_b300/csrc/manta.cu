@@ -482,7 +482,7 @@ manta_status manta_create(int32_t n_nodes, int32_t n_edges, const int32_t *edge_
   P.dep_key = dalloc<unsigned long long>(S, E, &ok);
   P.dep0 = dalloc<uint32_t>(S, E, &ok);
   P.dep1 = dalloc<uint32_t>(S, E, &ok);
-  P.dep_info = dalloc<uint32_t>(S, 4 * (size_t)E, &ok);
+  P.dep_info = dalloc<uint32_t>(S, 8 * (size_t)E, &ok);
   P.ctl = dalloc<Ctl>(S, 1, &ok);
   if (!ok) { manta_destroy(S); return fail(MANTA_E_OOM, "device allocation failed in manta_create"); }
   bool cp = upload(S, d_em, em) && upload(S, d_es, es) && upload(S, d_nt, ntype) && upload(S, d_esrc, esrc_u) &&

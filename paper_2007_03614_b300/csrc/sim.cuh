@@ -178,7 +178,8 @@ struct Params {
   // departure queues
   uint32_t *pending, *q_pos;
   uint32_t *dep_info;          // per departure-list entry of the step: edge, head trip or none,
-                               // competitors' slot range (4 words, written in P3, read in P4)
+                               // competitors' slot range; the trip's first route entry, route end,
+                               // lane word and next route entry (8 words, written in P3, read in P4)
   unsigned long long *dep_key;
   // per-lane request and stop-line slots
   unsigned long long *req_key;

@@ -1107,9 +1107,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       }
       if (req && IDX_OK(e, p.E, 11)) p.dep_key[e] = ((unsigned long long)tag << 32) | j;
       // what P4 needs of this departure in one entry: the edge, the queue
-      // head's trip (none when it does not request entry) and the slot range
-      // of its competitors, the in-lanes of the edge's tail node
-      reinterpret_cast<uint4 *>(p.dep_info)[i] = make_uint4(e, req ? j : MANTA_NONE, rg.x, rg.y);
+      // head's trip (none when it does not request entry), the slot range of
+      // its competitors (the in-lanes of the edge's tail node), and the
+      // trip's route bounds, lane word and next route entry, so that P4's
+      // chain of dependent round trips starts at the competitors
+      uint32_t rc = 0u, rend = 0u, ld0 = 0u, nx0 = 0u;
+      if (req) {
+        rc = __ldg(p.route_off + j);
+        rend = __ldg(p.route_off + j + 1u);
+        ld0 = ld_for_entry(p, rc, 0u);
+        nx0 = rc + 1u < rend ? __ldg(p.route + rc + 1u) : 0u;
+      }
+      uint4 *di = reinterpret_cast<uint4 *>(p.dep_info) + 2u * i;
+      di[0] = make_uint4(e, req ? j : MANTA_NONE, rg.x, rg.y);
+      di[1] = make_uint4(rc, rend, ld0, nx0);
     }
     // vehicles
     const int64_t kr = k - p.t0;
@@ -1532,21 +1543,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) manta_step_kernel(Params p) {
       } else if (t < t_arr) {
         const uint32_t i = t - t_dep;
         // round trip 1: the entry P3 wrote (edge, head trip, competitors'
-        // slot range); 2: the competitors' requests, the edge record and the
-        // trip's route; 3: the winner's counter updates together
-        const uint4 di = __ldcg(reinterpret_cast<const uint4 *>(p.dep_info) + i);
+        // slot range, the trip's route bounds, lane word and next route
+        // entry); 2: the competitors' requests and the edge record; 3: the
+        // winner's counter updates together
+        const uint4 *dip = reinterpret_cast<const uint4 *>(p.dep_info) + 2u * i;
+        const uint4 di = __ldcg(dip), dr = __ldcg(dip + 1);
         const uint32_t e = di.x, j = di.y;
         bool won = j != MANTA_NONE;
         const EdgeMeta em = load_em(p, e);
         const uint32_t qp = __ldcg(p.q_pos + e);
-        uint32_t rc = 0u, rend = 0u, ld0 = 0u, nx0 = 0u;
-        if (won) {
-          rc = __ldg(p.route_off + j);
-          rend = __ldg(p.route_off + j + 1u);
-          ld0 = ld_for_entry(p, rc, 0u);
-          nx0 = rc + 1u < rend ? __ldg(p.route + rc + 1u) : 0u;
-          won = min_competitor(p, di.z, di.w, MANTA_NONE, target_key(e, 0u), tag) > j;
-        }
+        const uint32_t rc = dr.x, rend = dr.y, ld0 = dr.z, nx0 = dr.w;
+        if (won) won = min_competitor(p, di.z, di.w, MANTA_NONE, target_key(e, 0u), tag) > j;
         // the result of this atomic is first used after the list append
         // below, so the two round trips overlap; the new vehicle's state
         // goes to its list position
