@@ -652,7 +652,8 @@ struct Walk {
   int sl;            // lane on the segment
   uint32_t r;        // route entry of the segment
   uint32_t se;       // its edge
-  uint32_t nent;     // route entry r + 1 (fetched one segment ahead)
+  uint32_t nent;     // route entry r + 1 (for the vehicle's own edge from its state, then fetched one
+                     // segment ahead)
   EdgeMeta sm;       // record of the segment's edge
   bool own;          // the segment is the vehicle's own edge
 };
