@@ -511,6 +511,38 @@ def test_discretionary_change_gap_acceptance_hand_trace(lead_at, lag_at):
     assert s.stats()["lane_changes"] == (1 if expected else 0)
 
 
+@pytest.mark.parametrize("lead_at,lag_at,cells", [
+    # vehicle 0 (cell 50, lane 0, behind the slow vehicle 1 at cell 60) is evaluated in full:
+    # own lane 51..60 (10), target lead 55..80 (26), overlap window 46..54 (9), lead again (26),
+    # lag 45..20 downward (26); vehicle 1 finds nothing ahead in 61..299 (239)
+    (80, 20, 10 + 26 + 9 + 26 + 26 + 239),
+    # target lead at 62: 55..62 (8) twice; lag 45..30 (16)
+    (62, 30, 10 + 8 + 9 + 8 + 16 + 239),
+    # a lane-1 vehicle at 48 overlaps: the overlap scan stops at its third cell
+    (80, 48, 10 + 26 + 3 + 239),
+    # target lead at 58 leaves no more room than the own lane: rejected after 55..58 (4)
+    (58, 20, 10 + 4 + 239),
+])
+def test_lane_change_scan_cells_hand_count(lead_at, lag_at, cells):
+    """lc_cells_scanned counts every lane-map cell the lane-change rule's scans
+    read (Section II-D: own-lane leader and target lead of a discretionary
+    change, then the lateral-overlap window, the lead and the lag of Eqs. 3-4),
+    each scan from its first cell to its hit or the end of its range.  Counted
+    here by hand on the hand-trace layout above for the first step (even: the
+    target is lane 1; the lane-1 vehicles have no lane 2 to move to)."""
+    net = nets.line(1, length=300.0, lanes=2, speed=20.0)
+    tr = nets.trips([[0]] * 4, [1e7] * 4)
+    s = O.OracleSim(net, seed=11)
+    nets.load(s, tr)
+    s.place(0, 0, 0, 50.2, 10.0)
+    s.place(1, 0, 0, 60.2, 2.0)
+    s.place(2, 0, 1, lead_at + 0.2, 6.0)
+    s.place(3, 0, 1, lag_at + 0.2, 12.0)
+    assert int(s.edge_cells()[0]) == 300
+    s.step(1)
+    assert s.stats()["lc_cells_scanned"] == cells
+
+
 def test_mandatory_change_probability_eq2():
     """Eq. 2 with x0 = 1 m: at 1 m from the end the change is certain (if the
     gaps accept); far from the end (m ~ 0) it never happens."""
