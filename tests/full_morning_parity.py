@@ -1,0 +1,115 @@
+"""Whole-morning parity of the CUDA path against the CPU oracle on the headline
+workload: the metro-shaped network and 3.2M trips, 05:00-12:00 at dt = 0.5 s
+(50,400 steps).  Too long for the test suite (the oracle needs hours on one
+core), so it runs as a script in three parts:
+
+    python tests/full_morning_parity.py --side oracle --out DIR_A    # CPU, hours
+    python tests/full_morning_parity.py --side gpu --out DIR_B       # one B300, seconds
+    python tests/full_morning_parity.py --compare DIR_A DIR_B
+
+Each side writes, at 08:00 and at 12:00, a digest of its whole state: SHA-256
+of every snapshot array (vehicles sorted by trip id; x and v as bit patterns),
+of the entry and exit counters, and of every statistics window's speed sums
+and counts, plus the statistics themselves.  The comparison requires every
+digest and statistic to be equal.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+T0_STEP = 36000                      # 05:00
+CHECKPOINTS = {"08:00": 21600, "12:00": 50400}
+WINDOW_STEPS = 600
+
+
+def _h(a: np.ndarray) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def digest(sim, steps_done: int) -> dict:
+    st = sim.stats()
+    sn = sim.snapshot()
+    order = np.argsort(sn["id"], kind="stable")
+    out = {"stats": {k: int(v) for k, v in st.items()}, "snapshot": {}}
+    for key, dt in (("id", np.uint32), ("edge", np.int32), ("lane", np.uint8), ("dwell", np.uint8),
+                    ("route_pos", np.int32)):
+        out["snapshot"][key] = _h(np.asarray(sn[key]).astype(dt)[order])
+    for key in ("x", "v"):
+        out["snapshot"][key] = _h(np.asarray(sn[key], dtype=np.float32)[order].view(np.uint32))
+    ec = sim.edge_counters(0)
+    out["entries"] = _h(np.asarray(ec["entries"], dtype=np.uint32))
+    out["exits"] = _h(np.asarray(ec["exits"], dtype=np.uint32))
+    out["windows"] = []
+    for w in range((steps_done + WINDOW_STEPS - 1) // WINDOW_STEPS):
+        e = sim.edge_counters(w)
+        out["windows"].append([_h(np.asarray(e["speed_sum"], dtype=np.uint64)),
+                               _h(np.asarray(e["speed_cnt"], dtype=np.uint32))])
+    return out
+
+
+def run(side: str, out_dir: str) -> None:
+    import bench
+    os.makedirs(out_dir, exist_ok=True)
+    net, tr = bench.workload()
+    if side == "oracle":
+        from oracle import oracle as O
+        sim = O.OracleSim(net, t0_step=T0_STEP)
+    else:
+        import torch
+        from paper_2007_03614_b300 import manta
+        sim = manta.Sim(net, stream=torch.cuda.Stream(), t0_step=T0_STEP)
+    sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+    done, t_start = 0, time.time()
+    for name, target in CHECKPOINTS.items():
+        while done < target:
+            n = min(1800, target - done)
+            sim.step(n)
+            done += n
+            print(f"{side} step {done} ({time.time() - t_start:.0f} s)", flush=True)
+        d = digest(sim, done)
+        d["side"], d["at"], d["steps"] = side, name, done
+        with open(os.path.join(out_dir, f"{side}_{name.replace(':', '')}.json"), "w") as f:
+            json.dump(d, f)
+        print(f"{side} {name}: {d['stats']}", flush=True)
+
+
+def compare(a_dir: str, b_dir: str) -> int:
+    bad = 0
+    for name in CHECKPOINTS:
+        tag = name.replace(":", "")
+        fa = [f for f in os.listdir(a_dir) if f.endswith(f"_{tag}.json")]
+        fb = [f for f in os.listdir(b_dir) if f.endswith(f"_{tag}.json")]
+        if not fa or not fb:
+            print(f"{name}: missing ({fa}, {fb})")
+            bad += 1
+            continue
+        a = json.load(open(os.path.join(a_dir, fa[0])))
+        b = json.load(open(os.path.join(b_dir, fb[0])))
+        same = {k: a[k] == b[k] for k in ("stats", "snapshot", "entries", "exits", "windows")}
+        print(f"{name}: steps {a['steps']}, on network {a['stats']['on_network']}, "
+              f"vehicle updates {a['stats']['vehicle_updates']}: "
+              + ", ".join(f"{k} {'equal' if v else 'DIFFERENT'}" for k, v in same.items()))
+        bad += sum(not v for v in same.values())
+    return bad
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--side", choices=["oracle", "gpu"])
+    ap.add_argument("--out")
+    ap.add_argument("--compare", nargs=2)
+    args = ap.parse_args()
+    if args.compare:
+        sys.exit(1 if compare(*args.compare) else 0)
+    run(args.side, args.out)
