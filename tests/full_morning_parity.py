@@ -7,7 +7,12 @@ core), so it runs as a script in three parts:
     python tests/full_morning_parity.py --side gpu --out DIR_B       # one B300, seconds
     python tests/full_morning_parity.py --compare DIR_A DIR_B
 
-Each side writes, at 08:00 and at 12:00, a digest of its whole state: SHA-256
+With --case peak-hour both sides start instead from the dense peak-hour state
+(the trips departing 07:00-07:30 placed along their routes at 07:30, the
+07:00-08:00 trips loaded) and run one hour, to 08:30 (about 1 h on one core).
+
+Each side writes, at each checkpoint (08:00 and 12:00; 08:30 for the peak
+hour), a digest of its whole state: SHA-256
 of every snapshot array (vehicles sorted by trip id; x and v as bit patterns),
 of the entry and exit counters, and of every statistics window's speed sums
 and counts, plus the statistics themselves.  The comparison requires every
@@ -30,6 +35,7 @@ if ROOT not in sys.path:
 
 T0_STEP = 36000                      # 05:00
 CHECKPOINTS = {"08:00": 21600, "12:00": 50400}
+PEAK_CHECKPOINTS = {"08:30": 7200}   # steps after 07:30
 WINDOW_STEPS = 600
 
 
@@ -58,20 +64,29 @@ def digest(sim, steps_done: int) -> dict:
     return out
 
 
-def run(side: str, out_dir: str) -> None:
+def run(side: str, out_dir: str, case: str = "morning") -> None:
     import bench
     os.makedirs(out_dir, exist_ok=True)
     net, tr = bench.workload()
+    t0, checkpoints = T0_STEP, CHECKPOINTS
+    if case == "peak-hour":
+        t0, tr, pl = bench.peak_sample(net, tr)
+        checkpoints = PEAK_CHECKPOINTS
     if side == "oracle":
         from oracle import oracle as O
-        sim = O.OracleSim(net, t0_step=T0_STEP)
+        sim = O.OracleSim(net, t0_step=t0)
     else:
         import torch
         from paper_2007_03614_b300 import manta
-        sim = manta.Sim(net, stream=torch.cuda.Stream(), t0_step=T0_STEP)
+        sim = manta.Sim(net, stream=torch.cuda.Stream(), t0_step=t0)
     sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
+    if case == "peak-hour":
+        if side == "oracle":
+            sim.place_many(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
+        else:
+            sim.place(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
     done, t_start = 0, time.time()
-    for name, target in CHECKPOINTS.items():
+    for name, target in checkpoints.items():
         while done < target:
             n = min(1800, target - done)
             sim.step(n)
@@ -86,7 +101,8 @@ def run(side: str, out_dir: str) -> None:
 
 def compare(a_dir: str, b_dir: str) -> int:
     bad = 0
-    for name in CHECKPOINTS:
+    names = sorted({f.rsplit("_", 1)[1][:-5] for d in (a_dir, b_dir) for f in os.listdir(d) if f.endswith(".json")})
+    for name in [n[:2] + ":" + n[2:] for n in names]:
         tag = name.replace(":", "")
         fa = [f for f in os.listdir(a_dir) if f.endswith(f"_{tag}.json")]
         fb = [f for f in os.listdir(b_dir) if f.endswith(f"_{tag}.json")]
@@ -109,7 +125,8 @@ if __name__ == "__main__":
     ap.add_argument("--side", choices=["oracle", "gpu"])
     ap.add_argument("--out")
     ap.add_argument("--compare", nargs=2)
+    ap.add_argument("--case", choices=["morning", "peak-hour"], default="morning")
     args = ap.parse_args()
     if args.compare:
         sys.exit(1 if compare(*args.compare) else 0)
-    run(args.side, args.out)
+    run(args.side, args.out, args.case)
