@@ -9,7 +9,11 @@ core), so it runs as a script in three parts:
 
 With --case peak-hour both sides start instead from the dense peak-hour state
 (the trips departing 07:00-07:30 placed along their routes at 07:30, the
-07:00-08:00 trips loaded) and run one hour, to 08:30 (about 1 h on one core).
+07:00-08:00 trips loaded) and run one hour, to 08:30 (about 40 min on one
+core).  With --case stress-incident they run the stress megaregion (~1.6M
+edges) from 08:00 to 09:00 with its incident lane closures active: the trips
+departing 07:45-08:00 placed along their routes (none in a closed lane), the
+07:45-08:05 trips loaded.
 
 Each side writes, at each checkpoint (08:00 and 12:00; 08:30 for the peak
 hour), a digest of its whole state: SHA-256
@@ -36,6 +40,32 @@ if ROOT not in sys.path:
 T0_STEP = 36000                      # 05:00
 CHECKPOINTS = {"08:00": 21600, "12:00": 50400}
 PEAK_CHECKPOINTS = {"08:30": 7200}   # steps after 07:30
+STRESS_CHECKPOINTS = {"08:30": 3600, "09:00": 7200}   # steps after 08:00
+
+
+def _subset(tr, lo_s, hi_s):
+    from paper_2007_03614_b300 import synth
+    sel = np.nonzero((tr.depart_time_s >= lo_s) & (tr.depart_time_s < hi_s))[0]
+    routes = [tr.route_edges[tr.route_off[i]:tr.route_off[i + 1]] for i in sel]
+    off = np.zeros(len(sel) + 1, np.int64)
+    off[1:] = np.cumsum([len(r) for r in routes])
+    return synth.Trips(route_off=off, route_edges=np.concatenate(routes).astype(np.int32),
+                       depart_time_s=tr.depart_time_s[sel])
+
+
+def _stress_case():
+    from paper_2007_03614_b300 import synth
+    net = synth.stress_network()
+    tr = synth.stress_trips(net)
+    clo = synth.incident_closures(net)
+    lo = 8 * 3600
+    sub = _subset(tr, lo - 900, lo + 300)
+    pl = synth.dense_state(net, sub, lo - 900, lo, head_frac=0.15, seed=13)
+    closed = {(e, l) for (e, l, _, _) in clo}
+    e = sub.route_edges[sub.route_off[pl.trip] + pl.route_pos]
+    keep = np.array([(int(a), int(b)) not in closed for a, b in zip(e, pl.lane)])
+    args = [a[keep] for a in (pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)]
+    return net, sub, int(lo / 0.5), args, clo
 WINDOW_STEPS = 600
 
 
@@ -67,11 +97,16 @@ def digest(sim, steps_done: int) -> dict:
 def run(side: str, out_dir: str, case: str = "morning") -> None:
     import bench
     os.makedirs(out_dir, exist_ok=True)
-    net, tr = bench.workload()
-    t0, checkpoints = T0_STEP, CHECKPOINTS
+    t0, checkpoints, place, closures = T0_STEP, CHECKPOINTS, None, ()
+    if case == "stress-incident":
+        net, tr, t0, place, closures = _stress_case()
+        checkpoints = STRESS_CHECKPOINTS
+    else:
+        net, tr = bench.workload()
     if case == "peak-hour":
         t0, tr, pl = bench.peak_sample(net, tr)
         checkpoints = PEAK_CHECKPOINTS
+        place = [pl.trip, pl.route_pos, pl.lane, pl.x, pl.v]
     if side == "oracle":
         from oracle import oracle as O
         sim = O.OracleSim(net, t0_step=t0)
@@ -79,12 +114,14 @@ def run(side: str, out_dir: str, case: str = "morning") -> None:
         import torch
         from paper_2007_03614_b300 import manta
         sim = manta.Sim(net, stream=torch.cuda.Stream(), t0_step=t0)
+    for (e, l, k0, k1) in closures:
+        sim.set_lane_closure(e, l, k0, k1)
     sim.load_trips(tr.route_off, tr.route_edges, tr.depart_time_s)
-    if case == "peak-hour":
+    if place is not None:
         if side == "oracle":
-            sim.place_many(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
+            sim.place_many(*place)
         else:
-            sim.place(pl.trip, pl.route_pos, pl.lane, pl.x, pl.v)
+            sim.place(*place)
     done, t_start = 0, time.time()
     for name, target in checkpoints.items():
         while done < target:
@@ -125,7 +162,7 @@ if __name__ == "__main__":
     ap.add_argument("--side", choices=["oracle", "gpu"])
     ap.add_argument("--out")
     ap.add_argument("--compare", nargs=2)
-    ap.add_argument("--case", choices=["morning", "peak-hour"], default="morning")
+    ap.add_argument("--case", choices=["morning", "peak-hour", "stress-incident"], default="morning")
     args = ap.parse_args()
     if args.compare:
         sys.exit(1 if compare(*args.compare) else 0)
