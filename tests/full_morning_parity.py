@@ -13,7 +13,9 @@ With --case peak-hour both sides start instead from the dense peak-hour state
 core).  With --case stress-incident they run the stress megaregion (~1.6M
 edges) from 08:00 to 09:00 with its incident lane closures active: the trips
 departing 07:45-08:00 placed along their routes (none in a closed lane), the
-07:45-08:05 trips loaded.
+07:45-08:05 trips loaded.  With --case late-morning they run the metro network
+from 11:00 to 12:00 from the dense late-morning state (the trips departing
+09:30-11:00 placed along their routes, the 09:30-11:05 trips loaded).
 
 Each side writes, at each checkpoint (08:00 and 12:00; 08:30 for the peak
 hour), a digest of its whole state: SHA-256
@@ -41,6 +43,7 @@ T0_STEP = 36000                      # 05:00
 CHECKPOINTS = {"08:00": 21600, "12:00": 50400}
 PEAK_CHECKPOINTS = {"08:30": 7200}   # steps after 07:30
 STRESS_CHECKPOINTS = {"08:30": 3600, "09:00": 7200}   # steps after 08:00
+LATE_CHECKPOINTS = {"11:30": 3600, "12:00": 7200}     # steps after 11:00
 
 
 def _subset(tr, lo_s, hi_s):
@@ -107,6 +110,13 @@ def run(side: str, out_dir: str, case: str = "morning") -> None:
         t0, tr, pl = bench.peak_sample(net, tr)
         checkpoints = PEAK_CHECKPOINTS
         place = [pl.trip, pl.route_pos, pl.lane, pl.x, pl.v]
+    elif case == "late-morning":
+        from paper_2007_03614_b300 import synth
+        lo = 11 * 3600
+        tr = _subset(tr, lo - 5400, lo + 300)
+        pl = synth.dense_state(net, tr, lo - 5400, lo, head_frac=0.1, seed=11)
+        t0, checkpoints = int(lo / 0.5), LATE_CHECKPOINTS
+        place = [pl.trip, pl.route_pos, pl.lane, pl.x, pl.v]
     if side == "oracle":
         from oracle import oracle as O
         sim = O.OracleSim(net, t0_step=t0)
@@ -162,7 +172,8 @@ if __name__ == "__main__":
     ap.add_argument("--side", choices=["oracle", "gpu"])
     ap.add_argument("--out")
     ap.add_argument("--compare", nargs=2)
-    ap.add_argument("--case", choices=["morning", "peak-hour", "stress-incident"], default="morning")
+    ap.add_argument("--case", choices=["morning", "peak-hour", "stress-incident", "late-morning"],
+                    default="morning")
     args = ap.parse_args()
     if args.compare:
         sys.exit(1 if compare(*args.compare) else 0)
